@@ -1,0 +1,17 @@
+"""FP64 CPU oracle for the regularised field-map estimator (arXiv 2005.08661).
+
+TEST INFRASTRUCTURE ONLY: the tests, the package smoke check and the benchmark's
+CPU-baseline leg may load it; the library's product path never does.  It shares no
+code with the CUDA path.  See fm_oracle.c for what each function computes and the
+paper passages it follows.
+
+Pins: every function here is checked against something the paper or the
+mathematics fixes (tests/test_oracle_*.py).  The exact iterate sequence of the
+solver beyond those pins (search-direction sign, Polak-Ribiere form, fixed inner
+step count) follows the readings stated in fm_oracle.c and is "parity unpinned"
+against the paper itself.
+"""
+from .oracle import Oracle, build_oracle, ic0_factor, ic0_solve, voxel_terms, voxel_r, lib_path
+
+__all__ = ["Oracle", "build_oracle", "ic0_factor", "ic0_solve", "voxel_terms", "voxel_r",
+           "lib_path"]

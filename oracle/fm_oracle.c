@@ -1,0 +1,463 @@
+/*
+ * fm_oracle.c -- plain, slow FP64 CPU oracle for the regularised 3-D field-map
+ * estimator of Lin & Fessler, "Efficient Regularized Field Map Estimation in 3D
+ * MRI" (arXiv 2005.08661).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the library's product path may link, load
+ * or call this file: only the tests, the package's smoke check and the benchmark's
+ * CPU-baseline leg use it.  It shares no code, header, table or constant with the
+ * CUDA path.
+ *
+ * What it computes, in the paper's order and notation (units: t in the caller's
+ * unit, w in radians per that unit):
+ *   Eq. 3  r_cdmnj = Gamma_mn / (sum_c' |s_c'j|^2) * s_cj * conj(s_dj) * conj(y_cmj) * y_dnj,
+ *          Gamma_mn = 1/L (field-map case).  Precomputed once (Algorithm box).
+ *   Eq. 2  Phi(w) = sum_j sum_{c,d,m,n} |r| (1 - cos(angle(r) + w_j (t_m - t_n))), literal
+ *          (all ordered tuples, including m = n).
+ *   Eq. 5  Psi = Phi + beta/2 ||C w||^2, C = non-periodic first-order differences between
+ *          6-neighbours that are both inside the support mask.
+ *   Eq. 8  grad Psi = grad Phi + beta C'C w, with (grad Phi)_j =
+ *          sum |r| (t_m - t_n) sin(angle(r) + w_j (t_m - t_n)) (first power of t_m - t_n:
+ *          the derivative of Eq. 2).
+ *   Eq. 9-11  d_j = sum |r| (t_m - t_n)^2 sin(u)/u, u = angle(r) + w_j (t_m - t_n) wrapped
+ *          into [-pi, pi] by removing the nearest multiple of 2 pi (Huber's optimal
+ *          curvature for 1 - cos).
+ *   Eq. 9  H = diag(d) + beta C'C over the mask voxels.
+ *   Eq. 12 IC(0): a generic incomplete Cholesky on H's nonzero pattern, textbook
+ *          right-looking k,i,j loop, natural (x fastest, then y, then z) order.
+ *   Eq. 6  w0_j = angle(conj(sum_c conj(s_c) y_c1) * sum_d conj(s_d) y_d2) / (t_2 - t_1).
+ *   Algorithm box + Eq. 13-16: preconditioned Polak-Ribiere NCG, z = -p + mu z with
+ *          mu^0 = 0, mu^i = (g^i - g^{i-1})'p^i / ((g^{i-1})'p^{i-1}); monotonic line
+ *          search alpha_{k+1} = alpha_k - f'(alpha_k) / (d^(k) + beta ||C z||^2),
+ *          d^(k) = sum_j z_j^2 d_j(w + alpha_k z), alpha_0 = 0, N_ls fixed steps.
+ * All reductions are sequential in voxel order.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_ERR_ARG (-1)
+#define ORC_ERR_NOT_PD (-4)
+#define ORC_ERR_OOM (-7)
+#define ORC_MAXL 32
+
+typedef struct {
+    int nx, ny, nz, nc, L;
+    long nv;
+    double beta;
+    double te[ORC_MAXL];
+    unsigned char *mask; /* [nv], 1 = unknown */
+    double *y;           /* [L][nc][nv][2] */
+    double *s;           /* [nc][nv][2] or NULL (s = 1) */
+    long T;              /* tuples per voxel: nc*nc*L*L */
+    long *slot;          /* [nv] -> index among mask voxels, -1 outside */
+    long nm;             /* number of mask voxels */
+    double *rabs, *rang; /* [nm][T] modulus and angle of r_cdmnj */
+    double *dt;          /* [T] t_m - t_n of each tuple */
+} orc_t;
+
+static const double TWO_PI = 6.283185307179586476925286766559;
+
+/* wrap an angle into [-pi, pi] by removing the nearest multiple of 2 pi */
+static double wrap_angle(double th) { return th - TWO_PI * nearbyint(th / TWO_PI); }
+
+static double sinc(double u) { return u == 0.0 ? 1.0 : sin(u) / u; }
+
+/* Eq. 3 for one voxel: y_vox[(l*nc + c)*2 + {0,1}], s_vox[c*2 + {0,1}] (NULL: s = 1). */
+static void pair_weights(int nc, int L, const double *y_vox, long ystride, const double *s_vox,
+                         long sstride, double *rabs, double *rang) {
+    double S = 0.0;
+    for (int c = 0; c < nc; ++c) {
+        double sr = s_vox ? s_vox[c * sstride] : 1.0, si = s_vox ? s_vox[c * sstride + 1] : 0.0;
+        S += sr * sr + si * si;
+    }
+    const double G = 1.0 / (double)L;
+    long t = 0;
+    for (int c = 0; c < nc; ++c)
+        for (int d = 0; d < nc; ++d)
+            for (int m = 0; m < L; ++m)
+                for (int n = 0; n < L; ++n, ++t) {
+                    if (S == 0.0) { rabs[t] = 0.0; rang[t] = 0.0; continue; }
+                    double scr = s_vox ? s_vox[c * sstride] : 1.0, sci = s_vox ? s_vox[c * sstride + 1] : 0.0;
+                    double sdr = s_vox ? s_vox[d * sstride] : 1.0, sdi = s_vox ? -s_vox[d * sstride + 1] : 0.0; /* conj(s_d) */
+                    const double *ycm = y_vox + (long)(m * nc + c) * ystride;
+                    const double *ydn = y_vox + (long)(n * nc + d) * ystride;
+                    double ar = ycm[0], ai = -ycm[1]; /* conj(y_cm) */
+                    double br = ydn[0], bi = ydn[1];
+                    /* s_c * conj(s_d) */
+                    double pr = scr * sdr - sci * sdi, pi_ = scr * sdi + sci * sdr;
+                    /* * conj(y_cm) */
+                    double qr = pr * ar - pi_ * ai, qi = pr * ai + pi_ * ar;
+                    /* * y_dn */
+                    double rr = qr * br - qi * bi, ri = qr * bi + qi * br;
+                    rr *= G / S;
+                    ri *= G / S;
+                    rabs[t] = hypot(rr, ri);
+                    rang[t] = atan2(ri, rr);
+                }
+}
+
+static void tuple_dt(int nc, int L, const double *te, double *dt) {
+    long t = 0;
+    for (int c = 0; c < nc; ++c)
+        for (int d = 0; d < nc; ++d)
+            for (int m = 0; m < L; ++m)
+                for (int n = 0; n < L; ++n, ++t) dt[t] = te[m] - te[n];
+}
+
+/* per-voxel data-term pieces at w: phi (Eq. 2 term), dphi (Eq. 8 term), curvature (Eq. 10) */
+static void voxel_terms(long T, const double *rabs, const double *rang, const double *dt, double w,
+                        double *phi, double *dphi, double *curv) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (long t = 0; t < T; ++t) {
+        double th = rang[t] + w * dt[t];
+        if (phi) a += rabs[t] * (1.0 - cos(th));
+        if (dphi) b += rabs[t] * dt[t] * sin(th);
+        if (curv) c += rabs[t] * dt[t] * dt[t] * sinc(wrap_angle(th));
+    }
+    if (phi) *phi = a;
+    if (dphi) *dphi = b;
+    if (curv) *curv = c;
+}
+
+void orc_destroy(orc_t *h) {
+    if (!h) return;
+    free(h->mask); free(h->y); free(h->s); free(h->slot); free(h->rabs); free(h->rang); free(h->dt);
+    free(h);
+}
+
+/* y: [L][nc][nv] complex (interleaved re,im); s: [nc][nv] complex or NULL; mask: [nv] or NULL */
+int orc_create(orc_t **out, int nx, int ny, int nz, int nc, int L, const double *y, const double *s,
+               const double *te, const unsigned char *mask, double beta) {
+    if (!out || nx < 1 || ny < 1 || nz < 1 || nc < 1 || L < 2 || L > ORC_MAXL || !y || !te) return ORC_ERR_ARG;
+    if (!s && nc != 1) return ORC_ERR_ARG;
+    orc_t *h = (orc_t *)calloc(1, sizeof(orc_t));
+    if (!h) return ORC_ERR_OOM;
+    h->nx = nx; h->ny = ny; h->nz = nz; h->nc = nc; h->L = L;
+    h->nv = (long)nx * ny * nz;
+    h->beta = beta;
+    for (int l = 0; l < L; ++l) h->te[l] = te[l];
+    h->T = (long)nc * nc * L * L;
+    h->mask = (unsigned char *)malloc(h->nv);
+    h->y = (double *)malloc(sizeof(double) * 2 * L * nc * h->nv);
+    h->s = s ? (double *)malloc(sizeof(double) * 2 * nc * h->nv) : NULL;
+    h->slot = (long *)malloc(sizeof(long) * h->nv);
+    h->dt = (double *)malloc(sizeof(double) * h->T);
+    if (!h->mask || !h->y || (s && !h->s) || !h->slot || !h->dt) { orc_destroy(h); return ORC_ERR_OOM; }
+    for (long j = 0; j < h->nv; ++j) h->mask[j] = mask ? (mask[j] != 0) : 1;
+    memcpy(h->y, y, sizeof(double) * 2 * L * nc * h->nv);
+    if (s) memcpy(h->s, s, sizeof(double) * 2 * nc * h->nv);
+    tuple_dt(nc, L, h->te, h->dt);
+    h->nm = 0;
+    for (long j = 0; j < h->nv; ++j) h->slot[j] = h->mask[j] ? h->nm++ : -1;
+    h->rabs = (double *)malloc(sizeof(double) * (h->nm ? h->nm : 1) * h->T);
+    h->rang = (double *)malloc(sizeof(double) * (h->nm ? h->nm : 1) * h->T);
+    if (!h->rabs || !h->rang) { orc_destroy(h); return ORC_ERR_OOM; }
+    /* precompute r_cdmnj (Eq. 3) once, as the Algorithm box does */
+    for (long j = 0; j < h->nv; ++j) {
+        long k = h->slot[j];
+        if (k < 0) continue;
+        pair_weights(nc, L, h->y + 2 * j, 2 * h->nv, h->s ? h->s + 2 * j : NULL, 2 * h->nv,
+                     h->rabs + k * h->T, h->rang + k * h->T);
+    }
+    *out = h;
+    return ORC_OK;
+}
+
+long orc_num_unknowns(const orc_t *h) { return h->nm; }
+
+/* Phi (Eq. 2) over the mask voxels */
+double orc_phi(const orc_t *h, const double *w) {
+    double acc = 0.0;
+    for (long j = 0; j < h->nv; ++j) {
+        long k = h->slot[j];
+        if (k < 0) continue;
+        double p;
+        voxel_terms(h->T, h->rabs + k * h->T, h->rang + k * h->T, h->dt, w[j], &p, NULL, NULL);
+        acc += p;
+    }
+    return acc;
+}
+
+/* neighbour helpers: forward neighbours (+x, +y, +z) of voxel j, -1 if outside grid or mask */
+static long fwd_nbr(const orc_t *h, long j, int axis) {
+    long x = j % h->nx, y = (j / h->nx) % h->ny, z = j / ((long)h->nx * h->ny);
+    long k = -1;
+    if (axis == 0 && x + 1 < h->nx) k = j + 1;
+    if (axis == 1 && y + 1 < h->ny) k = j + h->nx;
+    if (axis == 2 && z + 1 < h->nz) k = j + (long)h->nx * h->ny;
+    return (k >= 0 && h->mask[k]) ? k : -1;
+}
+
+static long bwd_nbr(const orc_t *h, long j, int axis) {
+    long x = j % h->nx, y = (j / h->nx) % h->ny, z = j / ((long)h->nx * h->ny);
+    long k = -1;
+    if (axis == 0 && x > 0) k = j - 1;
+    if (axis == 1 && y > 0) k = j - h->nx;
+    if (axis == 2 && z > 0) k = j - (long)h->nx * h->ny;
+    return (k >= 0 && h->mask[k]) ? k : -1;
+}
+
+/* sum over edges (both ends in the mask) of (a_j - a_k)(b_j - b_k) */
+static double edge_dot(const orc_t *h, const double *a, const double *b) {
+    double acc = 0.0;
+    for (long j = 0; j < h->nv; ++j) {
+        if (!h->mask[j]) continue;
+        for (int ax = 0; ax < 3; ++ax) {
+            long k = fwd_nbr(h, j, ax);
+            if (k >= 0) acc += (a[j] - a[k]) * (b[j] - b[k]);
+        }
+    }
+    return acc;
+}
+
+/* beta/2 ||C w||^2 */
+double orc_reg(const orc_t *h, const double *w) { return 0.5 * h->beta * edge_dot(h, w, w); }
+
+double orc_cost(const orc_t *h, const double *w) { return orc_phi(h, w) + orc_reg(h, w); }
+
+/* grad Psi (Eq. 8); zero outside the mask */
+void orc_grad(const orc_t *h, const double *w, double *g) {
+    for (long j = 0; j < h->nv; ++j) {
+        long k = h->slot[j];
+        if (k < 0) { g[j] = 0.0; continue; }
+        double dp;
+        voxel_terms(h->T, h->rabs + k * h->T, h->rang + k * h->T, h->dt, w[j], NULL, &dp, NULL);
+        double lap = 0.0;
+        for (int ax = 0; ax < 3; ++ax) {
+            long a = fwd_nbr(h, j, ax), b = bwd_nbr(h, j, ax);
+            if (a >= 0) lap += w[j] - w[a];
+            if (b >= 0) lap += w[j] - w[b];
+        }
+        g[j] = dp + h->beta * lap;
+    }
+}
+
+/* gradient of the data term alone */
+void orc_grad_phi(const orc_t *h, const double *w, double *g) {
+    for (long j = 0; j < h->nv; ++j) {
+        long k = h->slot[j];
+        if (k < 0) { g[j] = 0.0; continue; }
+        voxel_terms(h->T, h->rabs + k * h->T, h->rang + k * h->T, h->dt, w[j], NULL, g + j, NULL);
+    }
+}
+
+/* curvature d_j of Eq. 10 at w; zero outside the mask */
+void orc_curv(const orc_t *h, const double *w, double *d) {
+    for (long j = 0; j < h->nv; ++j) {
+        long k = h->slot[j];
+        if (k < 0) { d[j] = 0.0; continue; }
+        voxel_terms(h->T, h->rabs + k * h->T, h->rang + k * h->T, h->dt, w[j], NULL, NULL, d + j);
+    }
+}
+
+/* Eq. 6: initial field map from the first two echoes; zero outside the mask */
+void orc_init(const orc_t *h, double *w) {
+    for (long j = 0; j < h->nv; ++j) {
+        if (!h->mask[j]) { w[j] = 0.0; continue; }
+        double z1r = 0, z1i = 0, z2r = 0, z2i = 0;
+        for (int c = 0; c < h->nc; ++c) {
+            double sr = h->s ? h->s[2 * (c * h->nv + j)] : 1.0;
+            double si = h->s ? -h->s[2 * (c * h->nv + j) + 1] : 0.0; /* conj(s_c) */
+            const double *y1 = h->y + 2 * ((long)(0 * h->nc + c) * h->nv + j);
+            const double *y2 = h->y + 2 * ((long)(1 * h->nc + c) * h->nv + j);
+            z1r += sr * y1[0] - si * y1[1]; z1i += sr * y1[1] + si * y1[0];
+            z2r += sr * y2[0] - si * y2[1]; z2i += sr * y2[1] + si * y2[0];
+        }
+        /* conj(z1) * z2 */
+        double pr = z1r * z2r + z1i * z2i, pi_ = z1r * z2i - z1i * z2r;
+        double ang = (pr == 0.0 && pi_ == 0.0) ? 0.0 : atan2(pi_, pr);
+        w[j] = ang / (h->te[1] - h->te[0]);
+    }
+}
+
+/* ---------------------------------------------------------------------------------
+ * IC(0) of H = diag(d) + beta C'C (Eq. 9, Eq. 12) on the mask voxels, generic sparse
+ * code: H's lower triangle in compressed-column form (diagonal first in each column,
+ * rows ascending), factorised in place by the textbook right-looking loop that only
+ * updates entries inside the pattern.  Unknowns are numbered in natural voxel order.
+ * colptr: [n+1], rowidx/val: capacity 4 nv, umap: [nv] voxel of each unknown.
+ * ------------------------------------------------------------------------------- */
+int orc_ic0(int nx, int ny, int nz, const unsigned char *mask, const double *d, double beta,
+            long *colptr, long *rowidx, double *val, long *umap, long *n_out, long *nnz_out) {
+    long nv = (long)nx * ny * nz, nxy = (long)nx * ny;
+    long *uidx = (long *)malloc(sizeof(long) * nv);
+    if (!uidx) return ORC_ERR_OOM;
+    long n = 0;
+    for (long j = 0; j < nv; ++j) {
+        uidx[j] = (mask == NULL || mask[j]) ? n : -1;
+        if (uidx[j] >= 0) umap[n++] = j;
+    }
+    /* assemble lower(H) column by column */
+    long nnz = 0;
+    for (long u = 0; u < n; ++u) {
+        long j = umap[u];
+        long x = j % nx, y = (j / nx) % ny, z = j / nxy;
+        long nb[6] = {x > 0 ? j - 1 : -1, x + 1 < nx ? j + 1 : -1, y > 0 ? j - nx : -1,
+                      y + 1 < ny ? j + nx : -1, z > 0 ? j - nxy : -1, z + 1 < nz ? j + nxy : -1};
+        int cnt = 0;
+        for (int q = 0; q < 6; ++q) if (nb[q] >= 0 && uidx[nb[q]] >= 0) ++cnt;
+        colptr[u] = nnz;
+        rowidx[nnz] = u; val[nnz] = d[j] + beta * cnt; ++nnz;
+        long up[3] = {nb[1], nb[3], nb[5]}; /* ascending voxel (and unknown) index */
+        for (int q = 0; q < 3; ++q)
+            if (up[q] >= 0 && uidx[up[q]] >= 0) { rowidx[nnz] = uidx[up[q]]; val[nnz] = -beta; ++nnz; }
+    }
+    colptr[n] = nnz;
+    free(uidx);
+    /* right-looking IC(0), updates restricted to the pattern */
+    for (long k = 0; k < n; ++k) {
+        double akk = val[colptr[k]];
+        if (!(akk > 0.0)) return ORC_ERR_NOT_PD;
+        double lkk = sqrt(akk);
+        val[colptr[k]] = lkk;
+        for (long p = colptr[k] + 1; p < colptr[k + 1]; ++p) val[p] /= lkk;
+        for (long p = colptr[k] + 1; p < colptr[k + 1]; ++p) {
+            long i = rowidx[p];
+            for (long q = colptr[k] + 1; q <= p; ++q) {
+                long jj = rowidx[q];
+                for (long r = colptr[jj]; r < colptr[jj + 1]; ++r)
+                    if (rowidx[r] == i) { val[r] -= val[p] * val[q]; break; }
+            }
+        }
+    }
+    *n_out = n;
+    *nnz_out = nnz;
+    return ORC_OK;
+}
+
+/* x = (L L')^{-1} b with the compressed-column factor of orc_ic0 */
+void orc_ic0_solve(long n, const long *colptr, const long *rowidx, const double *val, const double *b,
+                   double *x) {
+    double *v = (double *)malloc(sizeof(double) * (n ? n : 1));
+    for (long k = 0; k < n; ++k) v[k] = b[k];
+    for (long k = 0; k < n; ++k) { /* forward: L v = b */
+        v[k] /= val[colptr[k]];
+        for (long p = colptr[k] + 1; p < colptr[k + 1]; ++p) v[rowidx[p]] -= val[p] * v[k];
+    }
+    for (long k = n - 1; k >= 0; --k) { /* back: L' x = v */
+        double s = v[k];
+        for (long p = colptr[k] + 1; p < colptr[k + 1]; ++p) s -= val[p] * x[rowidx[p]];
+        x[k] = s / val[colptr[k]];
+    }
+    free(v);
+}
+
+/* p = (L L')^{-1} g for the factor of H(w) = diag(d(w)) + beta C'C; voxel-indexed arrays */
+int orc_precondition(const orc_t *h, const double *d, const double *g, double *p) {
+    long nv = h->nv;
+    long *colptr = (long *)malloc(sizeof(long) * (nv + 1));
+    long *rowidx = (long *)malloc(sizeof(long) * 4 * nv);
+    double *val = (double *)malloc(sizeof(double) * 4 * nv);
+    long *umap = (long *)malloc(sizeof(long) * nv);
+    double *gb = (double *)malloc(sizeof(double) * nv), *pb = (double *)malloc(sizeof(double) * nv);
+    int st = ORC_ERR_OOM;
+    if (colptr && rowidx && val && umap && gb && pb) {
+        long n, nnz;
+        st = orc_ic0(h->nx, h->ny, h->nz, h->mask, d, h->beta, colptr, rowidx, val, umap, &n, &nnz);
+        if (st == ORC_OK) {
+            for (long u = 0; u < n; ++u) gb[u] = g[umap[u]];
+            orc_ic0_solve(n, colptr, rowidx, val, gb, pb);
+            for (long j = 0; j < nv; ++j) p[j] = 0.0;
+            for (long u = 0; u < n; ++u) p[umap[u]] = pb[u];
+        }
+    }
+    free(colptr); free(rowidx); free(val); free(umap); free(gb); free(pb);
+    return st;
+}
+
+/* ---------------------------------------------------------------------------------
+ * Preconditioned NCG with the monotonic line search (Algorithm box, Eq. 13-16).
+ * w: [nv] in/out (read as the start point unless init != 0, which applies Eq. 6).
+ * cost_hist [niter+1], alpha_hist [niter], mu_hist [niter], inner_cost [niter*nls]
+ * (Psi after each inner step) may be NULL.  precond: 0 = IC(0), 1 = diagonal of H,
+ * 2 = none.
+ * ------------------------------------------------------------------------------- */
+int orc_solve(const orc_t *h, double *w, int init, int niter, int nls, int precond, double *cost_hist,
+              double *alpha_hist, double *mu_hist, double *inner_cost) {
+    long nv = h->nv;
+    double *g = (double *)calloc(nv, sizeof(double)), *gprev = (double *)calloc(nv, sizeof(double));
+    double *d = (double *)calloc(nv, sizeof(double)), *p = (double *)calloc(nv, sizeof(double));
+    double *z = (double *)calloc(nv, sizeof(double)), *wk = (double *)calloc(nv, sizeof(double));
+    double *gk = (double *)calloc(nv, sizeof(double));
+    int st = ORC_OK;
+    if (!g || !gprev || !d || !p || !z || !wk || !gk) { st = ORC_ERR_OOM; goto done; }
+    if (init) orc_init(h, w);
+    for (long j = 0; j < nv; ++j) if (!h->mask[j]) w[j] = 0.0;
+    if (cost_hist) cost_hist[0] = orc_cost(h, w);
+    double gp_prev = 0.0;
+    for (int i = 0; i < niter; ++i) {
+        orc_grad(h, w, g);
+        orc_curv(h, w, d);
+        if (precond == 0) {
+            st = orc_precondition(h, d, g, p);
+            if (st != ORC_OK) goto done;
+        } else {
+            for (long j = 0; j < nv; ++j) {
+                if (!h->mask[j]) { p[j] = 0.0; continue; }
+                if (precond == 2) { p[j] = g[j]; continue; }
+                int cnt = 0;
+                for (int ax = 0; ax < 3; ++ax) cnt += (fwd_nbr(h, j, ax) >= 0) + (bwd_nbr(h, j, ax) >= 0);
+                double hjj = d[j] + h->beta * cnt;
+                if (!(hjj > 0.0)) { st = ORC_ERR_NOT_PD; goto done; }
+                p[j] = g[j] / hjj;
+            }
+        }
+        double gp = 0.0, gprevp = 0.0;
+        for (long j = 0; j < nv; ++j) { gp += g[j] * p[j]; gprevp += gprev[j] * p[j]; }
+        double mu = 0.0;
+        if (i > 0 && gp_prev != 0.0) mu = (gp - gprevp) / gp_prev;
+        for (long j = 0; j < nv; ++j) z[j] = -p[j] + mu * z[j];
+        double cz2 = edge_dot(h, z, z), a = edge_dot(h, z, w);
+        double alpha = 0.0;
+        for (int k = 0; k < nls; ++k) {
+            for (long j = 0; j < nv; ++j) wk[j] = w[j] + alpha * z[j];
+            orc_grad_phi(h, wk, gk);
+            orc_curv(h, wk, d);
+            double fp = 0.0, D = 0.0;
+            for (long j = 0; j < nv; ++j) { fp += z[j] * gk[j]; D += z[j] * z[j] * d[j]; }
+            fp += h->beta * (a + alpha * cz2);
+            double den = D + h->beta * cz2;
+            if (den == 0.0) { alpha = 0.0; break; }
+            alpha = alpha - fp / den;
+            if (inner_cost) {
+                for (long j = 0; j < nv; ++j) wk[j] = w[j] + alpha * z[j];
+                inner_cost[(long)i * nls + k] = orc_cost(h, wk);
+            }
+        }
+        for (long j = 0; j < nv; ++j) w[j] += alpha * z[j];
+        for (long j = 0; j < nv; ++j) gprev[j] = g[j];
+        gp_prev = gp;
+        if (alpha_hist) alpha_hist[i] = alpha;
+        if (mu_hist) mu_hist[i] = mu;
+        if (cost_hist) cost_hist[i + 1] = orc_cost(h, w);
+    }
+done:
+    free(g); free(gprev); free(d); free(p); free(z); free(wk); free(gk);
+    return st;
+}
+
+/* One voxel's data-term pieces straight from its raw data (for sampled checks on
+ * volumes too large for the grid functions).  y_vox: [L][nc] complex, s_vox: [nc]
+ * complex or NULL.  out = {phi_j, dphi_j, d_j}. */
+int orc_voxel(int nc, int L, const double *te, const double *y_vox, const double *s_vox, double w,
+              double *out) {
+    if (nc < 1 || L < 2 || L > ORC_MAXL) return ORC_ERR_ARG;
+    long T = (long)nc * nc * L * L;
+    double *ra = (double *)malloc(sizeof(double) * T), *rg = (double *)malloc(sizeof(double) * T);
+    double *dt = (double *)malloc(sizeof(double) * T);
+    if (!ra || !rg || !dt) { free(ra); free(rg); free(dt); return ORC_ERR_OOM; }
+    pair_weights(nc, L, y_vox, 2, s_vox, 2, ra, rg);
+    tuple_dt(nc, L, te, dt);
+    voxel_terms(T, ra, rg, dt, w, out, out + 1, out + 2);
+    free(ra); free(rg); free(dt);
+    return ORC_OK;
+}
+
+/* raw r_cdmnj of Eq. 3 for one voxel (modulus, angle), T = nc*nc*L*L, order c,d,m,n */
+int orc_voxel_r(int nc, int L, const double *y_vox, const double *s_vox, double *rabs, double *rang) {
+    if (nc < 1 || L < 2 || L > ORC_MAXL) return ORC_ERR_ARG;
+    pair_weights(nc, L, y_vox, 2, s_vox, 2, rabs, rang);
+    return ORC_OK;
+}

@@ -1,0 +1,242 @@
+"""ctypes binding of the FP64 C oracle (test infrastructure only; see fm_oracle.c)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = None
+_LOCK = threading.Lock()
+
+ORC_OK, ORC_ERR_ARG, ORC_ERR_NOT_PD, ORC_ERR_OOM = 0, -1, -4, -7
+
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_lp = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+_u8p = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
+
+
+def lib_path():
+    return os.path.join(_BUILD, "liboracle.so")
+
+
+def build_oracle(force=False):
+    """Compile fm_oracle.c with plain IEEE double semantics (no fused contractions)."""
+    out = lib_path()
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+        return out
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
+                           "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, out)
+    return out
+
+
+def _lib():
+    global _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        lib = C.CDLL(build_oracle())
+        vp = C.c_void_p
+        lib.orc_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                   _dp, vp, _dp, vp, C.c_double]
+        lib.orc_create.restype = C.c_int
+        lib.orc_destroy.argtypes = [vp]
+        for name in ("orc_phi", "orc_reg", "orc_cost"):
+            getattr(lib, name).argtypes = [vp, _dp]
+            getattr(lib, name).restype = C.c_double
+        for name in ("orc_grad", "orc_grad_phi", "orc_curv"):
+            getattr(lib, name).argtypes = [vp, _dp, _dp]
+            getattr(lib, name).restype = None
+        lib.orc_init.argtypes = [vp, _dp]
+        lib.orc_num_unknowns.argtypes = [vp]
+        lib.orc_num_unknowns.restype = C.c_long
+        lib.orc_precondition.argtypes = [vp, _dp, _dp, _dp]
+        lib.orc_precondition.restype = C.c_int
+        lib.orc_solve.argtypes = [vp, _dp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp]
+        lib.orc_solve.restype = C.c_int
+        lib.orc_ic0.argtypes = [C.c_int, C.c_int, C.c_int, vp, _dp, C.c_double, _lp, _lp, _dp,
+                                _lp, C.POINTER(C.c_long), C.POINTER(C.c_long)]
+        lib.orc_ic0.restype = C.c_int
+        lib.orc_ic0_solve.argtypes = [C.c_long, _lp, _lp, _dp, _dp, _dp]
+        lib.orc_voxel.argtypes = [C.c_int, C.c_int, _dp, _dp, vp, C.c_double, _dp]
+        lib.orc_voxel.restype = C.c_int
+        lib.orc_voxel_r.argtypes = [C.c_int, C.c_int, _dp, vp, _dp, _dp]
+        lib.orc_voxel_r.restype = C.c_int
+        _LIB = lib
+        return lib
+
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128).view(np.float64)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+class Oracle:
+    """FP64 oracle bound to one volume.
+
+    y: complex [L][N_c][nz][ny][nx]; smap: complex [N_c][nz][ny][nx] or None (s = 1);
+    te: [L]; mask: uint8 [nz][ny][nx] or None; beta: Eq. 5 weight.  Field maps are
+    float64 arrays of the grid's shape.
+    """
+
+    def __init__(self, y, smap, te, mask, beta):
+        lib = _lib()
+        y = np.asarray(y)
+        L, nc, nz, ny, nx = y.shape
+        self.shape = (nz, ny, nx)
+        self.nc, self.L = nc, L
+        self.beta = float(beta)
+        self.te = np.ascontiguousarray(te, dtype=np.float64)
+        self._y = _c128(y)
+        self._s = _c128(smap) if smap is not None else None
+        self._mask = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+        self.mask = (np.ones(self.shape, np.uint8) if mask is None else self._mask.reshape(self.shape))
+        h = C.c_void_p()
+        st = lib.orc_create(C.byref(h), nx, ny, nz, nc, L, self._y.reshape(-1), _ptr(self._s),
+                            self.te, _ptr(self._mask), self.beta)
+        if st != ORC_OK:
+            raise RuntimeError(f"orc_create failed: {st}")
+        self._h = h
+        self._lib = lib
+
+    @classmethod
+    def from_volume(cls, vol):
+        return cls(vol.y, vol.smap, vol.te, vol.mask, vol.beta)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.orc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _w(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        assert w.size == int(np.prod(self.shape))
+        return w.reshape(-1)
+
+    def phi(self, w):
+        return self._lib.orc_phi(self._h, self._w(w))
+
+    def reg(self, w):
+        return self._lib.orc_reg(self._h, self._w(w))
+
+    def cost(self, w):
+        return self._lib.orc_cost(self._h, self._w(w))
+
+    def _vec(self, fn, w):
+        out = np.zeros(int(np.prod(self.shape)), np.float64)
+        getattr(self._lib, fn)(self._h, self._w(w), out)
+        return out.reshape(self.shape)
+
+    def grad(self, w):
+        return self._vec("orc_grad", w)
+
+    def grad_phi(self, w):
+        return self._vec("orc_grad_phi", w)
+
+    def curv(self, w):
+        return self._vec("orc_curv", w)
+
+    def init(self):
+        out = np.zeros(int(np.prod(self.shape)), np.float64)
+        self._lib.orc_init(self._h, out)
+        return out.reshape(self.shape)
+
+    def precondition(self, d, g):
+        p = np.zeros(int(np.prod(self.shape)), np.float64)
+        st = self._lib.orc_precondition(self._h, self._w(d), self._w(g), p)
+        if st != ORC_OK:
+            raise RuntimeError(f"orc_precondition failed: {st}")
+        return p.reshape(self.shape)
+
+    def solve(self, w0=None, niter=10, nls=5, precond=0, inner=False):
+        """Run the NCG-MLS solve; returns dict(w, cost, alpha, mu[, inner])."""
+        w = np.zeros(int(np.prod(self.shape)), np.float64) if w0 is None else self._w(w0).copy()
+        cost = np.zeros(niter + 1)
+        alpha = np.zeros(max(niter, 1))
+        mu = np.zeros(max(niter, 1))
+        inn = np.zeros(max(niter * nls, 1)) if inner else None
+        st = self._lib.orc_solve(self._h, w, 1 if w0 is None else 0, niter, nls, precond,
+                                 _ptr(cost), _ptr(alpha), _ptr(mu), _ptr(inn))
+        if st != ORC_OK:
+            raise RuntimeError(f"orc_solve failed: {st}")
+        out = dict(w=w.reshape(self.shape), cost=cost, alpha=alpha[:niter], mu=mu[:niter])
+        if inner:
+            out["inner"] = inn[: niter * nls].reshape(niter, nls)
+        return out
+
+
+def ic0_factor(shape, mask, d, beta):
+    """Generic IC(0) of H = diag(d) + beta C'C on the mask voxels (natural order).
+
+    Returns (colptr, rowidx, val, umap): the factor L in compressed-column form over the
+    n unknowns (diagonal first in each column) and the voxel index of each unknown.
+    """
+    lib = _lib()
+    nz, ny, nx = shape
+    nv = nx * ny * nz
+    d = np.ascontiguousarray(d, dtype=np.float64).reshape(-1)
+    m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+    colptr = np.zeros(nv + 1, np.int64)
+    rowidx = np.zeros(4 * nv, np.int64)
+    val = np.zeros(4 * nv, np.float64)
+    umap = np.zeros(nv, np.int64)
+    n, nnz = C.c_long(), C.c_long()
+    st = lib.orc_ic0(nx, ny, nz, _ptr(m), d, float(beta), colptr, rowidx, val, umap, C.byref(n),
+                     C.byref(nnz))
+    if st != ORC_OK:
+        raise RuntimeError(f"orc_ic0 failed: {st}")
+    n, nnz = n.value, nnz.value
+    return colptr[: n + 1].copy(), rowidx[:nnz].copy(), val[:nnz].copy(), umap[:n].copy()
+
+
+def ic0_solve(colptr, rowidx, val, b):
+    lib = _lib()
+    n = colptr.size - 1
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n, np.float64)
+    lib.orc_ic0_solve(n, np.ascontiguousarray(colptr), np.ascontiguousarray(rowidx),
+                      np.ascontiguousarray(val), b, x)
+    return x
+
+
+def voxel_terms(te, y_vox, s_vox, w):
+    """(phi_j, dphi_j, d_j) of one voxel from raw data y_vox [L][N_c], s_vox [N_c] or None."""
+    lib = _lib()
+    y_vox = np.asarray(y_vox)
+    L, nc = y_vox.shape
+    out = np.zeros(3, np.float64)
+    sv = _c128(s_vox) if s_vox is not None else None
+    st = lib.orc_voxel(nc, L, np.ascontiguousarray(te, np.float64), _c128(y_vox).reshape(-1),
+                       _ptr(sv), float(w), out)
+    if st != ORC_OK:
+        raise RuntimeError(f"orc_voxel failed: {st}")
+    return out
+
+
+def voxel_r(y_vox, s_vox):
+    """|r| and angle(r) of Eq. 3 for one voxel, shaped [N_c][N_c][L][L] (c, d, m, n)."""
+    lib = _lib()
+    y_vox = np.asarray(y_vox)
+    L, nc = y_vox.shape
+    T = nc * nc * L * L
+    ra, rg = np.zeros(T), np.zeros(T)
+    sv = _c128(s_vox) if s_vox is not None else None
+    lib.orc_voxel_r(nc, L, _c128(y_vox).reshape(-1), _ptr(sv), ra, rg)
+    return ra.reshape(nc, nc, L, L), rg.reshape(nc, nc, L, L)
