@@ -1,0 +1,464 @@
+#!/usr/bin/env python3
+"""Throughput of the IC(0)-preconditioned NCG-MLS field-map solve on GB300.
+
+One step = the whole hot path over one synthetic acquisition: fm_set_data (the
+Algorithm box's precompute and the Eq. 6 initial map) followed by fm_solve with the
+workload's outer-iteration count.  Metric: voxel-NCG-iterations per second =
+N_v(grid) x N_outer / step time, summed over ranks.
+
+Default workload: 256 x 256 x 128 voxels, 8 coils, 3 echoes (0/2/10 ms), beta = 2^-3,
+100 outer iterations, 5 line-search steps, IC(0) preconditioner, FP32 voxel arithmetic
+with FP64 reductions and pivots.  Inputs are seeded synthetic volumes (synth/) standing in
+for the paper's datasets; each step streams 2.1 GB of inputs, far more than the 129 MB L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: one process per GPU under torch.distributed.run; each rank solves its own
+independent volume (weak scaling, no collective on the data path); the step time is
+the maximum over ranks.  --impl reference times the FP64 CPU oracle on the host cores
+(rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# ncu DRAM bytes per launch of the roofline kernel, scaled to the full workload (see
+# profiles/); None when the kernel changed since the counters were taken.
+NCU_TRAFFIC_BYTES = {}
+
+WORKLOADS = {
+    "full": dict(desc="256x256x128 voxels, 8 coils, 3 echoes (0/2/10 ms), SNR 15 dB, beta=2^-3, "
+                      "100 NCG iterations, N_ls=5, IC(0)", niter=100),
+    "small": dict(desc="64x64x16 voxels, 1 coil, 3 echoes (0/2/10 ms), SNR 20 dB, beta=2^-3, "
+                       "50 NCG iterations, N_ls=5, IC(0)", niter=50),
+    "medium": dict(desc="128x128x64 voxels, 8 coils, 3 echoes (0/2/10 ms), SNR 20 dB, beta=2^-3, "
+                        "100 NCG iterations, N_ls=5, IC(0)", niter=100),
+}
+CPU_SAMPLE = (32, 32, 16)  # oracle sample: centred sub-volume of the same acquisition
+
+
+def make_workload(name, seed_offset=0):
+    from synth import diff_config, full_config, small_config
+    if name == "full":
+        return full_config(seed=1002 + seed_offset)
+    if name == "medium":
+        return diff_config(seed=1005 + seed_offset)
+    return small_config(seed=1001 + seed_offset)
+
+
+def sub_volume(vol, size):
+    """Centred sub-block of a volume (same data, mask and coils) for oracle sampling."""
+    from synth import Volume
+    sx, sy, sz = size
+    x0, y0, z0 = (vol.nx - sx) // 2, (vol.ny - sy) // 2, (vol.nz - sz) // 2
+    sl = (slice(z0, z0 + sz), slice(y0, y0 + sy), slice(x0, x0 + sx))
+    return Volume(y=np.ascontiguousarray(vol.y[(slice(None), slice(None)) + sl]),
+                  smap=None if vol.smap is None else np.ascontiguousarray(vol.smap[(slice(None),) + sl]),
+                  mask=np.ascontiguousarray(vol.mask[sl]), te=vol.te, omega_true=vol.omega_true[sl],
+                  beta=vol.beta, name=f"{vol.name}_sub{sx}x{sy}x{sz}")
+
+
+# ------------------------------------------------------------------ flop / byte model
+
+def data_eval_flops(nc, L, literal):
+    """Algorithmic FP32 flops of one voxel's data-term evaluation (gradient + curvature).
+
+    Per echo pair: phase (2), half-angle sine/cosine (20), gradient/cost terms (6).  Literal
+    curvature per (pair, c, d): phase difference (1), wrap to [-pi, pi] (4), u^2 (1),
+    degree-8 polynomial in u^2 for sin(u)/u (16), amplitude multiply-accumulate (2) = 24;
+    plus 2 per (pair, d) for the rotated phase and 2 per (pair, c) for the outer sum."""
+    P = L * (L - 1) // 2
+    per_pair = 28
+    if literal:
+        per_pair += nc * nc * 24 + 4 * nc
+    else:
+        per_pair += 24
+    return P * per_pair
+
+
+def data_eval_bytes(nc, L, literal, ts=4):
+    P = L * (L - 1) // 2
+    b = P * 2 * ts + 1 + 2 * ts  # pair polar, mask bits, w and z
+    if literal:
+        b += L * nc * 2 * ts
+    return b
+
+
+def peak_numbers(sm_max_mhz, nsm):
+    peaks = {}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        mp = json.load(open(path))
+        peaks["hbm_gbs"] = float(mp["hbm_gbs"])
+        peaks["hbm_src"] = "of measured"
+    else:
+        peaks["hbm_gbs"] = 6800.0
+        peaks["hbm_src"] = "of fallback"
+    # FP32 CUDA-core peak: 128 FP32 lanes per SM, one FMA (2 flops) per lane per clock
+    peaks["fp32_tflops"] = 2 * 128 * nsm * sm_max_mhz * 1e6 / 1e12
+    return peaks
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(gpu_index), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in out.splitlines():
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ distributed
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ oracle (CPU baseline / reference arm)
+
+def oracle_sample(vol, iters):
+    """Time the FP64 oracle, single-threaded, on a centred sub-volume; returns (seconds, units)."""
+    from oracle import Oracle
+    sub = sub_volume(vol, CPU_SAMPLE)
+    t0 = time.perf_counter()
+    o = Oracle.from_volume(sub)
+    o.solve(niter=iters, nls=5)
+    dt = time.perf_counter() - t0
+    o.close()
+    return dt, sub.nvox * iters
+
+
+def cpu_desc():
+    model = ""
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part", "processor\t")) and "model name" in ln.lower():
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return model or os.uname().machine
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    vol = make_workload(args.workload)
+    sample = (f"FP64 C oracle, 1 thread, 1 NCG-MLS-IC(0) iteration (N_ls=5) per step on the centred "
+              f"{CPU_SAMPLE[0]}x{CPU_SAMPLE[1]}x{CPU_SAMPLE[2]} sub-volume of the workload ({vol.ncoil} coils), "
+              f"host {cpu_desc()}, nproc {os.cpu_count()}")
+    for _ in range(args.warmup):
+        oracle_sample(vol, 1)
+    times, units = [], 0
+    for _ in range(args.steps):
+        dt, u = oracle_sample(vol, 1)
+        times.append(dt)
+        units = u
+    t = sum(times) / len(times)
+    value = units / t
+    line = {"metric": "voxel-NCG-iters/s", "value": value, "unit": "voxel-iter/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOADS[args.workload]["desc"], "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "voxel-iter/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "voxel-iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ main arm
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_2005_08661_gb300 import FieldMap, build as fm_build
+    fm_build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    vol = make_workload(args.workload, seed_offset=rank)
+    niter = args.niter or WORKLOADS[args.workload]["niter"]
+    prec = args.precision
+    cd = torch.complex64 if prec == "fp32" else torch.complex128
+    rd = torch.float32 if prec == "fp32" else torch.float64
+    y_h = torch.from_numpy(vol.y).to(cd).pin_memory()
+    s_h = torch.from_numpy(vol.smap).to(cd).pin_memory() if vol.smap is not None else None
+    m_h = torch.from_numpy(vol.mask).pin_memory()
+    stream = torch.cuda.Stream(dev)
+    y_d = torch.empty_like(y_h, device=dev)
+    s_d = torch.empty_like(s_h, device=dev) if s_h is not None else None
+    m_d = torch.empty_like(m_h, device=dev)
+    with torch.cuda.stream(stream):
+        y_d.copy_(y_h)
+        if s_d is not None:
+            s_d.copy_(s_h)
+        m_d.copy_(m_h)
+    stream.synchronize()
+    nv = vol.nvox
+    nmask = int(vol.mask.sum())
+    fm = FieldMap(vol.nx, vol.ny, vol.nz, ncoil=vol.ncoil, necho=vol.necho, precision=prec, device=local,
+                  stream=stream)
+    fm.set_profiling(True)
+    w = torch.empty(vol.mask.shape, dtype=rd, device=dev)
+    w_h = torch.empty(vol.mask.shape, dtype=rd).pin_memory()
+
+    def step():
+        fm.set_data(y_d, s_d, vol.te, m_d, vol.beta)
+        fm.solve_into(w, True, niter)
+
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clk = clocks.stop()
+    t_step = e0.elapsed_time(e1) / 1000.0 / args.steps
+    kt = fm.kernel_times()
+    t_step = max_over_ranks(t_step, world, dev)
+    value = world * nv * niter / t_step
+
+    # end to end: host buffers in, field map out, through the same calls
+    h2d = y_h.numel() * y_h.element_size() + m_h.numel() + (s_h.numel() * s_h.element_size() if s_h is not None else 0)
+    d2h = w.numel() * w.element_size()
+    e2e = None
+    if not args.no_e2e:
+        def step_e2e():
+            with torch.cuda.stream(stream):
+                y_d.copy_(y_h, non_blocking=True)
+                if s_d is not None:
+                    s_d.copy_(s_h, non_blocking=True)
+                m_d.copy_(m_h, non_blocking=True)
+            fm.set_data(y_d, s_d, vol.te, m_d, vol.beta)
+            fm.solve_into(w, True, niter)
+            with torch.cuda.stream(stream):
+                w_h.copy_(w, non_blocking=True)
+        step_e2e()
+        stream.synchronize()
+        barrier(world)
+        e0.record(stream)
+        for _ in range(max(1, args.steps)):
+            step_e2e()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        t_e2e = max_over_ranks(e0.elapsed_time(e1) / 1000.0 / max(1, args.steps), world, dev)
+        e2e = {"value": world * nv * niter / t_e2e, "unit": "voxel-iter/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000 * t_e2e}
+
+    # roofline of the kernel with the largest share of the outer iteration
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peaks = peak_numbers(sm_max, nsm)
+    per_iter = {k: v[0] for k, v in kt.items() if v[1] > 0}
+    dom = max(per_iter, key=per_iter.get) if per_iter else None
+    literal = vol.ncoil > 1
+    roof = None
+    if dom is not None:
+        ms = per_iter[dom]
+        evals = {"grad": 1, "ls": 4}.get(dom, 0)
+        if evals and literal:
+            flops = evals * nmask * data_eval_flops(vol.ncoil, vol.necho, True)
+            ach = flops / (ms * 1e-3) / 1e12
+            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
+                    "frac": ach / peaks["fp32_tflops"], "peak_src": "derived: 2 flops x 128 FP32 lanes x "
+                    f"{nsm} SMs x {sm_max:.0f} MHz", "ms_per_launch": ms,
+                    "algorithmic_flops_per_launch": flops,
+                    "traffic": NCU_TRAFFIC_BYTES.get(dom)}
+        else:
+            ts = 4 if prec == "fp32" else 8
+            if evals:
+                byts = evals * (nmask * data_eval_bytes(vol.ncoil, vol.necho, literal, ts) + nv)
+            elif dom == "ic_fwd":
+                byts = nv * (1 + 2 * ts + 2 * ts)
+            elif dom == "ic_bwd":
+                byts = nv * (1 + 2 * ts + 3 * ts)
+            else:
+                byts = nv * (1 + 7 * ts)
+            ach = byts / (ms * 1e-3) / 1e9
+            roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm_gbs"], "peak_src": peaks["hbm_src"], "ms_per_launch": ms,
+                    "algorithmic_bytes_per_launch": byts, "traffic": NCU_TRAFFIC_BYTES.get(dom)}
+    kernels = {k: {"ms_per_launch": v[0], "share_of_iteration": (v[0] / sum(per_iter.values()) if per_iter else None)}
+               for k, v in kt.items() if v[1] > 0}
+
+    # time to the oracle's final cost on the small workload (stored by tests/golden/make_golden.py)
+    ttc = None
+    if rank == 0 and not args.no_ttc:
+        ttc = time_to_oracle_cost(prec, stream)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, units = oracle_sample(vol, 4)
+        cpu = {"value": units / dt, "unit": "voxel-iter/s", "cores": 1, "kind": "oracle",
+               "sample": f"FP64 C oracle, 1 thread, 4 NCG-MLS-IC(0) iterations (N_ls=5) on the centred "
+                         f"{CPU_SAMPLE[0]}x{CPU_SAMPLE[1]}x{CPU_SAMPLE[2]} sub-volume of the workload "
+                         f"({vol.ncoil} coils), {dt:.1f} s, host {cpu_desc()}, nproc {os.cpu_count()}"}
+
+    launches = args.steps * (1 + (5 if vol.ncoil >= 1 else 0) * niter + 1)
+    line = {"metric": "voxel-NCG-iters/s", "value": value, "unit": "voxel-iter/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload]["desc"], "voxels": nv, "mask_voxels": nmask,
+                       "niter": niter, "nls": 5, "precision": ("fp32 voxel arithmetic, fp64 reductions and IC "
+                                                               "pivots" if prec == "fp32" else "fp64"),
+                       "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (2.1 GB streamed per step)",
+                       "masked_voxel_iters_per_s": world * nmask * niter / t_step},
+            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "kernels": kernels, "clocks": clk,
+            "cpu_baseline": cpu, "time_to_oracle_cost": ttc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    fm.close()
+    return 0
+
+
+def time_to_oracle_cost(prec, stream):
+    """FP32/FP64 solve of the 64x64x16 workload: seconds until the cost first falls to the
+    FP64 oracle's 50-iteration cost x (1 + 1e-6)."""
+    import torch
+    from paper_2005_08661_gb300 import FieldMap
+    path = os.path.join(ROOT, "tests", "golden", "small_oracle_cost.json")
+    if not os.path.exists(path):
+        return None
+    gold = json.load(open(path))
+    target = gold["final_cost"] * (1 + 1e-6)
+    vol = make_workload("small")
+    cd = torch.complex64 if prec == "fp32" else torch.complex128
+    dev = torch.device("cuda", torch.cuda.current_device())
+    y = torch.from_numpy(vol.y).to(dev).to(cd)
+    m = torch.from_numpy(vol.mask).to(dev)
+    fm = FieldMap(vol.nx, vol.ny, vol.nz, 1, 3, precision=prec, stream=stream)
+    fm.set_data(y, None, vol.te, m, vol.beta)
+    nmax = gold["niter"]
+    _, cost = fm.solve(niter=nmax)
+    hit = [i for i, c in enumerate(cost) if c <= target]
+    if not hit:
+        fm.close()
+        return {"reached": False, "target": target, "final_cost": float(cost[-1])}
+    i_star = hit[0]
+    w = fm.empty()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        fm.set_data(y, None, vol.te, m, vol.beta)
+        fm.solve_into(w, True, i_star)
+    ts = []
+    for _ in range(5):
+        e0.record(stream)
+        fm.set_data(y, None, vol.te, m, vol.beta)
+        fm.solve_into(w, True, i_star)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1000.0)
+    fm.close()
+    return {"workload": WORKLOADS["small"]["desc"], "precision": prec, "iterations": i_star,
+            "seconds": statistics.median(ts), "oracle_cost": gold["final_cost"], "target_rel": 1e-6}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="full")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--niter", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ttc", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if (args.impl == "ours" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    try:
+        if args.impl == "reference":
+            return run_reference(args, world, rank)
+        return run_ours(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,211 @@
+/*
+ * fm.h -- C ABI of the GB300 regularised field-map estimator.
+ *
+ * Method: Lin & Fessler, "Efficient Regularized Field Map Estimation in 3D MRI"
+ * (arXiv 2005.08661).  Given multi-echo (optionally multi-coil) images y_clj, coil
+ * maps s_cj and echo times t_l (Sec. II, Eq. 1), it minimises
+ *     Psi(w) = Phi(w) + beta/2 ||C w||^2                                   (Eq. 5)
+ *     Phi(w) = sum_j sum_{m,n} sum_{c,d} |r_cdmnj| (1 - cos(angle r_cdmnj + w_j (t_m - t_n)))
+ *                                                                          (Eq. 2, r: Eq. 3)
+ * with C the 3-D first-order finite differences between 6-neighbours inside the
+ * support mask, by preconditioned Polak-Ribiere nonlinear CG with the monotonic
+ * line search (Algorithm box, Sec. III-C, Eq. 13-16) and an IC(0) preconditioner
+ * of H = diag(d) + beta C'C (Sec. III-B, Eq. 9-12).
+ *
+ * Conventions shared by every entry point
+ *   - Volumes are nx * ny * nz voxels, x fastest: voxel (x, y, z) is element
+ *     x + nx * (y + ny * z).  Arrays are dense and contiguous; no strides.
+ *   - Precision (fm_opts.precision): FM_FP32 -> voxel arrays are float and images
+ *     are complex64 (interleaved float re, im); FM_FP64 -> double / complex128.
+ *     In FM_FP32 mode every global sum (cost, dot products, line-search sums) and
+ *     the IC(0) pivot recurrence are carried in double.
+ *   - "device" pointers are CUDA device (or managed) memory of the context's
+ *     device; "host" pointers are ordinary host memory.  Caller arrays are
+ *     borrowed for the duration of the call only; the context owns everything it
+ *     allocates.
+ *   - Work is enqueued on the context's stream.  Calls that return a host value
+ *     (cost, cost history) synchronise that stream; the others return once the
+ *     work is enqueued, except that every call reports errors found by earlier
+ *     kernels of the same context at its next synchronisation.
+ *   - Field maps are in radians per unit of the echo times (echo times in ms ->
+ *     rad/ms).  Voxels outside the mask are not unknowns and are returned as 0.
+ *   - Every function returns FM_OK (0) or a negative FM_ERR_* code and never
+ *     aborts.  After an error the context can still be destroyed; FM_ERR_CUDA
+ *     after a sticky device fault leaves the context unusable.
+ */
+#ifndef FM_H
+#define FM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FM_API __attribute__((visibility("default")))
+#else
+#define FM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FM_OK 0
+#define FM_ERR_ARG (-1)       /* invalid argument (null pointer, bad size, bad option) */
+#define FM_ERR_STATE (-2)     /* call order wrong, e.g. a solve before fm_set_data */
+#define FM_ERR_CUDA (-3)      /* a CUDA runtime call failed */
+#define FM_ERR_NOT_PD (-4)    /* an IC(0) pivot was <= 0 (H not positive definite) */
+#define FM_ERR_TIMEOUT (-5)   /* a device-side wait exceeded fm_opts.spin_limit polls */
+#define FM_ERR_NONFINITE (-6) /* a global reduction (cost, dot, step) was not finite */
+#define FM_ERR_OOM (-7)       /* device or host allocation failed */
+
+#define FM_FP64 0
+#define FM_FP32 1
+
+#define FM_PC_IC0 0  /* IC(0) of H in natural order (Sec. III-B, Eq. 12): the paper's L_0 */
+#define FM_PC_DIAG 1 /* diag(H): the paper's NCG-MLS-D comparison (Sec. IV) */
+#define FM_PC_NONE 2 /* identity: the paper's NCG-MLS comparison (Sec. IV) */
+
+#define FM_CURV_LITERAL 0  /* d_j summed over every (c, d, m, n) term (Eq. 10) */
+#define FM_CURV_COMBINED 1 /* d_j from the coil-combined pair weights (labelled variant) */
+
+#define FM_MAX_ECHO 8
+#define FM_MAX_COIL 32
+
+typedef struct fm_ctx fm_ctx; /* opaque, owned by the library */
+
+typedef struct fm_opts {
+    int precision;       /* FM_FP32 (default) or FM_FP64 */
+    int nls;             /* monotonic line-search steps per outer iteration (N_i), >= 1; default 5 */
+    int precond;         /* FM_PC_IC0 (default) | FM_PC_DIAG | FM_PC_NONE */
+    int curvature;       /* FM_CURV_LITERAL (default) | FM_CURV_COMBINED */
+    long long spin_limit;/* polls (about 1 us each) before a device-side wait gives up with
+                            FM_ERR_TIMEOUT; default 1<<21 (about 2 s) */
+    int use_graph;       /* 1: replay the outer iteration as a captured CUDA graph (default 1) */
+} fm_opts;
+
+/* Fill *opts with the defaults listed above.  opts must not be NULL. */
+FM_API void fm_default_opts(fm_opts *opts);
+
+/*
+ * Create a context for one nx*ny*nz volume with ncoil coils and necho echoes
+ * (Sec. II: N_c >= 1, L >= 2).  opts may be NULL (defaults).  device is a CUDA
+ * device ordinal; cuda_stream is a cudaStream_t of that device or NULL for the
+ * legacy default stream.  Allocates every device buffer the solver needs (about
+ * (8 N_c L + 80) bytes per voxel in FM_FP32 mode).  *out is NULL on failure.
+ * Errors: FM_ERR_ARG (sizes < 1, ncoil > FM_MAX_COIL, necho outside 2..FM_MAX_ECHO,
+ * bad option), FM_ERR_CUDA, FM_ERR_OOM.
+ */
+FM_API int fm_create(fm_ctx **out, int nx, int ny, int nz, int ncoil, int necho, const fm_opts *opts,
+              int device, void *cuda_stream);
+
+/*
+ * Load one acquisition and precompute everything the iterations share (Algorithm
+ * box: "precompute r_cdmnj by Eq. 3 and t_m - t_n"; Sec. III-B).
+ *   y     device, complex [necho][ncoil][nz][ny][nx] (complex64 in FM_FP32 mode,
+ *         complex128 in FM_FP64 mode), the images y_clj of Eq. 1.
+ *   smap  device, complex [ncoil][nz][ny][nx] of the same type, the coil maps
+ *         s_cj; NULL means s = 1 and requires ncoil == 1 (Sec. II).
+ *   te    host double [necho], the echo times t_l (any unit; w is rad per unit).
+ *   mask  device uint8 [nz][ny][nx], nonzero = unknown voxel (Sec. IV mask); NULL
+ *         means every voxel is an unknown.
+ *   beta  the regularisation weight of Eq. 5, >= 0.
+ * Also computes the Eq. 6 initial field map used by fm_solve(init_from_data = 1).
+ * Errors: FM_ERR_ARG (NULL y, NULL smap with ncoil > 1, beta < 0 or not finite,
+ * non-finite te, t_2 == t_1), FM_ERR_CUDA.
+ */
+FM_API int fm_set_data(fm_ctx *ctx, const void *y, const void *smap, const double *te,
+                const uint8_t *mask, double beta);
+
+/*
+ * Write the Eq. 6 initial field map to omega (device [nz][ny][nx], float or double by
+ * precision).  Requires fm_set_data.
+ */
+FM_API int fm_init_omega(fm_ctx *ctx, void *omega);
+
+/*
+ * Evaluate at the field map omega (device [nz][ny][nx]):
+ *   cost  host double*, nullable: Psi(omega) (Eq. 5 with Phi of Eq. 2, literal
+ *         constant terms included), accumulated in double;
+ *   grad  device [nz][ny][nx], nullable: grad Psi (Eq. 8, with the first power of
+ *         t_m - t_n, the derivative of Eq. 2);
+ *   curv  device [nz][ny][nx], nullable: d_j of Eq. 10-11 (Huber curvature,
+ *         angle wrapped into [-pi, pi]).
+ * Outside the mask grad and curv are 0 and omega is ignored.  A non-NULL cost
+ * synchronises the stream.  Errors: FM_ERR_STATE before fm_set_data, FM_ERR_ARG.
+ */
+FM_API int fm_cost_grad(fm_ctx *ctx, const void *omega, double *cost, void *grad, void *curv);
+
+/*
+ * Form H = diag(d(omega)) + beta C'C (Eq. 9) and its IC(0) factor (Eq. 12), natural
+ * x-fastest order, zero fill-in: L = (Pi + E) Pi^{-1/2} with E the strict lower
+ * triangle of H and pivots pi_j = H_jj - sum_k E_jk^2 / pi_k.  The factor is kept
+ * in the context for fm_ic_apply.  inv_pivot (device [nz][ny][nx] of the voxel type,
+ * nullable) receives 1/pi_j (0 outside the mask).  Pivots are computed in double.
+ * Errors: FM_ERR_STATE, FM_ERR_NOT_PD (some pivot <= 0; reported at the next
+ * synchronising call), FM_ERR_TIMEOUT.
+ */
+FM_API int fm_ic_factor(fm_ctx *ctx, const void *omega, void *inv_pivot);
+
+/*
+ * p = (L L')^{-1} g with the factor of the last fm_ic_factor (Sec. III-B, the
+ * "precondition" step of the Algorithm box): a forward then a back substitution.
+ * g, p: device [nz][ny][nx], distinct.  Errors: FM_ERR_STATE if no factor exists.
+ */
+FM_API int fm_ic_apply(fm_ctx *ctx, const void *g, void *p);
+
+/*
+ * Run niter outer iterations of preconditioned NCG with the monotonic line search
+ * (Algorithm box; Eq. 13-16) from omega (device [nz][ny][nx], in/out), or from the
+ * Eq. 6 initial map when init_from_data != 0.  Per iteration: g = grad Psi, p =
+ * P^{-1} g (IC(0) by default), mu = 0 at i = 0 else (g_i - g_{i-1})'p_i /
+ * (g_{i-1}'p_{i-1}), z = -p + mu z, then nls steps alpha <- alpha - f'(alpha) /
+ * (sum_j z_j^2 d_j(w + alpha z) + beta ||C z||^2) from alpha = 0, and w <- w + alpha z.
+ * cost_hist (host double [niter + 1], nullable) receives Psi(w^0) .. Psi(w^niter);
+ * a non-NULL cost_hist synchronises the stream.  Errors: FM_ERR_STATE, FM_ERR_ARG
+ * (niter < 0), FM_ERR_NOT_PD, FM_ERR_TIMEOUT, FM_ERR_NONFINITE.
+ */
+FM_API int fm_solve(fm_ctx *ctx, void *omega, int init_from_data, int niter, double *cost_hist);
+
+/*
+ * Copy the step sizes alpha^(N_i) and Polak-Ribiere factors mu of the last fm_solve
+ * (host double [n] each, nullable; n <= that solve's niter).  Synchronises.
+ */
+FM_API int fm_get_history(fm_ctx *ctx, double *alpha_hist, double *mu_hist, int n);
+
+/* Kernel classes timed by fm_kernel_times. */
+#define FM_K_GRAD 0   /* data term + stencil gradient pass (fused update of the previous step) */
+#define FM_K_IC_FWD 1 /* IC(0) pivots + forward substitution wavefront */
+#define FM_K_IC_BWD 2 /* back substitution wavefront + g'p, g_prev'p */
+#define FM_K_DIR 3    /* Polak-Ribiere direction + first line-search step */
+#define FM_K_LS 4     /* persistent line search (steps 2..N_i) */
+#define FM_NKERNEL 5
+
+/*
+ * Turn per-kernel timing on or off (off by default).  While on, fm_solve brackets
+ * every kernel of the outer iteration with CUDA events on the context's stream (they
+ * are part of the captured graph), which adds a few microseconds per iteration.
+ */
+FM_API int fm_set_profiling(fm_ctx *ctx, int on);
+
+/*
+ * Average device duration in milliseconds of each kernel class over the most recent
+ * profiled outer iterations (the last graph replay, or the last iteration without a
+ * graph): avg_ms and count are host arrays of FM_NKERNEL entries (count: launches
+ * averaged, 0 if that class did not run).  Synchronises.
+ */
+FM_API int fm_kernel_times(fm_ctx *ctx, double *avg_ms, int *count);
+
+/* Release every resource of ctx.  NULL-safe.  Returns FM_OK. */
+FM_API int fm_destroy(fm_ctx *ctx);
+
+/* Static description of a status code. */
+FM_API const char *fm_strerror(int status);
+
+/* Description of the last error on ctx ("" if none); valid until the next call on ctx. */
+FM_API const char *fm_last_error(const fm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FM_H */

@@ -1,0 +1,267 @@
+// fm_internal.h -- device-side building blocks shared by the CUDA translation units of
+// the field-map library (not part of the public ABI; see include/fm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fm.h"
+
+namespace fm {
+
+constexpr int kMaxPairs = FM_MAX_ECHO * (FM_MAX_ECHO - 1) / 2;
+
+// Neighbour-bit byte stored per voxel: bit 0 = voxel is an unknown (inside the mask);
+// bits 1..6 = its (-x, +x, -y, +y, -z, +z) neighbour exists and is an unknown too.
+enum : uint8_t { NB_IN = 1, NB_XM = 2, NB_XP = 4, NB_YM = 8, NB_YP = 16, NB_ZM = 32, NB_ZP = 64 };
+
+// Device scalar slots (double) kept per context.
+enum Scal {
+    S_ALPHA = 0,   // current step alpha (line search state; applied by the next gradient pass)
+    S_GP,          // g_i' p_i
+    S_GPREVP,      // g_{i-1}' p_i
+    S_GP_PREV,     // g_{i-1}' p_{i-1}
+    S_MU,          // mu_i
+    S_CZ2,         // ||C z||^2
+    S_CZW,         // (C z)'(C w)
+    S_ZG,          // z' g
+    S_ZZD,         // sum z^2 d
+    S_COST,        // Psi(w)
+    S_K,           // omega-independent part of Phi (Eq. 2 terms with m = n, and the coil-combination remainder)
+    S_NSCAL
+};
+
+// Integer device state.
+enum IState { I_ERR = 0, I_ITER, I_DONE0, I_DONE1, I_BAR_COUNT, I_BAR_GEN, I_NISTATE };
+
+struct Pairs {
+    int P;                  // number of echo pairs m < n
+    int m[kMaxPairs], n[kMaxPairs];
+    double dt[kMaxPairs];   // t_m - t_n
+};
+
+template <typename T> struct V2;
+template <> struct V2<float> { using t = float2; };
+template <> struct V2<double> { using t = double2; };
+
+// ------------------------------------------------------------------ reductions
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic block sum of Q doubles (fixed shuffle tree); result valid in thread 0.
+template <int Q>
+__device__ __forceinline__ void block_sum(double (&v)[Q], double* sbuf /* >= 32*Q */) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) v[q] = warp_sum(v[q]);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < Q; ++q) sbuf[q * 32 + wid] = v[q];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            double x = lane < nw ? sbuf[q * 32 + lane] : 0.0;
+            v[q] = warp_sum(x);
+        }
+    }
+    __syncthreads();
+}
+
+// Sum partials[q * n + i] over i in a fixed order with the whole block; result in thread 0.
+template <int Q>
+__device__ __forceinline__ void sum_partials(const double* partials, int n, double (&out)[Q],
+                                             double* sbuf) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        double a = 0.0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) a += __ldcg(partials + (size_t)q * n + i);
+        out[q] = a;
+    }
+    block_sum<Q>(out, sbuf);
+}
+
+// Each block stores its Q partial sums; the last block to finish reduces all of them in
+// block order and returns true in every thread of that block (out valid in thread 0).
+template <int Q>
+__device__ __forceinline__ bool last_block_reduce(double (&v)[Q], double* partials, unsigned* done,
+                                                  double (&out)[Q], double* sbuf) {
+    __shared__ bool s_last;
+    block_sum<Q>(v, sbuf);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) partials[(size_t)q * gridDim.x + blockIdx.x] = v[q];
+        __threadfence();
+        unsigned prev = atomicAdd(done, 1u);
+        s_last = (prev == gridDim.x - 1);
+        if (s_last) __threadfence();
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    sum_partials<Q>(partials, gridDim.x, out, sbuf);
+    if (threadIdx.x == 0) *done = 0u;
+    return true;
+}
+
+// ------------------------------------------------------------------ memory ordering
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Spin until *flag == want, at most `limit` polls.  Returns false on timeout.
+__device__ __forceinline__ bool spin_until(const int* flag, int want, long long limit) {
+    long long n = 0;
+    unsigned ns = 32;
+    while (ld_acquire(flag) != want) {
+        if (++n > limit) return false;
+        __nanosleep(ns);
+        if (ns < 1024) ns <<= 1;  // backoff capped near 1 us per poll
+    }
+    return true;
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).  Bounded: on
+// timeout it records FM_ERR_TIMEOUT and returns false (the caller then exits).
+__device__ __forceinline__ bool grid_barrier(int* istate, long long limit) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int* count = istate + I_BAR_COUNT;
+        int* gen = istate + I_BAR_GEN;
+        int g0 = ld_acquire(gen);
+        __threadfence();
+        int arrived = atomicAdd(count, 1);
+        int ok = 1;
+        if (arrived == (int)gridDim.x - 1) {
+            atomicExch(count, 0);
+            __threadfence();
+            st_release(gen, g0 + 1);
+        } else {
+            long long n = 0;
+            unsigned ns = 32;
+            while (ld_acquire(gen) == g0) {
+                if (++n > limit) { ok = 0; break; }
+                __nanosleep(ns);
+                if (ns < 256) ns <<= 1;
+            }
+        }
+        __threadfence();
+        if (!ok) atomicCAS(istate + I_ERR, 0, FM_ERR_TIMEOUT);
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ void set_err(int* istate, int code) { atomicCAS(istate + I_ERR, 0, code); }
+
+// ------------------------------------------------------------------ launch wrappers
+
+struct Geo {
+    int nx, ny, nz;
+    long long nv;
+};
+
+struct SetupArgs {
+    Geo geo;
+    int nc, L;
+    Pairs pr;
+    const void* y;      // complex [L][nc][nv]
+    const void* smap;   // complex [nc][nv] or null
+    const uint8_t* mask;// [nv] or null
+    double te0, te1;    // first two echo times (Eq. 6)
+    void* pairs;        // T2 [P][nv]: (|R_mn|, angle R_mn)
+    void* coils;        // T2 [L][nc][nv]: (|W_cm|, angle W_cm), or null
+    uint8_t* nb;        // [nv]
+    void* w0;           // T [nv] initial field map (Eq. 6)
+    double* partials;   // [grid]
+    double* scal;
+    int* istate;
+};
+
+struct DataArgs {
+    Geo geo;
+    int nc, L;
+    Pairs pr;
+    double beta;
+    int literal;           // literal curvature over coils (nc > 1 and FM_CURV_LITERAL)
+    const void* pairs;
+    const void* coils;
+    const uint8_t* nb;
+    // gradient pass
+    const void* w_in;      // T [nv]
+    const void* z;         // T [nv] direction applied with scal[S_ALPHA] (update fused), or null
+    void* w_out;           // T [nv]
+    void* g;               // T [nv]
+    void* d;               // T [nv]
+    // direction pass
+    const void* p;         // T [nv]
+    const void* z_old;     // T [nv]
+    void* z_new;           // T [nv]
+    const void* g_prev;    // T [nv]
+    double* scal;
+    double* partials;      // [4][grid] (+ [2][2][grid] for the line search)
+    double* cost_hist;     // device [niter+1] or null
+    double* alpha_hist;
+    double* mu_hist;
+    int* istate;
+    int nls;
+    long long spin_limit;
+    int first_iter;        // direction pass: 1 -> mu = 0
+};
+
+struct IcArgs {
+    Geo geo;
+    int ntx, nty, ntz, ntiles;
+    const int* order;      // [ntiles] tiles in a dependency-respecting order
+    int* flags;            // [ntiles] 0/1
+    int* ticket;           // claim counter
+    int* done;             // finished-tile counter
+    double beta;
+    const uint8_t* nb;
+    // forward
+    const void* d;         // T [nv] (compute pivots) or null
+    const void* ip_in;     // T [nv] stored inverse pivots (apply only) or null
+    const void* g;         // T [nv] right-hand side
+    void* v;               // T [nv] forward result
+    void* ip_out;          // T [nv] inverse pivots (compute mode)
+    double* face;          // FP64 pivot faces per tile
+    // backward
+    const void* vin;       // T [nv]
+    const void* ipb;       // T [nv]
+    void* p;               // T [nv]
+    const void* gdot;      // T [nv] or null: g for g'p
+    const void* gpdot;     // T [nv] or null: g_prev for g_prev'p
+    double* tile_part;     // [2][ntiles]
+    double* scal;
+    int* istate;
+    long long spin_limit;
+};
+
+template <typename T> cudaError_t launch_setup(const SetupArgs& a, int grid, cudaStream_t s);
+template <typename T> cudaError_t launch_grad(const DataArgs& a, int grid, cudaStream_t s);
+template <typename T> cudaError_t launch_dir(const DataArgs& a, int grid, cudaStream_t s);
+template <typename T> cudaError_t launch_ls(const DataArgs& a, int grid, cudaStream_t s);
+template <typename T> cudaError_t launch_pdiag(const DataArgs& a, int mode, int grid, cudaStream_t s);
+template <typename T> int ls_max_blocks_per_sm(const DataArgs& a);
+template <typename T> cudaError_t launch_ic_fwd(const IcArgs& a, int grid, cudaStream_t s);
+template <typename T> cudaError_t launch_ic_bwd(const IcArgs& a, int grid, cudaStream_t s);
+template <typename T> int ic_tz();
+template <typename T> size_t ic_smem_bytes();
+template <typename T> int ic_max_blocks_per_sm();
+
+constexpr int kThreads = 256;     // data-term / stencil kernels
+constexpr int kTileX = 32, kTileY = 32;
+
+}  // namespace fm

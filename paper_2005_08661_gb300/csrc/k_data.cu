@@ -1,0 +1,403 @@
+// k_data.cu -- the per-voxel data term (cost, gradient, Huber curvature), fused with the
+// regulariser stencil, the NCG direction update and the monotonic line search.
+//
+// Per voxel j at field value w (Sec. II-III; see k_setup.cu for the pair factorisation):
+//   Phi_j  = K_j + 4 sum_{m<n} |R_mn| sin^2(theta_mn / 2),  theta_mn = angle R_mn + w (t_m - t_n)
+//   dPhi_j = 2 sum_{m<n} (t_m - t_n) |R_mn| sin(theta_mn)                         (Eq. 8)
+//   d_j    = 2 sum_{m<n} (t_m - t_n)^2 sum_{c,d} |W_cm||W_dn| sinc(wrap(angle W_dn - angle W_cm
+//                                                              + w (t_m - t_n)))  (Eq. 10-11)
+// (the (n, m, d, c) term of every sum equals its (m, n, c, d) mirror, hence the factor 2),
+// or, in the labelled FM_CURV_COMBINED variant and always for one coil,
+//   d_j    = 2 sum_{m<n} (t_m - t_n)^2 |R_mn| sinc(wrap(theta_mn)).
+// wrap() removes the nearest multiple of 2 pi ("mod pi" of Eq. 11 read as the wrap into
+// [-pi, pi], Huber's optimal curvature for 1 - cos).
+//
+// FP32 mode evaluates the voxel arithmetic in float and sums in double; FP64 mode is double
+// throughout.  Global sums are block partials reduced in a fixed order (bitwise
+// reproducible).
+#include <cooperative_groups.h>
+
+#include "fm_internal.h"
+
+namespace fm {
+
+// ------------------------------------------------------------------ scalar helpers
+
+__device__ __forceinline__ float wrap_angle(float t) {
+    // nearest integer of t / (2 pi) by the 1.5 * 2^23 rounding constant (|t| < 2^21 here)
+    const float k = fmaf(t, 0.159154943091895336f, 12582912.0f) - 12582912.0f;
+    return fmaf(k, -6.28318530717958648f, t);
+}
+__device__ __forceinline__ double wrap_angle(double t) {
+    return t - 6.283185307179586476925286766559 * rint(t * 0.15915494309189533576888376337251);
+}
+
+// sin(u)/u on [-pi, pi]: Taylor series sum_k (-u^2)^k / (2k+1)! through k = 8 (truncation
+// error below pi^18 / 19! ~ 7e-9, under float resolution).
+__device__ __forceinline__ float sinc_wrapped(float u) {
+    const float v = u * u;
+    float p = 2.81145725434552076e-15f;     //  1/17!
+    p = fmaf(p, v, -7.64716373181981647e-13f);  // -1/15!
+    p = fmaf(p, v, 1.60590438368216146e-10f);   //  1/13!
+    p = fmaf(p, v, -2.50521083854417188e-08f);  // -1/11!
+    p = fmaf(p, v, 2.75573192239858907e-06f);   //  1/9!
+    p = fmaf(p, v, -1.98412698412698413e-04f);  // -1/7!
+    p = fmaf(p, v, 8.33333333333333333e-03f);   //  1/5!
+    p = fmaf(p, v, -1.66666666666666667e-01f);  // -1/3!
+    return fmaf(p, v, 1.0f);
+}
+__device__ __forceinline__ double sinc_wrapped(double u) { return u == 0.0 ? 1.0 : sin(u) / u; }
+
+__device__ __forceinline__ void sin_cos(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sin_cos(double x, double* s, double* c) { sincos(x, s, c); }
+
+// ------------------------------------------------------------------ per-voxel data term
+
+// Adds the data-term pieces of voxel j at field value w.  NC > 0: literal curvature over
+// NC coils held in registers; NC == 0: literal curvature, runtime coil count; NC == 1:
+// coil-combined curvature (exact for one coil).
+template <typename T, int NC, bool COST, bool CURV>
+__device__ __forceinline__ void eval_voxel(const DataArgs& a, long long j, T w, T& cost, T& grad,
+                                           T& curv) {
+    using T2 = typename V2<T>::t;
+    const long long nv = a.geo.nv;
+    const T2* pairs = (const T2*)a.pairs;
+    const T2* coils = (const T2*)a.coils;
+    T c_acc = 0, g_acc = 0, d_acc = 0;
+    for (int p = 0; p < a.pr.P; ++p) {
+        const T dt = (T)a.pr.dt[p];
+        const T2 R = pairs[(size_t)p * nv + j];
+        const T th = R.y + w * dt;
+        T s, c;
+        sin_cos(th * T(0.5), &s, &c);
+        if (COST) c_acc += R.x * (s * s);
+        g_acc += dt * R.x * (s * c);
+        if (CURV) {
+            if (NC == 1) {
+                d_acc += dt * dt * R.x * sinc_wrapped(wrap_angle(th));
+            } else if (NC > 1) {
+                const int m = a.pr.m[p], n = a.pr.n[p];
+                T psi[NC > 1 ? NC : 1], ad[NC > 1 ? NC : 1];
+#pragma unroll
+                for (int dd = 0; dd < NC; ++dd) {
+                    const T2 q = coils[((size_t)n * NC + dd) * nv + j];
+                    ad[dd] = q.x;
+                    psi[dd] = q.y + w * dt;
+                }
+                T inner = 0;
+#pragma unroll
+                for (int cc = 0; cc < NC; ++cc) {
+                    const T2 q = coils[((size_t)m * NC + cc) * nv + j];
+                    T acc = 0;
+#pragma unroll
+                    for (int dd = 0; dd < NC; ++dd) acc += ad[dd] * sinc_wrapped(wrap_angle(psi[dd] - q.y));
+                    inner += q.x * acc;
+                }
+                d_acc += dt * dt * inner;
+            } else {
+                const int m = a.pr.m[p], n = a.pr.n[p], nc = a.nc;
+                T inner = 0;
+                for (int cc = 0; cc < nc; ++cc) {
+                    const T2 q = coils[((size_t)m * nc + cc) * nv + j];
+                    T acc = 0;
+                    for (int dd = 0; dd < nc; ++dd) {
+                        const T2 r = coils[((size_t)n * nc + dd) * nv + j];
+                        acc += r.x * sinc_wrapped(wrap_angle(r.y + w * dt - q.y));
+                    }
+                    inner += q.x * acc;
+                }
+                d_acc += dt * dt * inner;
+            }
+        }
+    }
+    cost = T(4) * c_acc;
+    grad = T(4) * g_acc;
+    curv = T(2) * d_acc;
+}
+
+// ------------------------------------------------------------------ gradient pass
+
+// w_out = w_in + alpha z (the previous iteration's update, Algorithm box), then at w_out:
+// g = grad Psi (Eq. 8), d (Eq. 10), and Psi (Eq. 5) reduced to scal[S_COST] / cost_hist.
+template <typename T, int NC>
+__global__ void __launch_bounds__(kThreads) k_grad(DataArgs a) {
+    __shared__ double sbuf[32];
+    const long long nv = a.geo.nv;
+    const int nx = a.geo.nx;
+    const long long nxy = (long long)nx * a.geo.ny;
+    const T* w_in = (const T*)a.w_in;
+    const T* z = (const T*)a.z;
+    T* w_out = (T*)a.w_out;
+    T* g = (T*)a.g;
+    T* d = (T*)a.d;
+    const T alpha = z ? (T)a.scal[S_ALPHA] : T(0);
+    const T beta = (T)a.beta;
+    auto upd = [&](long long k) -> T { return z ? w_in[k] + alpha * z[k] : w_in[k]; };
+    double acc = 0.0;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nv;
+         j += (long long)gridDim.x * blockDim.x) {
+        const uint8_t b = a.nb[j];
+        if (!(b & NB_IN)) {
+            w_out[j] = T(0);
+            if (g) g[j] = T(0);
+            if (d) d[j] = T(0);
+            continue;
+        }
+        const T wj = upd(j);
+        w_out[j] = wj;
+        T lap = 0, reg = 0;
+        if (b & NB_XM) lap += wj - upd(j - 1);
+        if (b & NB_YM) lap += wj - upd(j - nx);
+        if (b & NB_ZM) lap += wj - upd(j - nxy);
+        if (b & NB_XP) { const T e = wj - upd(j + 1); lap += e; reg += e * e; }
+        if (b & NB_YP) { const T e = wj - upd(j + nx); lap += e; reg += e * e; }
+        if (b & NB_ZP) { const T e = wj - upd(j + nxy); lap += e; reg += e * e; }
+        T cst, gr, cu;
+        eval_voxel<T, NC, true, true>(a, j, wj, cst, gr, cu);
+        if (g) g[j] = gr + beta * lap;
+        if (d) d[j] = cu;
+        acc += (double)cst + 0.5 * a.beta * (double)reg;
+    }
+    double v[1] = {acc}, out[1];
+    if (last_block_reduce<1>(v, a.partials, (unsigned*)(a.istate + I_DONE0), out, sbuf)) {
+        if (threadIdx.x == 0) {
+            const double total = a.scal[S_K] + out[0];
+            a.scal[S_COST] = total;
+            if (a.cost_hist) a.cost_hist[a.istate[I_ITER]] = total;
+            if (!isfinite(total)) set_err(a.istate, FM_ERR_NONFINITE);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ direction pass
+
+// mu (Polak-Ribiere with the preconditioned gradients), z = -p + mu z, and the sums the
+// first line-search step needs: ||C z||^2, (C z)'(C w), z'g, sum z^2 d (Sec. III-C).
+// The first step alpha_1 = -z'g / (sum z^2 d + beta ||C z||^2) is taken here.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_dir(DataArgs a) {
+    __shared__ double sbuf[4 * 32];
+    const long long nv = a.geo.nv;
+    const int nx = a.geo.nx;
+    const long long nxy = (long long)nx * a.geo.ny;
+    const int it = a.istate[I_ITER];
+    double mu = 0.0;
+    if (it > 0) {
+        const double den = a.scal[S_GP_PREV];
+        mu = den != 0.0 ? (a.scal[S_GP] - a.scal[S_GPREVP]) / den : 0.0;
+    }
+    const T muT = (T)mu;
+    const T* p = (const T*)a.p;
+    const T* zo = (const T*)a.z_old;
+    T* zn = (T*)a.z_new;
+    const T* w = (const T*)a.w_out;
+    const T* g = (const T*)a.g;
+    const T* d = (const T*)a.d;
+    auto zval = [&](long long k) -> T { return -p[k] + muT * zo[k]; };
+    double s_cz2 = 0.0, s_czw = 0.0, s_zg = 0.0, s_zzd = 0.0;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nv;
+         j += (long long)gridDim.x * blockDim.x) {
+        const uint8_t b = a.nb[j];
+        if (!(b & NB_IN)) { zn[j] = T(0); continue; }
+        const T zj = zval(j), wj = w[j];
+        zn[j] = zj;
+        T cz2 = 0, czw = 0;
+        if (b & NB_XP) { const T e = zj - zval(j + 1), f = wj - w[j + 1]; cz2 += e * e; czw += e * f; }
+        if (b & NB_YP) { const T e = zj - zval(j + nx), f = wj - w[j + nx]; cz2 += e * e; czw += e * f; }
+        if (b & NB_ZP) { const T e = zj - zval(j + nxy), f = wj - w[j + nxy]; cz2 += e * e; czw += e * f; }
+        s_cz2 += (double)cz2;
+        s_czw += (double)czw;
+        s_zg += (double)(zj * g[j]);
+        s_zzd += (double)(zj * zj * d[j]);
+    }
+    double v[4] = {s_cz2, s_czw, s_zg, s_zzd}, out[4];
+    if (last_block_reduce<4>(v, a.partials, (unsigned*)(a.istate + I_DONE0), out, sbuf)) {
+        if (threadIdx.x == 0) {
+            a.scal[S_CZ2] = out[0];
+            a.scal[S_CZW] = out[1];
+            a.scal[S_ZG] = out[2];
+            a.scal[S_ZZD] = out[3];
+            a.scal[S_MU] = mu;
+            a.scal[S_GP_PREV] = a.scal[S_GP];
+            const double den = out[3] + a.beta * out[0];
+            const double alpha = den != 0.0 ? -out[2] / den : 0.0;
+            a.scal[S_ALPHA] = alpha;
+            if (a.mu_hist) a.mu_hist[it] = mu;
+            if (!isfinite(alpha) || !isfinite(mu) || !isfinite(den)) set_err(a.istate, FM_ERR_NONFINITE);
+            if (a.nls <= 1) {
+                if (a.alpha_hist) a.alpha_hist[it] = alpha;
+                a.istate[I_ITER] = it + 1;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ line search
+
+// Steps k = 1 .. nls-1 of the monotonic line search (Eq. 16) as one persistent cooperative
+// kernel: each step re-evaluates the data term at w + alpha_k z, reduces
+// sum z_j dPhi_j and sum z_j^2 d_j in double (fixed order, every block computes the same
+// total), and updates alpha without leaving the device.
+template <typename T, int NC>
+__global__ void __launch_bounds__(kThreads) k_ls(DataArgs a) {
+    __shared__ double sbuf[2 * 32];
+    __shared__ double s_tot[2];
+    const long long nv = a.geo.nv;
+    const T* w = (const T*)a.w_out;
+    const T* z = (const T*)a.z_new;
+    const double cz2 = a.scal[S_CZ2], czw = a.scal[S_CZW];
+    const int it = a.istate[I_ITER];
+    double alpha = a.scal[S_ALPHA];
+    const int nb = gridDim.x;
+    for (int k = 1; k < a.nls; ++k) {
+        const T aT = (T)alpha;
+        double s1 = 0.0, s2 = 0.0;
+        for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nv;
+             j += (long long)gridDim.x * blockDim.x) {
+            if (!(a.nb[j] & NB_IN)) continue;
+            const T zj = z[j];
+            if (zj == T(0)) continue;
+            T cst, gr, cu;
+            eval_voxel<T, NC, false, true>(a, j, w[j] + aT * zj, cst, gr, cu);
+            s1 += (double)(zj * gr);
+            s2 += (double)(zj * zj * cu);
+        }
+        double v[2] = {s1, s2};
+        block_sum<2>(v, sbuf);
+        double* part = a.partials + 4 * (size_t)nb + (size_t)(k & 1) * 2 * nb;
+        if (threadIdx.x == 0) {
+            part[blockIdx.x] = v[0];
+            part[nb + blockIdx.x] = v[1];
+        }
+        if (!grid_barrier(a.istate, a.spin_limit)) return;
+        double tot[2];
+        sum_partials<2>(part, nb, tot, sbuf);
+        if (threadIdx.x == 0) { s_tot[0] = tot[0]; s_tot[1] = tot[1]; }
+        __syncthreads();
+        const double fp = s_tot[0] + a.beta * (czw + alpha * cz2);
+        const double den = s_tot[1] + a.beta * cz2;
+        __syncthreads();
+        if (den == 0.0) { alpha = 0.0; break; }
+        alpha = alpha - fp / den;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.scal[S_ALPHA] = alpha;
+        if (a.alpha_hist) a.alpha_hist[it] = alpha;
+        if (!isfinite(alpha)) set_err(a.istate, FM_ERR_NONFINITE);
+        a.istate[I_ITER] = it + 1;
+    }
+}
+
+// ------------------------------------------------------------------ diagonal / no preconditioner
+
+// p = g / H_jj (mode 1, the NCG-MLS-D comparison) or p = g (mode 2), with g'p and g_prev'p.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_pdiag(DataArgs a, int mode) {
+    __shared__ double sbuf[2 * 32];
+    const long long nv = a.geo.nv;
+    const T* g = (const T*)a.g;
+    const T* gp = (const T*)a.g_prev;
+    const T* d = (const T*)a.d;
+    T* p = (T*)a.z_new;  // output slot
+    double s_gp = 0.0, s_gpp = 0.0;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nv;
+         j += (long long)gridDim.x * blockDim.x) {
+        const uint8_t b = a.nb[j];
+        if (!(b & NB_IN)) { p[j] = T(0); continue; }
+        T pj = g[j];
+        if (mode == 1) {
+            const int cnt = __popc((unsigned)(b >> 1) & 0x3fu);
+            const T h = d[j] + (T)a.beta * (T)cnt;
+            if (!(h > T(0))) set_err(a.istate, FM_ERR_NOT_PD);
+            pj = h > T(0) ? pj / h : T(0);
+        }
+        p[j] = pj;
+        s_gp += (double)(g[j] * pj);
+        s_gpp += (double)(gp[j] * pj);
+    }
+    double v[2] = {s_gp, s_gpp}, out[2];
+    if (last_block_reduce<2>(v, a.partials, (unsigned*)(a.istate + I_DONE0), out, sbuf)) {
+        if (threadIdx.x == 0) {
+            a.scal[S_GP] = out[0];
+            a.scal[S_GPREVP] = out[1];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+
+template <typename T, int NC>
+static cudaError_t grad_nc(const DataArgs& a, int grid, cudaStream_t s) {
+    k_grad<T, NC><<<grid, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_grad(const DataArgs& a, int grid, cudaStream_t s) {
+    if (!a.literal) return grad_nc<T, 1>(a, grid, s);
+    switch (a.nc) {
+        case 2: return grad_nc<T, 2>(a, grid, s);
+        case 4: return grad_nc<T, 4>(a, grid, s);
+        case 8: return grad_nc<T, 8>(a, grid, s);
+        default: return grad_nc<T, 0>(a, grid, s);
+    }
+}
+
+template <typename T>
+cudaError_t launch_dir(const DataArgs& a, int grid, cudaStream_t s) {
+    k_dir<T><<<grid, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, int NC>
+static cudaError_t ls_nc(const DataArgs& a, int grid, cudaStream_t s) {
+    DataArgs copy = a;
+    void* args[] = {&copy};
+    return cudaLaunchCooperativeKernel((const void*)k_ls<T, NC>, dim3(grid), dim3(kThreads), args, 0, s);
+}
+
+template <typename T>
+cudaError_t launch_ls(const DataArgs& a, int grid, cudaStream_t s) {
+    if (!a.literal) return ls_nc<T, 1>(a, grid, s);
+    switch (a.nc) {
+        case 2: return ls_nc<T, 2>(a, grid, s);
+        case 4: return ls_nc<T, 4>(a, grid, s);
+        case 8: return ls_nc<T, 8>(a, grid, s);
+        default: return ls_nc<T, 0>(a, grid, s);
+    }
+}
+
+template <typename T, int NC>
+static int ls_occ() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ls<T, NC>, kThreads, 0) != cudaSuccess) return 0;
+    return n;
+}
+
+template <typename T>
+int ls_max_blocks_per_sm(const DataArgs& a) {
+    if (!a.literal) return ls_occ<T, 1>();
+    switch (a.nc) {
+        case 2: return ls_occ<T, 2>();
+        case 4: return ls_occ<T, 4>();
+        case 8: return ls_occ<T, 8>();
+        default: return ls_occ<T, 0>();
+    }
+}
+
+template <typename T>
+cudaError_t launch_pdiag(const DataArgs& a, int mode, int grid, cudaStream_t s) {
+    k_pdiag<T><<<grid, kThreads, 0, s>>>(a, mode);
+    return cudaGetLastError();
+}
+
+#define FM_INST(T)                                                                  \
+    template cudaError_t launch_grad<T>(const DataArgs&, int, cudaStream_t);        \
+    template cudaError_t launch_dir<T>(const DataArgs&, int, cudaStream_t);         \
+    template cudaError_t launch_ls<T>(const DataArgs&, int, cudaStream_t);          \
+    template cudaError_t launch_pdiag<T>(const DataArgs&, int, int, cudaStream_t);  \
+    template int ls_max_blocks_per_sm<T>(const DataArgs&);
+FM_INST(float)
+FM_INST(double)
+
+}  // namespace fm

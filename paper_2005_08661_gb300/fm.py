@@ -1,0 +1,233 @@
+"""Thin ctypes binding of libfm.so (include/fm.h).
+
+Argument marshalling only: every step of the estimator runs in the library's CUDA
+kernels.  PyTorch supplies device memory and the stream.  The library must have been
+built (``paper_2005_08661_gb300.build.build()``); there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+FM_OK, FM_ERR_ARG, FM_ERR_STATE, FM_ERR_CUDA = 0, -1, -2, -3
+FM_ERR_NOT_PD, FM_ERR_TIMEOUT, FM_ERR_NONFINITE, FM_ERR_OOM = -4, -5, -6, -7
+FM_FP64, FM_FP32 = 0, 1
+FM_PC_IC0, FM_PC_DIAG, FM_PC_NONE = 0, 1, 2
+FM_CURV_LITERAL, FM_CURV_COMBINED = 0, 1
+
+_PREC = {"fp32": FM_FP32, "fp64": FM_FP64}
+_PC = {"ic0": FM_PC_IC0, "diag": FM_PC_DIAG, "none": FM_PC_NONE}
+_CURV = {"literal": FM_CURV_LITERAL, "combined": FM_CURV_COMBINED}
+
+
+class FmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class FmOpts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("nls", C.c_int), ("precond", C.c_int), ("curvature", C.c_int),
+                ("spin_limit", C.c_longlong), ("use_graph", C.c_int)]
+
+
+_LIB = None
+_LOCK = threading.Lock()
+
+EXPORTS = ["fm_default_opts", "fm_create", "fm_set_data", "fm_init_omega", "fm_cost_grad", "fm_ic_factor",
+           "fm_ic_apply", "fm_solve", "fm_get_history", "fm_set_profiling", "fm_kernel_times", "fm_destroy",
+           "fm_strerror", "fm_last_error"]
+KERNELS = ["grad", "ic_fwd", "ic_bwd", "dir", "ls"]
+
+
+def lib_path():
+    return _build.lib_path()
+
+
+def load_library(path=None):
+    """Load libfm.so and declare its signatures.  Raises if the library is missing."""
+    global _LIB
+    with _LOCK:
+        if _LIB is not None and path is None:
+            return _LIB
+        p = path or lib_path()
+        if not os.path.exists(p):
+            raise RuntimeError(f"CUDA library not built: {p} is missing (run __graft_entry__.build() "
+                               "or python -m paper_2005_08661_gb300.build)")
+        lib = C.CDLL(p)
+        vp, i, d = C.c_void_p, C.c_int, C.c_double
+        lib.fm_default_opts.argtypes = [C.POINTER(FmOpts)]
+        lib.fm_default_opts.restype = None
+        lib.fm_create.argtypes = [C.POINTER(vp), i, i, i, i, i, C.POINTER(FmOpts), i, vp]
+        lib.fm_set_data.argtypes = [vp, vp, vp, C.POINTER(d), vp, d]
+        lib.fm_init_omega.argtypes = [vp, vp]
+        lib.fm_cost_grad.argtypes = [vp, vp, C.POINTER(d), vp, vp]
+        lib.fm_ic_factor.argtypes = [vp, vp, vp]
+        lib.fm_ic_apply.argtypes = [vp, vp, vp]
+        lib.fm_solve.argtypes = [vp, vp, i, i, C.POINTER(d)]
+        lib.fm_get_history.argtypes = [vp, C.POINTER(d), C.POINTER(d), i]
+        lib.fm_set_profiling.argtypes = [vp, i]
+        lib.fm_kernel_times.argtypes = [vp, C.POINTER(d), C.POINTER(i)]
+        lib.fm_destroy.argtypes = [vp]
+        for fn in ("fm_create", "fm_set_data", "fm_init_omega", "fm_cost_grad", "fm_ic_factor", "fm_ic_apply",
+                   "fm_solve", "fm_get_history", "fm_set_profiling", "fm_kernel_times", "fm_destroy"):
+            getattr(lib, fn).restype = C.c_int
+        lib.fm_strerror.argtypes = [i]
+        lib.fm_strerror.restype = C.c_char_p
+        lib.fm_last_error.argtypes = [vp]
+        lib.fm_last_error.restype = C.c_char_p
+        if path is None:
+            _LIB = lib
+        return lib
+
+
+def _dptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class FieldMap:
+    """One volume's field-map estimator on one GPU (a handle on an fm_ctx)."""
+
+    def __init__(self, nx, ny, nz, ncoil=1, necho=3, precision="fp32", nls=5, precond="ic0",
+                 curvature="literal", spin_limit=1 << 21, use_graph=True, device=None, stream=None):
+        import torch
+        self._torch = torch
+        self.lib = load_library()
+        self.shape = (nz, ny, nx)
+        self.ncoil, self.necho = ncoil, necho
+        self.precision = precision
+        self.rdtype = torch.float32 if precision == "fp32" else torch.float64
+        self.cdtype = torch.complex64 if precision == "fp32" else torch.complex128
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.device = dev
+        if stream is None:
+            stream = torch.cuda.current_stream(dev)
+        self.stream = stream
+        o = FmOpts()
+        self.lib.fm_default_opts(C.byref(o))
+        o.precision = _PREC[precision]
+        o.nls = int(nls)
+        o.precond = _PC[precond]
+        o.curvature = _CURV[curvature]
+        o.spin_limit = int(spin_limit)
+        o.use_graph = 1 if use_graph else 0
+        self.opts = o
+        h = C.c_void_p()
+        sp = stream.cuda_stream if stream is not None else 0
+        st = self.lib.fm_create(C.byref(h), nx, ny, nz, ncoil, necho, C.byref(o), dev.index,
+                                C.c_void_p(sp) if sp else None)
+        if st != FM_OK:
+            raise FmError(st, f"fm_create: {self.lib.fm_strerror(st).decode()}")
+        self._h = h
+
+    # ---------------------------------------------------------------- helpers
+    def _check(self, st, what):
+        if st != FM_OK:
+            msg = self.lib.fm_last_error(self._h).decode() if self._h else ""
+            raise FmError(st, f"{what}: {self.lib.fm_strerror(st).decode()}: {msg}")
+
+    def _vec(self, x, name):
+        t = self._torch
+        if not (isinstance(x, t.Tensor) and x.is_cuda and x.dtype == self.rdtype and x.is_contiguous()
+                and x.numel() == int(np.prod(self.shape))):
+            raise TypeError(f"{name} must be a contiguous {self.rdtype} CUDA tensor with {int(np.prod(self.shape))} "
+                            "elements")
+        return x
+
+    def empty(self):
+        return self._torch.empty(self.shape, dtype=self.rdtype, device=self.device)
+
+    # ---------------------------------------------------------------- API
+    def set_data(self, y, smap, te, mask=None, beta=2.0 ** -3):
+        t = self._torch
+        nz, ny, nx = self.shape
+        if not (y.is_cuda and y.dtype == self.cdtype and y.is_contiguous()
+                and tuple(y.shape) == (self.necho, self.ncoil, nz, ny, nx)):
+            raise TypeError(f"y must be a contiguous {self.cdtype} CUDA tensor of shape "
+                            f"{(self.necho, self.ncoil, nz, ny, nx)}")
+        if smap is not None and not (smap.is_cuda and smap.dtype == self.cdtype and smap.is_contiguous()
+                                     and tuple(smap.shape) == (self.ncoil, nz, ny, nx)):
+            raise TypeError("smap must match y's dtype with shape (ncoil, nz, ny, nx)")
+        if mask is not None and not (mask.is_cuda and mask.dtype == t.uint8 and mask.is_contiguous()
+                                     and tuple(mask.shape) == self.shape):
+            raise TypeError("mask must be a contiguous uint8 CUDA tensor of the volume's shape")
+        te_arr = (C.c_double * self.necho)(*[float(v) for v in te])
+        self._check(self.lib.fm_set_data(self._h, _dptr(y), _dptr(smap), te_arr, _dptr(mask), float(beta)),
+                    "fm_set_data")
+
+    def init_omega(self):
+        out = self.empty()
+        self._check(self.lib.fm_init_omega(self._h, _dptr(out)), "fm_init_omega")
+        return out
+
+    def cost_grad(self, omega, want_cost=True, want_grad=True, want_curv=True):
+        self._vec(omega, "omega")
+        g = self.empty() if want_grad else None
+        d = self.empty() if want_curv else None
+        cost = C.c_double(0.0)
+        self._check(self.lib.fm_cost_grad(self._h, _dptr(omega), C.byref(cost) if want_cost else None,
+                                          _dptr(g), _dptr(d)), "fm_cost_grad")
+        return (cost.value if want_cost else None), g, d
+
+    def ic_factor(self, omega, want_pivots=True):
+        self._vec(omega, "omega")
+        ip = self.empty() if want_pivots else None
+        self._check(self.lib.fm_ic_factor(self._h, _dptr(omega), _dptr(ip)), "fm_ic_factor")
+        return ip
+
+    def ic_apply(self, g, out=None):
+        self._vec(g, "g")
+        p = self.empty() if out is None else self._vec(out, "out")
+        self._check(self.lib.fm_ic_apply(self._h, _dptr(g), _dptr(p)), "fm_ic_apply")
+        return p
+
+    def solve(self, omega=None, niter=50, want_history=True):
+        """Run niter NCG-MLS iterations; omega=None starts from Eq. 6.  Returns (omega, costs)."""
+        init = omega is None
+        w = self.empty() if init else self._vec(omega, "omega").clone()
+        hist = (C.c_double * (niter + 1))() if want_history else None
+        self._check(self.lib.fm_solve(self._h, _dptr(w), 1 if init else 0, int(niter), hist), "fm_solve")
+        return w, (np.array(hist[:], dtype=np.float64) if want_history else None)
+
+    def solve_into(self, omega, init, niter, hist=None):
+        """Lowest-overhead form: omega is updated in place; hist is a ctypes double array or None."""
+        self._check(self.lib.fm_solve(self._h, _dptr(omega), 1 if init else 0, int(niter), hist), "fm_solve")
+        return omega
+
+    def history(self, n):
+        a = (C.c_double * max(n, 1))()
+        m = (C.c_double * max(n, 1))()
+        self._check(self.lib.fm_get_history(self._h, a, m, int(n)), "fm_get_history")
+        return np.array(a[:n]), np.array(m[:n])
+
+    def set_profiling(self, on=True):
+        self._check(self.lib.fm_set_profiling(self._h, 1 if on else 0), "fm_set_profiling")
+
+    def kernel_times(self):
+        """{kernel: (average ms, launches averaged)} of the last profiled iterations."""
+        ms = (C.c_double * len(KERNELS))()
+        cnt = (C.c_int * len(KERNELS))()
+        self._check(self.lib.fm_kernel_times(self._h, ms, cnt), "fm_kernel_times")
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNELS)}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.fm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
