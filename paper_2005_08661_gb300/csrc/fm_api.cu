@@ -180,10 +180,10 @@ cudaError_t run_ic(fm_ctx* c, const void* d, const void* g, void* p, const void*
     f.ip_out = c->ip;
     {
         fm_ctx* pc = slot >= 0 ? c : nullptr;
-        if (pc && pc->profiling) cudaEventRecord(pc->ev[slot][FM_K_IC_FWD][0], c->stream);
+        if (pc && pc->profiling) cudaEventRecordWithFlags(pc->ev[slot][FM_K_IC_FWD][0], c->stream, cudaEventRecordExternal);
         e = launch_ic_fwd<T>(f, c->grid_ic, c->stream);
         if (pc && pc->profiling) {
-            cudaEventRecord(pc->ev[slot][FM_K_IC_FWD][1], c->stream);
+            cudaEventRecordWithFlags(pc->ev[slot][FM_K_IC_FWD][1], c->stream, cudaEventRecordExternal);
             pc->ev_rec[slot][FM_K_IC_FWD] = true;
         }
     }
@@ -198,10 +198,10 @@ cudaError_t run_ic(fm_ctx* c, const void* d, const void* g, void* p, const void*
     b.gdot = gdot;
     b.gpdot = gpdot;
     b.tile_part = (gdot || gpdot) ? c->tile_part : nullptr;
-    if (slot >= 0 && c->profiling) cudaEventRecord(c->ev[slot][FM_K_IC_BWD][0], c->stream);
+    if (slot >= 0 && c->profiling) cudaEventRecordWithFlags(c->ev[slot][FM_K_IC_BWD][0], c->stream, cudaEventRecordExternal);
     e = launch_ic_bwd<T>(b, c->grid_ic, c->stream);
     if (slot >= 0 && c->profiling) {
-        cudaEventRecord(c->ev[slot][FM_K_IC_BWD][1], c->stream);
+        cudaEventRecordWithFlags(c->ev[slot][FM_K_IC_BWD][1], c->stream, cudaEventRecordExternal);
         c->ev_rec[slot][FM_K_IC_BWD] = true;
     }
     return e;
@@ -212,11 +212,11 @@ struct Mark {
     fm_ctx* c;
     int cur, k;
     Mark(fm_ctx* c_, int cur_, int k_) : c(c_), cur(cur_), k(k_) {
-        if (c->profiling) cudaEventRecord(c->ev[cur][k][0], c->stream);
+        if (c->profiling) cudaEventRecordWithFlags(c->ev[cur][k][0], c->stream, cudaEventRecordExternal);
     }
     ~Mark() {
         if (c->profiling) {
-            cudaEventRecord(c->ev[cur][k][1], c->stream);
+            cudaEventRecordWithFlags(c->ev[cur][k][1], c->stream, cudaEventRecordExternal);
             c->ev_rec[cur][k] = true;
         }
     }
