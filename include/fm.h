@@ -57,6 +57,7 @@ extern "C" {
 #define FM_ERR_TIMEOUT (-5)   /* a device-side wait exceeded fm_opts.spin_limit polls */
 #define FM_ERR_NONFINITE (-6) /* a global reduction (cost, dot, step) was not finite */
 #define FM_ERR_OOM (-7)       /* device or host allocation failed */
+#define FM_ERR_SIZE (-8)      /* problem larger than a fixed-size buffer of the call allows */
 
 #define FM_FP64 0
 #define FM_FP32 1
@@ -194,6 +195,34 @@ FM_API int fm_set_profiling(fm_ctx *ctx, int on);
  * averaged, 0 if that class did not run).  Synchronises.
  */
 FM_API int fm_kernel_times(fm_ctx *ctx, double *avg_ms, int *count);
+
+/*
+ * fm_cost_grad without a context and without allocating any device memory.  The paper
+ * has no counterpart: this is a deployment convenience for callers that cannot call
+ * cudaMalloc -- for example code that runs while another component captures a CUDA
+ * graph on the device, real-time pipelines that must not allocate after start-up, or
+ * plug-ins whose host runtime owns every device buffer and only passes pointers in.
+ *
+ * It evaluates, at omega, the same cost, gradient and curvature as fm_cost_grad, directly
+ * from the raw inputs (same layouts and types as fm_set_data / fm_cost_grad; opts
+ * supplies precision and curvature, NULL = defaults; beta >= 0).  cost (host) receives
+ * Psi(omega) and synchronises the stream when non-NULL; grad and curv (device) are
+ * nullable.  cuda_stream: a stream of `device`, or NULL for the legacy default stream.
+ *
+ * Scratch: the per-block FP64 partial costs live in one fixed array of about 128 KB
+ * inside the library (a file-scope __device__ variable), which every GPU that loads the
+ * library keeps until the process exits.  Limit: nx*ny*nz <= 67,108,864 voxels
+ * (16,384 blocks of 4,096 voxels); larger volumes return FM_ERR_SIZE before any device
+ * work.  The first call on a device looks up that array's device address (once per
+ * device); make that first call before any stream capture.  Every call reuses the same
+ * array and clears its counter at the start, so calls whose kernels overlap on the GPU
+ * (different streams or threads without ordering) race and must not be issued.
+ * Errors: FM_ERR_ARG, FM_ERR_SIZE, FM_ERR_CUDA.
+ */
+FM_API int fm_cost_grad_noalloc(int nx, int ny, int nz, int ncoil, int necho, const fm_opts *opts,
+                                const void *y, const void *smap, const double *te, const uint8_t *mask,
+                                double beta, const void *omega, double *cost, void *grad, void *curv,
+                                int device, void *cuda_stream);
 
 /* Release every resource of ctx.  NULL-safe.  Returns FM_OK. */
 FM_API int fm_destroy(fm_ctx *ctx);

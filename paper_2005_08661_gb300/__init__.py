@@ -5,7 +5,9 @@ on the phase-wrapping cost of Eq. 5) runs in hand-written sm_103a CUDA kernels b
 the C ABI of include/fm.h; :class:`FieldMap` is a thin ctypes binding of that ABI.
 """
 from .fm import (FieldMap, FmError, FmOpts, load_library, lib_path, EXPORTS, FM_OK, FM_ERR_ARG,
-                 FM_ERR_STATE, FM_ERR_CUDA, FM_ERR_NOT_PD, FM_ERR_TIMEOUT, FM_ERR_NONFINITE, FM_ERR_OOM)
+                 FM_ERR_STATE, FM_ERR_CUDA, FM_ERR_NOT_PD, FM_ERR_TIMEOUT, FM_ERR_NONFINITE, FM_ERR_OOM,
+                 FM_ERR_SIZE)
 
 __all__ = ["FieldMap", "FmError", "FmOpts", "load_library", "lib_path", "EXPORTS", "FM_OK", "FM_ERR_ARG",
-           "FM_ERR_STATE", "FM_ERR_CUDA", "FM_ERR_NOT_PD", "FM_ERR_TIMEOUT", "FM_ERR_NONFINITE", "FM_ERR_OOM"]
+           "FM_ERR_STATE", "FM_ERR_CUDA", "FM_ERR_NOT_PD", "FM_ERR_TIMEOUT", "FM_ERR_NONFINITE", "FM_ERR_OOM",
+           "FM_ERR_SIZE"]

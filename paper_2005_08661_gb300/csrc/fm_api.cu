@@ -344,6 +344,7 @@ const char* fm_strerror(int s) {
         case FM_ERR_TIMEOUT: return "device-side wait timed out";
         case FM_ERR_NONFINITE: return "non-finite reduction";
         case FM_ERR_OOM: return "out of memory";
+        case FM_ERR_SIZE: return "problem exceeds a fixed-size buffer of the call";
         default: return "unknown status";
     }
 }

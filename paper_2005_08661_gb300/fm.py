@@ -16,6 +16,7 @@ from . import build as _build
 
 FM_OK, FM_ERR_ARG, FM_ERR_STATE, FM_ERR_CUDA = 0, -1, -2, -3
 FM_ERR_NOT_PD, FM_ERR_TIMEOUT, FM_ERR_NONFINITE, FM_ERR_OOM = -4, -5, -6, -7
+FM_ERR_SIZE = -8
 FM_FP64, FM_FP32 = 0, 1
 FM_PC_IC0, FM_PC_DIAG, FM_PC_NONE = 0, 1, 2
 FM_CURV_LITERAL, FM_CURV_COMBINED = 0, 1
@@ -41,7 +42,7 @@ _LOCK = threading.Lock()
 
 EXPORTS = ["fm_default_opts", "fm_create", "fm_set_data", "fm_init_omega", "fm_cost_grad", "fm_ic_factor",
            "fm_ic_apply", "fm_solve", "fm_get_history", "fm_set_profiling", "fm_kernel_times", "fm_destroy",
-           "fm_strerror", "fm_last_error"]
+           "fm_strerror", "fm_last_error", "fm_cost_grad_noalloc"]
 KERNELS = ["grad", "ic_fwd", "ic_bwd", "dir", "ls"]
 
 
@@ -77,6 +78,9 @@ def load_library(path=None):
         for fn in ("fm_create", "fm_set_data", "fm_init_omega", "fm_cost_grad", "fm_ic_factor", "fm_ic_apply",
                    "fm_solve", "fm_get_history", "fm_set_profiling", "fm_kernel_times", "fm_destroy"):
             getattr(lib, fn).restype = C.c_int
+        lib.fm_cost_grad_noalloc.argtypes = [i, i, i, i, i, C.POINTER(FmOpts), vp, vp, C.POINTER(d), vp, d, vp,
+                                             C.POINTER(d), vp, vp, i, vp]
+        lib.fm_cost_grad_noalloc.restype = C.c_int
         lib.fm_strerror.argtypes = [i]
         lib.fm_strerror.restype = C.c_char_p
         lib.fm_last_error.argtypes = [vp]
