@@ -28,6 +28,7 @@ struct fm_ctx {
     // device buffers
     void *pairs = nullptr, *coils = nullptr, *w0 = nullptr;
     uint8_t* nb = nullptr;
+    int *vlist = nullptr, *chunk_off = nullptr;
     void *w[2] = {nullptr, nullptr}, *z[2] = {nullptr, nullptr}, *g[2] = {nullptr, nullptr};
     void *d = nullptr, *p = nullptr, *v = nullptr, *ip = nullptr;
     double *scal = nullptr, *partials = nullptr, *face = nullptr, *tile_part = nullptr;
@@ -89,7 +90,7 @@ void free_all(fm_ctx* c) {
         for (auto& b : a)
             for (cudaEvent_t& e : b)
                 if (e) cudaEventDestroy(e);
-    void* bufs[] = {c->pairs, c->coils, c->w0, c->nb, c->w[0], c->w[1], c->z[0], c->z[1], c->g[0],
+    void* bufs[] = {c->pairs, c->coils, c->w0, c->nb, c->vlist, c->chunk_off, c->w[0], c->w[1], c->z[0], c->z[1], c->g[0],
                     c->g[1], c->d, c->p, c->v, c->ip, c->scal, c->partials, c->face, c->tile_part,
                     c->hist_cost, c->hist_alpha, c->hist_mu, c->istate, c->icint, c->order};
     for (void* b : bufs)
@@ -125,6 +126,7 @@ DataArgs base_args(fm_ctx* c) {
     a.pairs = c->pairs;
     a.coils = c->coils;
     a.nb = c->nb;
+    a.vlist = c->vlist;
     a.scal = c->scal;
     a.partials = c->partials;
     a.istate = c->istate;
@@ -281,9 +283,18 @@ int solve_t(fm_ctx* c, void* omega, int init, int niter, double* cost_hist) {
     const size_t vb = (size_t)c->nv * c->ts;
     cudaStream_t s = c->stream;
     FM_CK(cudaMemsetAsync(c->istate + I_ERR, 0, sizeof(int), s), "reset");
-    FM_CK(cudaMemcpyAsync(c->w[0], init ? c->w0 : omega, vb, cudaMemcpyDeviceToDevice, s), "copy omega");
-    FM_CK(cudaMemsetAsync(c->z[0], 0, vb, s), "reset direction");
-    FM_CK(cudaMemsetAsync(c->g[1], 0, vb, s), "reset gradient");
+    // the kernels write mask voxels only: every entry outside the mask starts (and stays) 0
+    if (init) {
+        FM_CK(cudaMemcpyAsync(c->w[0], c->w0, vb, cudaMemcpyDeviceToDevice, s), "copy omega");
+    } else {
+        FM_CK(launch_masked_copy<T>(omega, c->w[0], c->nb, c->nv, c->grid_data, s), "copy omega");
+    }
+    FM_CK(cudaMemsetAsync(c->w[1], 0, vb, s), "reset field map");
+    for (int k = 0; k < 2; ++k) {
+        FM_CK(cudaMemsetAsync(c->z[k], 0, vb, s), "reset direction");
+        FM_CK(cudaMemsetAsync(c->g[k], 0, vb, s), "reset gradient");
+    }
+    FM_CK(cudaMemsetAsync(c->p, 0, vb, s), "reset preconditioned gradient");
     FM_CK(cudaMemsetAsync(c->scal + S_ALPHA, 0, sizeof(double), s), "reset step");
     FM_CK(cudaMemsetAsync(c->scal + S_GP, 0, 4 * sizeof(double), s), "reset dots");
     FM_CK(cudaMemsetAsync(c->istate + I_ITER, 0, sizeof(int), s), "reset counter");
@@ -357,7 +368,7 @@ int fm_create(fm_ctx** out, int nx, int ny, int nz, int ncoil, int necho, const 
     *out = nullptr;
     if (nx < 1 || ny < 1 || nz < 1 || ncoil < 1 || ncoil > FM_MAX_COIL || necho < 2 || necho > FM_MAX_ECHO)
         return FM_ERR_ARG;
-    if ((long long)nx * ny > (1LL << 40) / nz) return FM_ERR_ARG;
+    if ((long long)nx * ny * nz >= (1LL << 31)) return FM_ERR_ARG;  // voxel indices are 32-bit
     fm_opts o;
     fm_default_opts(&o);
     if (opts) o = *opts;
@@ -373,7 +384,6 @@ int fm_create(fm_ctx** out, int nx, int ny, int nz, int ncoil, int necho, const 
     c->device = device;
     c->ts = o.precision == FM_FP64 ? 8 : 4;
     c->literal = (ncoil > 1 && o.curvature == FM_CURV_LITERAL);
-    int rc = FM_OK;
     auto bail = [&](int code) { free_all(c); delete c; return code; };
     if (cuda_stream) {
         c->stream = (cudaStream_t)cuda_stream;
@@ -409,11 +419,14 @@ int fm_create(fm_ctx** out, int nx, int ny, int nz, int ncoil, int necho, const 
     A(&c->pairs, (size_t)P * 2 * vb);
     if (c->literal) A(&c->coils, (size_t)necho * ncoil * 2 * vb);
     A(&c->nb, (size_t)c->nv);
+    const long long nchunks = (c->nv + kChunk - 1) / kChunk;
+    A(&c->vlist, (size_t)c->nv * sizeof(int));
+    A(&c->chunk_off, (size_t)nchunks * sizeof(int));
     A(&c->w0, vb);
     for (int k = 0; k < 2; ++k) { A(&c->w[k], vb); A(&c->z[k], vb); A(&c->g[k], vb); }
     A(&c->d, vb); A(&c->p, vb); A(&c->v, vb); A(&c->ip, vb);
     A(&c->scal, S_NSCAL * sizeof(double));
-    A(&c->partials, 8 * (size_t)std::max(c->grid_data, c->grid_ls) * sizeof(double));
+    A(&c->partials, std::max<size_t>(8 * (size_t)std::max(c->grid_data, c->grid_ls), nchunks) * sizeof(double));
     A(&c->face, (size_t)c->ntiles * (64 * tz + 1024) * sizeof(double));
     A(&c->tile_part, 2 * (size_t)c->ntiles * sizeof(double));
     A(&c->istate, I_NISTATE * sizeof(int));
@@ -434,7 +447,6 @@ int fm_create(fm_ctx** out, int nx, int ny, int nz, int ncoil, int necho, const 
         cudaMemset(c->istate, 0, I_NISTATE * sizeof(int)) != cudaSuccess ||
         cudaMemset(c->nb, 0, (size_t)c->nv) != cudaSuccess)
         return bail(FM_ERR_CUDA);
-    (void)rc;
     *out = c;
     return FM_OK;
 }
@@ -485,11 +497,13 @@ int fm_set_data(fm_ctx* c, const void* y, const void* smap, const double* te, co
     a.coils = c->coils;
     a.nb = c->nb;
     a.w0 = c->w0;
+    a.vlist = c->vlist;
+    a.chunk_off = c->chunk_off;
     a.partials = c->partials;
     a.scal = c->scal;
     a.istate = c->istate;
-    cudaError_t e = c->o.precision == FM_FP64 ? launch_setup<double>(a, c->grid_data, c->stream)
-                                              : launch_setup<float>(a, c->grid_data, c->stream);
+    cudaError_t e = c->o.precision == FM_FP64 ? launch_setup<double>(a, c->stream)
+                                              : launch_setup<float>(a, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "setup kernel");
     c->have_data = true;
     c->have_factor = false;
@@ -512,6 +526,9 @@ int fm_cost_grad(fm_ctx* c, const void* omega, double* cost, void* grad, void* c
     DevGuard guard(c->device);
     void* g = grad ? grad : c->g[0];
     void* d = curv ? curv : c->d;
+    const size_t vb = (size_t)c->nv * c->ts;
+    FM_CK(cudaMemsetAsync(g, 0, vb, c->stream), "clear gradient");  // entries outside the mask stay 0
+    FM_CK(cudaMemsetAsync(d, 0, vb, c->stream), "clear curvature");
     cudaError_t e = c->o.precision == FM_FP64
                         ? run_grad<double>(c, omega, nullptr, c->w[0], g, d, nullptr)
                         : run_grad<float>(c, omega, nullptr, c->w[0], g, d, nullptr);

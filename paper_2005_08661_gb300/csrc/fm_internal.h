@@ -32,7 +32,10 @@ enum Scal {
 };
 
 // Integer device state.
-enum IState { I_ERR = 0, I_ITER, I_DONE0, I_DONE1, I_BAR_COUNT, I_BAR_GEN, I_NISTATE };
+enum IState { I_ERR = 0, I_ITER, I_DONE0, I_DONE1, I_BAR_COUNT, I_BAR_GEN, I_NMASK, I_NISTATE };
+
+// Setup works on chunks of 1024 consecutive voxels (mask compaction keeps voxel order).
+constexpr int kChunk = 1024;
 
 struct Pairs {
     int P;                  // number of echo pairs m < n
@@ -185,7 +188,9 @@ struct SetupArgs {
     void* coils;        // T2 [L][nc][nv]: (|W_cm|, angle W_cm), or null
     uint8_t* nb;        // [nv]
     void* w0;           // T [nv] initial field map (Eq. 6)
-    double* partials;   // [grid]
+    int* vlist;         // [nv] voxel index of each mask voxel, ascending (compact order)
+    int* chunk_off;     // [nchunks] mask voxels before each chunk (exclusive scan)
+    double* partials;   // [nchunks]
     double* scal;
     int* istate;
 };
@@ -196,9 +201,10 @@ struct DataArgs {
     Pairs pr;
     double beta;
     int literal;           // literal curvature over coils (nc > 1 and FM_CURV_LITERAL)
-    const void* pairs;
-    const void* coils;
+    const void* pairs;     // compact order: [P][cap]
+    const void* coils;     // compact order: [L][nc][cap]
     const uint8_t* nb;
+    const int* vlist;      // [cap] voxel index of compact entry k
     // gradient pass
     const void* w_in;      // T [nv]
     const void* z;         // T [nv] direction applied with scal[S_ALPHA] (update fused), or null
@@ -249,7 +255,9 @@ struct IcArgs {
     long long spin_limit;
 };
 
-template <typename T> cudaError_t launch_setup(const SetupArgs& a, int grid, cudaStream_t s);
+template <typename T> cudaError_t launch_setup(const SetupArgs& a, cudaStream_t s);
+template <typename T> cudaError_t launch_masked_copy(const void* in, void* out, const uint8_t* nb, long long nv,
+                                                     int grid, cudaStream_t s);
 template <typename T> cudaError_t launch_grad(const DataArgs& a, int grid, cudaStream_t s);
 template <typename T> cudaError_t launch_dir(const DataArgs& a, int grid, cudaStream_t s);
 template <typename T> cudaError_t launch_ls(const DataArgs& a, int grid, cudaStream_t s);

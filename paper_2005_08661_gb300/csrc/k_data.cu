@@ -57,8 +57,8 @@ __device__ __forceinline__ void sin_cos(double x, double* s, double* c) { sincos
 // NC coils held in registers; NC == 0: literal curvature, runtime coil count; NC == 1:
 // coil-combined curvature (exact for one coil).
 template <typename T, int NC, bool COST, bool CURV>
-__device__ __forceinline__ void eval_voxel(const DataArgs& a, long long j, T w, T& cost, T& grad,
-                                           T& curv) {
+__device__ __forceinline__ void eval_voxel(const DataArgs& a, long long j /* compact index */, T w, T& cost,
+                                           T& grad, T& curv) {
     using T2 = typename V2<T>::t;
     const long long nv = a.geo.nv;
     const T2* pairs = (const T2*)a.pairs;
@@ -119,10 +119,11 @@ __device__ __forceinline__ void eval_voxel(const DataArgs& a, long long j, T w, 
 
 // w_out = w_in + alpha z (the previous iteration's update, Algorithm box), then at w_out:
 // g = grad Psi (Eq. 8), d (Eq. 10), and Psi (Eq. 5) reduced to scal[S_COST] / cost_hist.
+// Runs over the compact list of mask voxels; entries outside the mask are never written
+// (the host zeroes them once).
 template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads) k_grad(DataArgs a) {
     __shared__ double sbuf[32];
-    const long long nv = a.geo.nv;
     const int nx = a.geo.nx;
     const long long nxy = (long long)nx * a.geo.ny;
     const T* w_in = (const T*)a.w_in;
@@ -133,16 +134,12 @@ __global__ void __launch_bounds__(kThreads) k_grad(DataArgs a) {
     const T alpha = z ? (T)a.scal[S_ALPHA] : T(0);
     const T beta = (T)a.beta;
     auto upd = [&](long long k) -> T { return z ? w_in[k] + alpha * z[k] : w_in[k]; };
+    const long long nm = a.istate[I_NMASK];
     double acc = 0.0;
-    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nv;
-         j += (long long)gridDim.x * blockDim.x) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nm;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long j = a.vlist[k];
         const uint8_t b = a.nb[j];
-        if (!(b & NB_IN)) {
-            w_out[j] = T(0);
-            if (g) g[j] = T(0);
-            if (d) d[j] = T(0);
-            continue;
-        }
         const T wj = upd(j);
         w_out[j] = wj;
         T lap = 0, reg = 0;
@@ -153,7 +150,7 @@ __global__ void __launch_bounds__(kThreads) k_grad(DataArgs a) {
         if (b & NB_YP) { const T e = wj - upd(j + nx); lap += e; reg += e * e; }
         if (b & NB_ZP) { const T e = wj - upd(j + nxy); lap += e; reg += e * e; }
         T cst, gr, cu;
-        eval_voxel<T, NC, true, true>(a, j, wj, cst, gr, cu);
+        eval_voxel<T, NC, true, true>(a, k, wj, cst, gr, cu);
         if (g) g[j] = gr + beta * lap;
         if (d) d[j] = cu;
         acc += (double)cst + 0.5 * a.beta * (double)reg;
@@ -177,7 +174,6 @@ __global__ void __launch_bounds__(kThreads) k_grad(DataArgs a) {
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_dir(DataArgs a) {
     __shared__ double sbuf[4 * 32];
-    const long long nv = a.geo.nv;
     const int nx = a.geo.nx;
     const long long nxy = (long long)nx * a.geo.ny;
     const int it = a.istate[I_ITER];
@@ -194,11 +190,12 @@ __global__ void __launch_bounds__(kThreads) k_dir(DataArgs a) {
     const T* g = (const T*)a.g;
     const T* d = (const T*)a.d;
     auto zval = [&](long long k) -> T { return -p[k] + muT * zo[k]; };
+    const long long nm = a.istate[I_NMASK];
     double s_cz2 = 0.0, s_czw = 0.0, s_zg = 0.0, s_zzd = 0.0;
-    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nv;
-         j += (long long)gridDim.x * blockDim.x) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nm;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long j = a.vlist[k];
         const uint8_t b = a.nb[j];
-        if (!(b & NB_IN)) { zn[j] = T(0); continue; }
         const T zj = zval(j), wj = w[j];
         zn[j] = zj;
         T cz2 = 0, czw = 0;
@@ -242,29 +239,29 @@ template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads) k_ls(DataArgs a) {
     __shared__ double sbuf[2 * 32];
     __shared__ double s_tot[2];
-    const long long nv = a.geo.nv;
     const T* w = (const T*)a.w_out;
     const T* z = (const T*)a.z_new;
     const double cz2 = a.scal[S_CZ2], czw = a.scal[S_CZW];
     const int it = a.istate[I_ITER];
     double alpha = a.scal[S_ALPHA];
     const int nb = gridDim.x;
-    for (int k = 1; k < a.nls; ++k) {
+    const long long nm = a.istate[I_NMASK];
+    for (int step = 1; step < a.nls; ++step) {
         const T aT = (T)alpha;
         double s1 = 0.0, s2 = 0.0;
-        for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nv;
-             j += (long long)gridDim.x * blockDim.x) {
-            if (!(a.nb[j] & NB_IN)) continue;
+        for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nm;
+             k += (long long)gridDim.x * blockDim.x) {
+            const long long j = a.vlist[k];
             const T zj = z[j];
             if (zj == T(0)) continue;
             T cst, gr, cu;
-            eval_voxel<T, NC, false, true>(a, j, w[j] + aT * zj, cst, gr, cu);
+            eval_voxel<T, NC, false, true>(a, k, w[j] + aT * zj, cst, gr, cu);
             s1 += (double)(zj * gr);
             s2 += (double)(zj * zj * cu);
         }
         double v[2] = {s1, s2};
         block_sum<2>(v, sbuf);
-        double* part = a.partials + 4 * (size_t)nb + (size_t)(k & 1) * 2 * nb;
+        double* part = a.partials + 4 * (size_t)nb + (size_t)(step & 1) * 2 * nb;
         if (threadIdx.x == 0) {
             part[blockIdx.x] = v[0];
             part[nb + blockIdx.x] = v[1];
@@ -294,16 +291,16 @@ __global__ void __launch_bounds__(kThreads) k_ls(DataArgs a) {
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_pdiag(DataArgs a, int mode) {
     __shared__ double sbuf[2 * 32];
-    const long long nv = a.geo.nv;
     const T* g = (const T*)a.g;
     const T* gp = (const T*)a.g_prev;
     const T* d = (const T*)a.d;
     T* p = (T*)a.z_new;  // output slot
     double s_gp = 0.0, s_gpp = 0.0;
-    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nv;
-         j += (long long)gridDim.x * blockDim.x) {
+    const long long nm = a.istate[I_NMASK];
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nm;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long j = a.vlist[k];
         const uint8_t b = a.nb[j];
-        if (!(b & NB_IN)) { p[j] = T(0); continue; }
         T pj = g[j];
         if (mode == 1) {
             const int cnt = __popc((unsigned)(b >> 1) & 0x3fu);

@@ -9,56 +9,217 @@
 //   L = (Pi + E) Pi^{-1/2},   L L' = H on H's nonzero set.
 // Forward (fused with the pivots): (Pi + E) v = g  ->  v_j = (g_j + beta sum_{k lower} v_k) / pi_j.
 // Back:                           (Pi + E') p = Pi v  ->  p_j = v_j + beta/pi_j sum_{k upper} p_k.
-// Voxels outside the mask are identity rows (p_j = 0) and never couple.
+// Voxels outside the mask are identity rows with 1/pi = v = p = 0, so every sum may run over
+// all grid neighbours: an outside neighbour contributes exactly 0.
 //
 // Parallel schedule: voxel (x, y, z) depends on (x-1, y, z), (x, y-1, z), (x, y, z-1), so
-// every hyperplane x + y + z = const is independent.  The grid is cut into 32 x 32 x TZ
+// every hyperplane x + y + z = const is independent.  The grid is cut into 32 x 32 x 8
 // tiles; a CTA claims tiles through an atomic ticket in a dependency-respecting order (a
-// tile's predecessors always hold smaller tickets, so no co-residency is assumed), waits on
-// the predecessors' ready flags (bounded spin), and sweeps the tile's 64 + TZ - 2 local
-// hyperplanes: lane = y, warp = z, and each thread walks its x row one step per
-// hyperplane, taking the -y value from the neighbouring lane by shuffle, the -z value from
-// the warp below through shared memory and the -x value from its own register.  Inputs
-// are staged in shared memory and outputs are written back row-coalesced.  Pivots are
-// carried in double in every precision mode; their tile faces go through a small FP64
-// face buffer.
+// tile's predecessors always hold smaller tickets, so no co-residency is assumed), starts
+// the asynchronous copy of the tile's inputs into shared memory, waits on the predecessors'
+// ready flags (bounded spin), and sweeps the tile's 70 local hyperplanes: lane = y,
+// warp = z, and each thread walks its x row one step per hyperplane, taking the -y value
+// from the neighbouring lane by shuffle, the -z value from the warp below through shared
+// memory and the -x value from its own register.  Outputs are written back row-coalesced
+// and the tile's flag is released before the back sweep's dot products.
+//
+// Pivot arithmetic: FP64 mode uses IEEE double.  FP32 mode carries the pivot recurrence
+// in double-float (an unevaluated sum hi + lo of two floats, about 46 significant bits)
+// on the FP32 pipes, because the GB300 FP64 pipe issues at about 1/64 of the FP32 rate and
+// sits on the sweep's critical path; the solves themselves run in float.
 #include "fm_internal.h"
 
 namespace fm {
 
 constexpr int kTZ = 8;
-constexpr int kFace = 32 * kTZ + 32 * kTZ + 32 * 32;  // doubles per tile: +x, +y, +z faces
+constexpr int kRows = kTZ * 32;  // rows of 32 x-values per tile (== threads per CTA)
+constexpr int kFaceN = 32 * kTZ + 32 * kTZ + 32 * 32;  // pivot values per tile: +x, +y, +z faces
+
+// ------------------------------------------------------------------ double-float
+
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ DF df_quick(float a, float b) {  // requires |a| >= |b| or a == 0
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_add(DF x, DF y) {
+    const DF s = df_two_sum(x.hi, y.hi);
+    const DF t = df_two_sum(x.lo, y.lo);
+    DF u = df_quick(s.hi, __fadd_rn(s.lo, t.hi));
+    return df_quick(u.hi, __fadd_rn(u.lo, t.lo));
+}
+__device__ __forceinline__ DF df_mul(DF x, DF y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return df_quick(p, e);
+}
+__device__ __forceinline__ DF df_from(double v) {
+    const float hi = (float)v;
+    return {hi, (float)(v - (double)hi)};
+}
+__device__ __forceinline__ DF df_neg(DF x) { return {-x.hi, -x.lo}; }
+// 1/x by one Newton step on the float reciprocal, carried in double-float
+__device__ __forceinline__ DF df_recip(DF x) {
+    const float r = __frcp_rn(x.hi);
+    // e = 1 - x r exactly enough: x.hi r + x.lo r in double-float
+    const float p = __fmul_rn(x.hi, r);
+    float pe = __fmaf_rn(x.hi, r, -p);
+    pe = __fmaf_rn(x.lo, r, pe);
+    const DF xr = df_quick(p, pe);
+    const DF e = df_add({1.0f, 0.0f}, df_neg(xr));
+    return df_add({r, 0.0f}, df_mul({r, 0.0f}, e));
+}
+
+// Pivot arithmetic per precision mode: P is the carried type (double or DF, 8 bytes).
+template <typename T> struct PivOps;
+template <> struct PivOps<double> {
+    using P = double;
+    static __device__ __forceinline__ P zero() { return 0.0; }
+    static __device__ __forceinline__ P add(P a, P b) { return a + b; }
+    // H_jj - beta^2 s with H_jj = d + beta n; returns 1/pi and whether pi > 0
+    static __device__ __forceinline__ P inv_pivot(double d, int n, double beta, P s, bool& ok) {
+        const double piv = d + beta * (double)n - beta * beta * s;
+        ok = piv > 0.0;
+        return ok ? 1.0 / piv : 0.0;
+    }
+    static __device__ __forceinline__ double to_T(P x) { return x; }
+};
+template <> struct PivOps<float> {
+    using P = DF;
+    static __device__ __forceinline__ P zero() { return {0.0f, 0.0f}; }
+    static __device__ __forceinline__ P add(P a, P b) { return df_add(a, b); }
+    static __device__ __forceinline__ P inv_pivot(float d, int n, double beta, P s, bool& ok) {
+        const DF b = df_from(beta), b2 = df_from(beta * beta);
+        const DF h = df_add({d, 0.0f}, df_mul(b, {(float)n, 0.0f}));
+        const DF piv = df_add(h, df_neg(df_mul(b2, s)));
+        ok = piv.hi > 0.0f;
+        return ok ? df_recip(piv) : DF{0.0f, 0.0f};
+    }
+    static __device__ __forceinline__ float to_T(P x) { return x.hi; }
+};
+
+// Pivot faces are written by other CTAs of the same launch: read them through L2.
+__device__ __forceinline__ double ld_face(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ DF ld_face(const DF* p) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    return {v.x, v.y};
+}
+
+// ------------------------------------------------------------------ asynchronous staging
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp4(void* s, const void* g) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp8(void* s, const void* g) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp16(void* s, const void* g) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// Start copying this thread's row (ly, lz) = (r & 31, r >> 5) of a T tile into s[r * 32 ..];
+// elements outside the grid are filled with `fill`.
+template <typename T>
+__device__ __forceinline__ void stage_row(T* s, const T* g, int r, int x0, int y0, int z0, const Geo& geo,
+                                          T fill) {
+    T* srow = s + r * 32;
+    const int y = y0 + (r & 31), z = z0 + (r >> 5);
+    if (y >= geo.ny || z >= geo.nz) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) srow[i] = fill;
+        return;
+    }
+    const T* grow = g + ((long long)z * geo.ny + y) * geo.nx + x0;
+    const int nvalid = min(32, geo.nx - x0);
+    if (nvalid == 32 && ((reinterpret_cast<uintptr_t>(grow) & 15) == 0)) {
+        constexpr int per = 16 / sizeof(T);
+#pragma unroll
+        for (int i = 0; i < 32; i += per) cp16(srow + i, grow + i);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            if (i < nvalid) {
+                if (sizeof(T) == 4) cp4(srow + i, grow + i);
+                else cp8(srow + i, grow + i);
+            } else {
+                srow[i] = fill;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void stage_row_u8(uint8_t* s, const uint8_t* g, int r, int x0, int y0, int z0,
+                                             const Geo& geo) {
+    uint8_t* srow = s + r * 32;
+    const int y = y0 + (r & 31), z = z0 + (r >> 5);
+    if (y >= geo.ny || z >= geo.nz) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) srow[i] = 0;
+        return;
+    }
+    const uint8_t* grow = g + ((long long)z * geo.ny + y) * geo.nx + x0;
+    const int nvalid = min(32, geo.nx - x0);
+    if (nvalid == 32 && ((reinterpret_cast<uintptr_t>(grow) & 15) == 0)) {
+        cp16(srow, grow);
+        cp16(srow + 16, grow + 16);
+    } else {
+        uint8_t v[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = i < nvalid ? grow[i] : (uint8_t)0;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) srow[i] = v[i];
+    }
+}
 
 template <typename T>
 struct FwdSmem {
-    static constexpr size_t bytes =
-        2 * kTZ * 1024 * sizeof(T) + kTZ * 1024 +                   // g->v, d->ip, nb
-        (kTZ * 32 * 2 + 1024 + 2 * kTZ * 32) * sizeof(double) +     // ip faces + z exchange
-        (kTZ * 32 * 2 + 1024 + 2 * kTZ * 32) * sizeof(T);           // v faces + z exchange
+    using P = typename PivOps<T>::P;
+    static constexpr size_t bytes = 2 * kRows * 32 * sizeof(T) + (kTZ * 32 * 2 + 1024 + 2 * kTZ * 32) * sizeof(P) +
+                                    (kTZ * 32 * 2 + 1024 + 2 * kTZ * 32) * sizeof(T) + kRows * 32;
 };
 template <typename T>
 struct BwdSmem {
-    static constexpr size_t bytes = 2 * kTZ * 1024 * sizeof(T) + kTZ * 1024 +
-                                    (kTZ * 32 * 2 + 1024 + 2 * kTZ * 32) * sizeof(T);
+    static constexpr size_t bytes = 2 * kRows * 32 * sizeof(T) + (kTZ * 32 * 2 + 1024 + 2 * kTZ * 32) * sizeof(T);
 };
 
+// mode 0: pivots from d (factor + forward); mode 1: stored 1/pi (forward only)
 template <typename T>
 __global__ void __launch_bounds__(32 * kTZ) k_ic_fwd(IcArgs a, int mode) {
+    using Ops = PivOps<T>;
+    using P = typename Ops::P;
     extern __shared__ __align__(16) unsigned char smem[];
-    T* sg = (T*)smem;                                   // [kTZ][32][32]: g, then v
-    T* sd = sg + kTZ * 1024;                            // d (or stored 1/pi), then 1/pi
-    double* fx_ip = (double*)(sd + kTZ * 1024);         // [kTZ][32] (lz, ly)
-    double* fy_ip = fx_ip + kTZ * 32;                   // [kTZ][32] (lz, lx)
-    double* fz_ip = fy_ip + kTZ * 32;                   // [32][32]  (ly, lx)
-    double* zb_ip = fz_ip + 1024;                       // [2][kTZ][32]
+    T* sg = (T*)smem;                              // [kTZ][32][32]: g, then v
+    T* sd = sg + kRows * 32;                       // d (or stored 1/pi), then 1/pi
+    P* fx_ip = (P*)(sd + kRows * 32);              // [kTZ][32] (lz, ly)
+    P* fy_ip = fx_ip + kTZ * 32;                   // [kTZ][32] (lz, lx)
+    P* fz_ip = fy_ip + kTZ * 32;                   // [32][32]  (ly, lx)
+    P* zb_ip = fz_ip + 1024;                       // [2][kTZ][32]
     T* fx_v = (T*)(zb_ip + 2 * kTZ * 32);
     T* fy_v = fx_v + kTZ * 32;
     T* fz_v = fy_v + kTZ * 32;
     T* zb_v = fz_v + 1024;
-    uint8_t* snb = (uint8_t*)(zb_v + 2 * kTZ * 32);     // [kTZ][32][32]
+    uint8_t* snb = (uint8_t*)(zb_v + 2 * kTZ * 32);  // [kTZ][32][32]
     __shared__ int s_tile;
 
-    const int nx = a.geo.nx, ny = a.geo.ny, nz = a.geo.nz;
+    const Geo geo = a.geo;
+    const int nx = geo.nx, ny = geo.ny, nz = geo.nz;
     const long long nxy = (long long)nx * ny;
     const int tid = threadIdx.x, lane = tid & 31, wz = tid >> 5;
     const T* g = (const T*)a.g;
@@ -66,8 +227,8 @@ __global__ void __launch_bounds__(32 * kTZ) k_ic_fwd(IcArgs a, int mode) {
     const T* ipin = (const T*)a.ip_in;
     T* v = (T*)a.v;
     T* ipo = (T*)a.ip_out;
+    P* face = (P*)a.face;
     const T betaT = (T)a.beta;
-    const double beta = a.beta, beta2 = a.beta * a.beta;
 
     for (;;) {
         if (tid == 0) {
@@ -80,21 +241,10 @@ __global__ void __launch_bounds__(32 * kTZ) k_ic_fwd(IcArgs a, int mode) {
         const int X = tile % a.ntx, Y = (tile / a.ntx) % a.nty, Z = tile / (a.ntx * a.nty);
         const int x0 = X * 32, y0 = Y * 32, z0 = Z * kTZ;
 
-        // stage this tile's inputs (they do not depend on other tiles)
-        for (int i = tid; i < kTZ * 1024; i += blockDim.x) {
-            const int x = x0 + (i & 31), y = y0 + ((i >> 5) & 31), z = z0 + (i >> 10);
-            T gv = 0, dv = 0;
-            uint8_t b = 0;
-            if (x < nx && y < ny && z < nz) {
-                const long long j = (long long)z * nxy + (long long)y * nx + x;
-                gv = g[j];
-                dv = mode == 0 ? d[j] : ipin[j];
-                b = a.nb[j];
-            }
-            sg[i] = gv;
-            sd[i] = dv;
-            snb[i] = b;
-        }
+        // start the copies of this tile's inputs (they do not depend on other tiles)
+        stage_row<T>(sg, g, tid, x0, y0, z0, geo, T(0));
+        stage_row<T>(sd, mode == 0 ? d : ipin, tid, x0, y0, z0, geo, T(0));
+        if (mode == 0) stage_row_u8(snb, a.nb, tid, x0, y0, z0, geo);
         // wait for the -x, -y, -z neighbour tiles
         if (tid == 0) {
             bool ok = true;
@@ -105,110 +255,111 @@ __global__ void __launch_bounds__(32 * kTZ) k_ic_fwd(IcArgs a, int mode) {
             __threadfence();
         }
         __syncthreads();
-        // faces produced by the neighbour tiles in this launch (read through L2)
-        for (int i = tid; i < kTZ * 32; i += blockDim.x) {
-            const int hi = i >> 5, lo = i & 31;  // x-face: (lz, ly); y-face: (lz, lx)
-            double ip = 0.0;
-            T vv = 0;
+        // faces produced by the neighbour tiles in this launch (read through L2): thread tid
+        // owns x-face and y-face entry tid and z-face entries tid + 256 q
+        {
+            const int hi = tid >> 5, lo = tid & 31;
+            P ipx = Ops::zero(), ipy = Ops::zero(), ipz[4];
+            T vx = 0, vy = 0, vz[4];
             if (X > 0 && y0 + lo < ny && z0 + hi < nz) {
-                const long long j = (long long)(z0 + hi) * nxy + (long long)(y0 + lo) * nx + (x0 - 1);
-                vv = __ldcg(v + j);
-                if (mode == 0) ip = __ldcg(a.face + (size_t)(tile - 1) * kFace + i);
+                vx = __ldcg(v + (long long)(z0 + hi) * nxy + (long long)(y0 + lo) * nx + (x0 - 1));
+                if (mode == 0) ipx = ld_face(face + (size_t)(tile - 1) * kFaceN + tid);
             }
-            fx_ip[i] = ip;
-            fx_v[i] = vv;
-            ip = 0.0;
-            vv = 0;
             if (Y > 0 && x0 + lo < nx && z0 + hi < nz) {
-                const long long j = (long long)(z0 + hi) * nxy + (long long)(y0 - 1) * nx + (x0 + lo);
-                vv = __ldcg(v + j);
-                if (mode == 0) ip = __ldcg(a.face + (size_t)(tile - a.ntx) * kFace + 32 * kTZ + i);
+                vy = __ldcg(v + (long long)(z0 + hi) * nxy + (long long)(y0 - 1) * nx + (x0 + lo));
+                if (mode == 0) ipy = ld_face(face + (size_t)(tile - a.ntx) * kFaceN + 32 * kTZ + tid);
             }
-            fy_ip[i] = ip;
-            fy_v[i] = vv;
-        }
-        for (int i = tid; i < 1024; i += blockDim.x) {
-            const int ly = i >> 5, lx = i & 31;
-            double ip = 0.0;
-            T vv = 0;
-            if (Z > 0 && x0 + lx < nx && y0 + ly < ny) {
-                const long long j = (long long)(z0 - 1) * nxy + (long long)(y0 + ly) * nx + (x0 + lx);
-                vv = __ldcg(v + j);
-                if (mode == 0)
-                    ip = __ldcg(a.face + (size_t)(tile - a.ntx * a.nty) * kFace + 64 * kTZ + i);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = tid + 256 * q, ly = i >> 5, lx = i & 31;
+                ipz[q] = Ops::zero();
+                vz[q] = 0;
+                if (Z > 0 && x0 + lx < nx && y0 + ly < ny) {
+                    vz[q] = __ldcg(v + (long long)(z0 - 1) * nxy + (long long)(y0 + ly) * nx + (x0 + lx));
+                    if (mode == 0) ipz[q] = ld_face(face + (size_t)(tile - a.ntx * a.nty) * kFaceN + 64 * kTZ + i);
+                }
             }
-            fz_ip[i] = ip;
-            fz_v[i] = vv;
+            fx_ip[tid] = ipx;
+            fx_v[tid] = vx;
+            fy_ip[tid] = ipy;
+            fy_v[tid] = vy;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                fz_ip[tid + 256 * q] = ipz[q];
+                fz_v[tid + 256 * q] = vz[q];
+            }
         }
+        cp_wait_all();
         __syncthreads();
 
         // sweep the local hyperplanes s = lx + ly + lz
         const int ly = lane, lz = wz;
-        double out_ip = 0.0;
+        P out_ip = Ops::zero();
         T out_v = 0;
         bool bad = false;
+        P* myface = face + (size_t)tile * kFaceN;
         for (int s = 0; s < 64 + kTZ - 2; ++s) {
-            const double up_ip = __shfl_up_sync(0xffffffffu, out_ip, 1);
+            P up_ip;
+            if constexpr (sizeof(P) == 8 && sizeof(T) == 8) {
+                up_ip = __shfl_up_sync(0xffffffffu, out_ip, 1);
+            } else {
+                DF o = *reinterpret_cast<DF*>(&out_ip);
+                DF u{__shfl_up_sync(0xffffffffu, o.hi, 1), __shfl_up_sync(0xffffffffu, o.lo, 1)};
+                up_ip = *reinterpret_cast<P*>(&u);
+            }
             const T up_v = __shfl_up_sync(0xffffffffu, out_v, 1);
             const int lx = s - ly - lz;
             if (lx >= 0 && lx < 32) {
                 const int i = (lz * 32 + ly) * 32 + lx;
-                const uint8_t b = snb[i];
-                double ipj = 0.0;
+                P ipj = Ops::zero();
                 T vj = 0;
-                if (b & NB_IN) {
-                    double sip = 0.0;
-                    T sv = 0;
-                    if (b & NB_XM) {
-                        if (lx == 0) { sip += fx_ip[lz * 32 + ly]; sv += fx_v[lz * 32 + ly]; }
-                        else { sip += out_ip; sv += out_v; }
+                const P xip = lx == 0 ? fx_ip[lz * 32 + ly] : out_ip;
+                const T xv = lx == 0 ? fx_v[lz * 32 + ly] : out_v;
+                const P yip = ly == 0 ? fy_ip[lz * 32 + lx] : up_ip;
+                const T yv = ly == 0 ? fy_v[lz * 32 + lx] : up_v;
+                const int q = ((s - 1) & 1) * kTZ * 32 + (lz - 1) * 32 + ly;
+                const P zip = lz == 0 ? fz_ip[ly * 32 + lx] : zb_ip[q];
+                const T zv = lz == 0 ? fz_v[ly * 32 + lx] : zb_v[q];
+                if (mode == 0) {
+                    const uint8_t b = snb[i];
+                    if (b & NB_IN) {
+                        bool ok;
+                        ipj = Ops::inv_pivot(sd[i], __popc((unsigned)(b >> 1) & 0x3fu), a.beta,
+                                             Ops::add(Ops::add(xip, yip), zip), ok);
+                        bad |= !ok;
+                        vj = (sg[i] + betaT * ((xv + yv) + zv)) * (T)Ops::to_T(ipj);
                     }
-                    if (b & NB_YM) {
-                        if (ly == 0) { sip += fy_ip[lz * 32 + lx]; sv += fy_v[lz * 32 + lx]; }
-                        else { sip += up_ip; sv += up_v; }
-                    }
-                    if (b & NB_ZM) {
-                        if (lz == 0) { sip += fz_ip[ly * 32 + lx]; sv += fz_v[ly * 32 + lx]; }
-                        else {
-                            const int q = ((s - 1) & 1) * kTZ * 32 + (lz - 1) * 32 + ly;
-                            sip += zb_ip[q];
-                            sv += zb_v[q];
-                        }
-                    }
-                    if (mode == 0) {
-                        const int cnt = __popc((unsigned)(b >> 1) & 0x3fu);
-                        const double piv = (double)sd[i] + beta * (double)cnt - beta2 * sip;
-                        if (piv > 0.0) ipj = 1.0 / piv;
-                        else bad = true;
-                    } else {
-                        ipj = (double)sd[i];
-                    }
-                    vj = (sg[i] + betaT * sv) * (T)ipj;
+                    sd[i] = (T)Ops::to_T(ipj);
+                } else {
+                    const T ipt = sd[i];
+                    vj = (sg[i] + betaT * ((xv + yv) + zv)) * ipt;
                 }
                 sg[i] = vj;
-                sd[i] = (T)ipj;
                 out_ip = ipj;
                 out_v = vj;
                 zb_ip[(s & 1) * kTZ * 32 + lz * 32 + ly] = ipj;
                 zb_v[(s & 1) * kTZ * 32 + lz * 32 + ly] = vj;
                 if (mode == 0) {
-                    double* f = a.face + (size_t)tile * kFace;
-                    if (lx == 31) f[lz * 32 + ly] = ipj;
-                    if (ly == 31) f[32 * kTZ + lz * 32 + lx] = ipj;
-                    if (lz == kTZ - 1) f[64 * kTZ + ly * 32 + lx] = ipj;
+                    if (lx == 31) myface[lz * 32 + ly] = ipj;
+                    if (ly == 31) myface[32 * kTZ + lz * 32 + lx] = ipj;
+                    if (lz == kTZ - 1) myface[64 * kTZ + ly * 32 + lx] = ipj;
                 }
             }
             __syncthreads();
         }
         if (bad) set_err(a.istate, FM_ERR_NOT_PD);
 
-        // write back, then publish the tile
-        for (int i = tid; i < kTZ * 1024; i += blockDim.x) {
-            const int x = x0 + (i & 31), y = y0 + ((i >> 5) & 31), z = z0 + (i >> 10);
-            if (x < nx && y < ny && z < nz) {
-                const long long j = (long long)z * nxy + (long long)y * nx + x;
-                v[j] = sg[i];
-                if (mode == 0 && ipo) ipo[j] = sd[i];
+        // write back row-coalesced (warp lz writes its 32 rows, lane = x), then publish
+        {
+            const int nvalid = min(32, nx - x0);
+            const int z = z0 + wz;
+            if (z < nz && lane < nvalid) {
+                for (int ly2 = 0; ly2 < 32 && y0 + ly2 < ny; ++ly2) {
+                    const long long j = (long long)z * nxy + (long long)(y0 + ly2) * nx + x0 + lane;
+                    const int i = (wz * 32 + ly2) * 32 + lane;
+                    v[j] = sg[i];
+                    if (mode == 0 && ipo) ipo[j] = sd[i];
+                }
             }
         }
         __syncthreads();
@@ -223,17 +374,17 @@ template <typename T>
 __global__ void __launch_bounds__(32 * kTZ) k_ic_bwd(IcArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     T* sv = (T*)smem;                 // [kTZ][32][32]: v, then p
-    T* sip = sv + kTZ * 1024;         // 1/pi
-    T* fx = sip + kTZ * 1024;         // [kTZ][32] (lz, ly) p at x0 + 32
+    T* sip = sv + kRows * 32;         // 1/pi
+    T* fx = sip + kRows * 32;         // [kTZ][32] (lz, ly) p at x0 + 32
     T* fy = fx + kTZ * 32;            // [kTZ][32] (lz, lx) p at y0 + 32
     T* fz = fy + kTZ * 32;            // [32][32] (ly, lx) p at z0 + kTZ
     T* zb = fz + 1024;                // [2][kTZ][32]
-    uint8_t* snb = (uint8_t*)(zb + 2 * kTZ * 32);
     __shared__ int s_tile;
     __shared__ bool s_last;
     __shared__ double sbuf[2 * 32];
 
-    const int nx = a.geo.nx, ny = a.geo.ny, nz = a.geo.nz;
+    const Geo geo = a.geo;
+    const int nx = geo.nx, ny = geo.ny, nz = geo.nz;
     const long long nxy = (long long)nx * ny;
     const int tid = threadIdx.x, lane = tid & 31, wz = tid >> 5;
     const T* vin = (const T*)a.vin;
@@ -254,20 +405,8 @@ __global__ void __launch_bounds__(32 * kTZ) k_ic_bwd(IcArgs a) {
         const int X = tile % a.ntx, Y = (tile / a.ntx) % a.nty, Z = tile / (a.ntx * a.nty);
         const int x0 = X * 32, y0 = Y * 32, z0 = Z * kTZ;
 
-        for (int i = tid; i < kTZ * 1024; i += blockDim.x) {
-            const int x = x0 + (i & 31), y = y0 + ((i >> 5) & 31), z = z0 + (i >> 10);
-            T vv = 0, iv = 0;
-            uint8_t b = 0;
-            if (x < nx && y < ny && z < nz) {
-                const long long j = (long long)z * nxy + (long long)y * nx + x;
-                vv = vin[j];
-                iv = ipb[j];
-                b = a.nb[j];
-            }
-            sv[i] = vv;
-            sip[i] = iv;
-            snb[i] = b;
-        }
+        stage_row<T>(sv, vin, tid, x0, y0, z0, geo, T(0));
+        stage_row<T>(sip, ipb, tid, x0, y0, z0, geo, T(0));
         if (tid == 0) {
             bool ok = true;
             if (X + 1 < a.ntx) ok = spin_until(a.flags + tile + 1, 1, a.spin_limit) && ok;
@@ -277,24 +416,26 @@ __global__ void __launch_bounds__(32 * kTZ) k_ic_bwd(IcArgs a) {
             __threadfence();
         }
         __syncthreads();
-        for (int i = tid; i < kTZ * 32; i += blockDim.x) {
-            const int hi = i >> 5, lo = i & 31;
-            T q = 0;
+        {
+            const int hi = tid >> 5, lo = tid & 31;
+            T qx = 0, qy = 0, qz[4];
             if (X + 1 < a.ntx && y0 + lo < ny && z0 + hi < nz)
-                q = __ldcg(p + (long long)(z0 + hi) * nxy + (long long)(y0 + lo) * nx + (x0 + 32));
-            fx[i] = q;
-            q = 0;
+                qx = __ldcg(p + (long long)(z0 + hi) * nxy + (long long)(y0 + lo) * nx + (x0 + 32));
             if (Y + 1 < a.nty && x0 + lo < nx && z0 + hi < nz)
-                q = __ldcg(p + (long long)(z0 + hi) * nxy + (long long)(y0 + 32) * nx + (x0 + lo));
-            fy[i] = q;
+                qy = __ldcg(p + (long long)(z0 + hi) * nxy + (long long)(y0 + 32) * nx + (x0 + lo));
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = tid + 256 * q, ly = i >> 5, lx = i & 31;
+                qz[q] = 0;
+                if (Z + 1 < a.ntz && x0 + lx < nx && y0 + ly < ny)
+                    qz[q] = __ldcg(p + (long long)(z0 + kTZ) * nxy + (long long)(y0 + ly) * nx + (x0 + lx));
+            }
+            fx[tid] = qx;
+            fy[tid] = qy;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) fz[tid + 256 * q] = qz[q];
         }
-        for (int i = tid; i < 1024; i += blockDim.x) {
-            const int ly = i >> 5, lx = i & 31;
-            T q = 0;
-            if (Z + 1 < a.ntz && x0 + lx < nx && y0 + ly < ny)
-                q = __ldcg(p + (long long)(z0 + kTZ) * nxy + (long long)(y0 + ly) * nx + (x0 + lx));
-            fz[i] = q;
-        }
+        cp_wait_all();
         __syncthreads();
 
         const int ly = lane, lz = wz;
@@ -304,17 +445,10 @@ __global__ void __launch_bounds__(32 * kTZ) k_ic_bwd(IcArgs a) {
             const int lx = s - ly - lz;
             if (lx >= 0 && lx < 32) {
                 const int i = (lz * 32 + ly) * 32 + lx;
-                const uint8_t b = snb[i];
-                T pj = 0;
-                if (b & NB_IN) {
-                    T sum = 0;
-                    if (b & NB_XP) sum += lx == 31 ? fx[lz * 32 + ly] : out;
-                    if (b & NB_YP) sum += ly == 31 ? fy[lz * 32 + lx] : dn;
-                    if (b & NB_ZP)
-                        sum += lz == kTZ - 1 ? fz[ly * 32 + lx]
-                                             : zb[((s + 1) & 1) * kTZ * 32 + (lz + 1) * 32 + ly];
-                    pj = sv[i] + beta * sip[i] * sum;
-                }
+                const T px = lx == 31 ? fx[lz * 32 + ly] : out;
+                const T py = ly == 31 ? fy[lz * 32 + lx] : dn;
+                const T pz = lz == kTZ - 1 ? fz[ly * 32 + lx] : zb[((s + 1) & 1) * kTZ * 32 + (lz + 1) * 32 + ly];
+                const T pj = sv[i] + beta * sip[i] * ((px + py) + pz);
                 sv[i] = pj;
                 out = pj;
                 zb[(s & 1) * kTZ * 32 + lz * 32 + ly] = pj;
@@ -322,39 +456,50 @@ __global__ void __launch_bounds__(32 * kTZ) k_ic_bwd(IcArgs a) {
             __syncthreads();
         }
 
-        double acc[2] = {0.0, 0.0};
-        for (int i = tid; i < kTZ * 1024; i += blockDim.x) {
-            const int x = x0 + (i & 31), y = y0 + ((i >> 5) & 31), z = z0 + (i >> 10);
-            if (x < nx && y < ny && z < nz) {
-                const long long j = (long long)z * nxy + (long long)y * nx + x;
-                const T pj = sv[i];
-                p[j] = pj;
-                if (gd) acc[0] += (double)(gd[j] * pj);
-                if (gpd) acc[1] += (double)(gpd[j] * pj);
-            }
-        }
-        block_sum<2>(acc, sbuf);
-        if (tid == 0) {
-            if (a.tile_part) {
-                a.tile_part[tile] = acc[0];
-                a.tile_part[a.ntiles + tile] = acc[1];
-            }
-            __threadfence();
-            st_release(a.flags + tile, 1);
-            const int prev = atomicAdd(a.done, 1);
-            s_last = (prev == a.ntiles - 1);
-            if (s_last) __threadfence();
+        // write back, publish, then the dot products (off the wavefront's critical path)
+        const int nvalid = min(32, nx - x0);
+        const int z = z0 + wz;
+        const bool zin = z < nz && lane < nvalid;
+        if (zin) {
+            for (int ly2 = 0; ly2 < 32 && y0 + ly2 < ny; ++ly2)
+                p[(long long)z * nxy + (long long)(y0 + ly2) * nx + x0 + lane] = sv[(wz * 32 + ly2) * 32 + lane];
         }
         __syncthreads();
-        if (s_last && a.tile_part) {
-            double tot[2];
-            sum_partials<2>(a.tile_part, a.ntiles, tot, sbuf);
+        if (tid == 0) {
+            __threadfence();
+            st_release(a.flags + tile, 1);
+        }
+        if (a.tile_part) {
+            double acc[2] = {0.0, 0.0};
+            if (zin) {
+                for (int ly2 = 0; ly2 < 32 && y0 + ly2 < ny; ++ly2) {
+                    const long long j = (long long)z * nxy + (long long)(y0 + ly2) * nx + x0 + lane;
+                    const T pj = sv[(wz * 32 + ly2) * 32 + lane];
+                    if (gd) acc[0] += (double)(gd[j] * pj);
+                    if (gpd) acc[1] += (double)(gpd[j] * pj);
+                }
+            }
+            block_sum<2>(acc, sbuf);
             if (tid == 0) {
-                a.scal[S_GP] = tot[0];
-                a.scal[S_GPREVP] = tot[1];
-                if (!isfinite(tot[0]) || !isfinite(tot[1])) set_err(a.istate, FM_ERR_NONFINITE);
+                a.tile_part[tile] = acc[0];
+                a.tile_part[a.ntiles + tile] = acc[1];
+                __threadfence();
+                const int prev = atomicAdd(a.done, 1);
+                s_last = (prev == a.ntiles - 1);
+                if (s_last) __threadfence();
+            }
+            __syncthreads();
+            if (s_last) {
+                double tot[2];
+                sum_partials<2>(a.tile_part, a.ntiles, tot, sbuf);
+                if (tid == 0) {
+                    a.scal[S_GP] = tot[0];
+                    a.scal[S_GPREVP] = tot[1];
+                    if (!isfinite(tot[0]) || !isfinite(tot[1])) set_err(a.istate, FM_ERR_NONFINITE);
+                }
             }
         }
+        __syncthreads();
     }
 }
 

@@ -1,6 +1,6 @@
 // k_setup.cu -- once-per-acquisition precompute (Algorithm box: "precompute r_cdmnj by
-// Eq. 3 and t_m - t_n"), neighbour bits of the support mask, the Eq. 6 initial map and
-// the omega-independent part of the cost.
+// Eq. 3 and t_m - t_n"), neighbour bits of the support mask, the compact list of mask
+// voxels, the Eq. 6 initial map and the omega-independent part of the cost.
 //
 // With W_cm = conj(s_c) y_cm / sqrt(L S), S = sum_c |s_c|^2 (field-map case, Gamma = 1/L),
 // Eq. 3 factors exactly as r_cdmn = conj(W_cm) W_dn.  Hence
@@ -10,63 +10,150 @@
 //   Phi_j(w) = K_j + 4 sum_{m<n} |R_mn| sin^2((angle R_mn + w (t_m - t_n)) / 2),
 //   K_j = (sum_m A_m)^2 - (sum_m |Z_m|)^2  (the m = n terms plus, for each pair, the
 //   coil-combination remainder sum_cd |r| - |R|), which does not depend on w.
-// Stored per voxel: (|R_mn|, angle R_mn) for each pair m < n, and (|W_cm|, angle W_cm)
-// for the literal curvature sum of Eq. 10, which does not collapse over coils.
+// Stored per mask voxel, in the compact (ascending voxel) order the data-term kernels
+// iterate: (|R_mn|, angle R_mn) for each pair m < n, and (|W_cm|, angle W_cm) for the
+// literal curvature sum of Eq. 10, which does not collapse over coils.
+//
+// Compaction: k_mask_count counts mask voxels per 1024-voxel chunk, k_chunk_scan turns the
+// counts into exclusive offsets (single block, fixed order), and k_setup ranks each mask
+// voxel inside its chunk with warp ballots, so the compact order is the voxel order.
 #include "fm_internal.h"
 
 namespace fm {
 
+constexpr int kSetupThreads = 256;
+
+__device__ __forceinline__ bool in_mask(const uint8_t* mask, long long j) { return mask ? mask[j] != 0 : true; }
+
+__global__ void __launch_bounds__(kSetupThreads) k_mask_count(const uint8_t* mask, long long nv, int* counts) {
+    __shared__ int warp_cnt[kSetupThreads / 32];
+    const long long base = (long long)blockIdx.x * kChunk;
+    int c = 0;
+#pragma unroll
+    for (int q = 0; q < kChunk / kSetupThreads; ++q) {
+        const long long j = base + q * kSetupThreads + threadIdx.x;
+        c += (j < nv && in_mask(mask, j)) ? 1 : 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) warp_cnt[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < kSetupThreads / 32; ++w) t += warp_cnt[w];
+        counts[blockIdx.x] = t;
+    }
+}
+
+// Exclusive scan of counts[0..n) in place (one block of 1024 threads, tiles of 1024);
+// the total goes to *total.
+__global__ void __launch_bounds__(1024) k_chunk_scan(int* counts, int n, int* total) {
+    __shared__ int warp_sum[32];
+    __shared__ int s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int base = 0; base < n; base += 1024) {
+        const int i = base + threadIdx.x;
+        const int x = i < n ? counts[i] : 0;
+        int incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) warp_sum[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            int ws = warp_sum[lane];
+            int wi = ws;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += y;
+            }
+            warp_sum[lane] = wi - ws;  // exclusive warp offsets
+        }
+        __syncthreads();
+        const int carry = s_carry;
+        if (i < n) counts[i] = carry + warp_sum[wid] + incl - x;
+        __syncthreads();
+        if (threadIdx.x == 1023) s_carry = carry + warp_sum[wid] + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = s_carry;
+}
+
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_setup(SetupArgs a) {
+__global__ void __launch_bounds__(kSetupThreads) k_setup(SetupArgs a) {
     using T2 = typename V2<T>::t;
     __shared__ double sbuf[32];
+    __shared__ int warp_cnt[kSetupThreads / 32];
     const long long nv = a.geo.nv;
     const int nx = a.geo.nx, ny = a.geo.ny, nz = a.geo.nz, nc = a.nc, L = a.L;
+    const long long nxy = (long long)nx * ny;
     const T2* y = (const T2*)a.y;
     const T2* sm = (const T2*)a.smap;
     T2* pairs = (T2*)a.pairs;
     T2* coils = (T2*)a.coils;
     T* w0 = (T*)a.w0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const long long base = (long long)blockIdx.x * kChunk;
+    int running = a.chunk_off[blockIdx.x];
     double kacc = 0.0;
-    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nv;
-         j += (long long)gridDim.x * blockDim.x) {
+    for (int q = 0; q < kChunk / kSetupThreads; ++q) {
+        const long long j = base + q * kSetupThreads + threadIdx.x;
+        const bool in = j < nv && in_mask(a.mask, j);
+        // rank of this mask voxel in voxel order
+        const unsigned bal = __ballot_sync(0xffffffffu, in);
+        if (lane == 0) warp_cnt[wid] = __popc(bal);
+        __syncthreads();
+        int off = running;
+        for (int w = 0; w < wid; ++w) off += warp_cnt[w];
+        int tot = 0;
+        for (int w = 0; w < kSetupThreads / 32; ++w) tot += warp_cnt[w];
+        const int k = off + __popc(bal & ((1u << lane) - 1u));
+        __syncthreads();
+        running += tot;
+        if (j >= nv) continue;
         const int x = (int)(j % nx);
         const int yy = (int)((j / nx) % ny);
-        const int z = (int)(j / ((long long)nx * ny));
-        const bool in = a.mask ? a.mask[j] != 0 : true;
+        const int z = (int)(j / nxy);
         uint8_t bits = 0;
         if (in) {
-            const long long nxy = (long long)nx * ny;
-            auto m = [&](long long k) { return a.mask ? a.mask[k] != 0 : true; };
             bits = NB_IN;
-            if (x > 0 && m(j - 1)) bits |= NB_XM;
-            if (x + 1 < nx && m(j + 1)) bits |= NB_XP;
-            if (yy > 0 && m(j - nx)) bits |= NB_YM;
-            if (yy + 1 < ny && m(j + nx)) bits |= NB_YP;
-            if (z > 0 && m(j - nxy)) bits |= NB_ZM;
-            if (z + 1 < nz && m(j + nxy)) bits |= NB_ZP;
+            if (x > 0 && in_mask(a.mask, j - 1)) bits |= NB_XM;
+            if (x + 1 < nx && in_mask(a.mask, j + 1)) bits |= NB_XP;
+            if (yy > 0 && in_mask(a.mask, j - nx)) bits |= NB_YM;
+            if (yy + 1 < ny && in_mask(a.mask, j + nx)) bits |= NB_YP;
+            if (z > 0 && in_mask(a.mask, j - nxy)) bits |= NB_ZM;
+            if (z + 1 < nz && in_mask(a.mask, j + nxy)) bits |= NB_ZP;
         }
         a.nb[j] = bits;
+        if (!in) {
+            w0[j] = T(0);
+            continue;
+        }
+        a.vlist[k] = (int)j;
         double S = 0.0;
         for (int c = 0; c < nc; ++c) {
-            double sr = sm ? (double)sm[(size_t)c * nv + j].x : 1.0;
-            double si = sm ? (double)sm[(size_t)c * nv + j].y : 0.0;
+            const double sr = sm ? (double)sm[(size_t)c * nv + j].x : 1.0;
+            const double si = sm ? (double)sm[(size_t)c * nv + j].y : 0.0;
             S += sr * sr + si * si;
         }
-        const bool live = in && S > 0.0;
-        const double scale = live ? 1.0 / sqrt((double)L * S) : 0.0;
+        const double scale = S > 0.0 ? 1.0 / sqrt((double)L * S) : 0.0;
         double Zr[FM_MAX_ECHO], Zi[FM_MAX_ECHO], Am[FM_MAX_ECHO];
         for (int mm = 0; mm < L; ++mm) {
             double zr = 0.0, zi = 0.0, am = 0.0;
             for (int c = 0; c < nc; ++c) {
-                double sr = sm ? (double)sm[(size_t)c * nv + j].x : 1.0;
-                double si = sm ? (double)sm[(size_t)c * nv + j].y : 0.0;
-                T2 yv = y[((size_t)mm * nc + c) * nv + j];
-                double yr = (double)yv.x, yi = (double)yv.y;
+                const double sr = sm ? (double)sm[(size_t)c * nv + j].x : 1.0;
+                const double si = sm ? (double)sm[(size_t)c * nv + j].y : 0.0;
+                const T2 yv = y[((size_t)mm * nc + c) * nv + j];
+                const double yr = (double)yv.x, yi = (double)yv.y;
                 // conj(s) * y, scaled
-                double wr = (sr * yr + si * yi) * scale;
-                double wi = (sr * yi - si * yr) * scale;
-                double amp = sqrt(wr * wr + wi * wi);
+                const double wr = (sr * yr + si * yi) * scale;
+                const double wi = (sr * yi - si * yr) * scale;
+                const double amp = sqrt(wr * wr + wi * wi);
                 zr += wr;
                 zi += wi;
                 am += amp;
@@ -74,7 +161,7 @@ __global__ void __launch_bounds__(kThreads) k_setup(SetupArgs a) {
                     T2 o;
                     o.x = (T)amp;
                     o.y = (T)(amp > 0.0 ? atan2(wi, wr) : 0.0);
-                    coils[((size_t)mm * nc + c) * nv + j] = o;
+                    coils[((size_t)mm * nc + c) * nv + k] = o;
                 }
             }
             Zr[mm] = zr;
@@ -84,23 +171,23 @@ __global__ void __launch_bounds__(kThreads) k_setup(SetupArgs a) {
         for (int p = 0; p < a.pr.P; ++p) {
             const int mm = a.pr.m[p], n = a.pr.n[p];
             // R = conj(Z_m) Z_n
-            double rr = Zr[mm] * Zr[n] + Zi[mm] * Zi[n];
-            double ri = Zr[mm] * Zi[n] - Zi[mm] * Zr[n];
+            const double rr = Zr[mm] * Zr[n] + Zi[mm] * Zi[n];
+            const double ri = Zr[mm] * Zi[n] - Zi[mm] * Zr[n];
             T2 o;
             o.x = (T)sqrt(rr * rr + ri * ri);
             o.y = (T)((rr == 0.0 && ri == 0.0) ? 0.0 : atan2(ri, rr));
-            pairs[(size_t)p * nv + j] = o;
+            pairs[(size_t)p * nv + k] = o;
         }
         double sa = 0.0, sz = 0.0;
         for (int mm = 0; mm < L; ++mm) {
             sa += Am[mm];
             sz += sqrt(Zr[mm] * Zr[mm] + Zi[mm] * Zi[mm]);
         }
-        if (live) kacc += (sa - sz) * (sa + sz);
+        if (S > 0.0) kacc += (sa - sz) * (sa + sz);
         // Eq. 6: angle(conj(z_1) z_2) / (t_2 - t_1); z_m and Z_m differ by a positive scale
-        double er = Zr[0] * Zr[1] + Zi[0] * Zi[1];
-        double ei = Zr[0] * Zi[1] - Zi[0] * Zr[1];
-        double w = (live && (er != 0.0 || ei != 0.0)) ? atan2(ei, er) / (a.te1 - a.te0) : 0.0;
+        const double er = Zr[0] * Zr[1] + Zi[0] * Zi[1];
+        const double ei = Zr[0] * Zi[1] - Zi[0] * Zr[1];
+        const double w = (S > 0.0 && (er != 0.0 || ei != 0.0)) ? atan2(ei, er) / (a.te1 - a.te0) : 0.0;
         w0[j] = (T)w;
     }
     double v[1] = {kacc}, out[1];
@@ -113,12 +200,29 @@ __global__ void __launch_bounds__(kThreads) k_setup(SetupArgs a) {
 }
 
 template <typename T>
-cudaError_t launch_setup(const SetupArgs& a, int grid, cudaStream_t s) {
-    k_setup<T><<<grid, kThreads, 0, s>>>(a);
+__global__ void __launch_bounds__(kSetupThreads) k_masked_copy(const T* in, T* out, const uint8_t* nb, long long nv) {
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nv; j += (long long)gridDim.x * blockDim.x)
+        out[j] = (nb[j] & NB_IN) ? in[j] : T(0);
+}
+
+template <typename T>
+cudaError_t launch_setup(const SetupArgs& a, cudaStream_t s) {
+    const int nchunks = (int)((a.geo.nv + kChunk - 1) / kChunk);
+    k_mask_count<<<nchunks, kSetupThreads, 0, s>>>(a.mask, a.geo.nv, a.chunk_off);
+    k_chunk_scan<<<1, 1024, 0, s>>>(a.chunk_off, nchunks, a.istate + I_NMASK);
+    k_setup<T><<<nchunks, kSetupThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_setup<float>(const SetupArgs&, int, cudaStream_t);
-template cudaError_t launch_setup<double>(const SetupArgs&, int, cudaStream_t);
+template <typename T>
+cudaError_t launch_masked_copy(const void* in, void* out, const uint8_t* nb, long long nv, int grid, cudaStream_t s) {
+    k_masked_copy<T><<<grid, kSetupThreads, 0, s>>>((const T*)in, (T*)out, nb, nv);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_setup<float>(const SetupArgs&, cudaStream_t);
+template cudaError_t launch_setup<double>(const SetupArgs&, cudaStream_t);
+template cudaError_t launch_masked_copy<float>(const void*, void*, const uint8_t*, long long, int, cudaStream_t);
+template cudaError_t launch_masked_copy<double>(const void*, void*, const uint8_t*, long long, int, cudaStream_t);
 
 }  // namespace fm
