@@ -74,18 +74,19 @@ def sub_volume(vol, size):
 # ------------------------------------------------------------------ flop / byte model
 
 def data_eval_flops(nc, L, literal):
-    """Algorithmic FP32 flops of one voxel's data-term evaluation (gradient + curvature).
+    """Algorithmic FP32 flops of one voxel's data-term evaluation (gradient + curvature),
+    counting a fused multiply-add as 2.
 
     Per echo pair: phase (2), half-angle sine/cosine (20), gradient/cost terms (6).  Literal
-    curvature per (pair, c, d): phase difference (1), wrap to [-pi, pi] (4), u^2 (1),
-    degree-8 polynomial in u^2 for sin(u)/u (16), amplitude multiply-accumulate (2) = 24;
+    curvature per (pair, c, d): phase difference (1), wrap to [-pi, pi] (5), u^2 (1),
+    degree-6 polynomial in u^2 for sin(u)/u (12), amplitude multiply-accumulate (2) = 21;
     plus 2 per (pair, d) for the rotated phase and 2 per (pair, c) for the outer sum."""
     P = L * (L - 1) // 2
     per_pair = 28
     if literal:
-        per_pair += nc * nc * 24 + 4 * nc
+        per_pair += nc * nc * 21 + 4 * nc
     else:
-        per_pair += 24
+        per_pair += 21
     return P * per_pair
 
 

@@ -79,8 +79,8 @@ typedef struct fm_opts {
     int nls;             /* monotonic line-search steps per outer iteration (N_i), >= 1; default 5 */
     int precond;         /* FM_PC_IC0 (default) | FM_PC_DIAG | FM_PC_NONE */
     int curvature;       /* FM_CURV_LITERAL (default) | FM_CURV_COMBINED */
-    long long spin_limit;/* polls (about 1 us each) before a device-side wait gives up with
-                            FM_ERR_TIMEOUT; default 1<<21 (about 2 s) */
+    long long spin_limit;/* polls (at most about 0.3 us apart) before a device-side wait gives
+                            up with FM_ERR_TIMEOUT; default 1<<21 (about half a second) */
     int use_graph;       /* 1: replay the outer iteration as a captured CUDA graph (default 1) */
 } fm_opts;
 

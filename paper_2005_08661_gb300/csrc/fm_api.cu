@@ -31,7 +31,8 @@ struct fm_ctx {
     int *vlist = nullptr, *chunk_off = nullptr;
     void *w[2] = {nullptr, nullptr}, *z[2] = {nullptr, nullptr}, *g[2] = {nullptr, nullptr};
     void *d = nullptr, *p = nullptr, *v = nullptr, *ip = nullptr;
-    double *scal = nullptr, *partials = nullptr, *face = nullptr, *tile_part = nullptr;
+    double *scal = nullptr, *partials = nullptr, *tile_part = nullptr;
+    void* face = nullptr;
     double *hist_cost = nullptr, *hist_alpha = nullptr, *hist_mu = nullptr;
     int hist_cap = 0;
     int* istate = nullptr;
@@ -427,7 +428,8 @@ int fm_create(fm_ctx** out, int nx, int ny, int nz, int ncoil, int necho, const 
     A(&c->d, vb); A(&c->p, vb); A(&c->v, vb); A(&c->ip, vb);
     A(&c->scal, S_NSCAL * sizeof(double));
     A(&c->partials, std::max<size_t>(8 * (size_t)std::max(c->grid_data, c->grid_ls), nchunks) * sizeof(double));
-    A(&c->face, (size_t)c->ntiles * (64 * tz + 1024) * sizeof(double));
+    A(&c->face, (size_t)c->ntiles *
+                    (o.precision == FM_FP64 ? ic_face_bytes_per_tile<double>() : ic_face_bytes_per_tile<float>()));
     A(&c->tile_part, 2 * (size_t)c->ntiles * sizeof(double));
     A(&c->istate, I_NISTATE * sizeof(int));
     A(&c->icint, (4 + 2 * (size_t)c->ntiles) * sizeof(int));

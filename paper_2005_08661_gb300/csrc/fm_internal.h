@@ -129,7 +129,7 @@ __device__ __forceinline__ bool spin_until(const int* flag, int want, long long 
     while (ld_acquire(flag) != want) {
         if (++n > limit) return false;
         __nanosleep(ns);
-        if (ns < 1024) ns <<= 1;  // backoff capped near 1 us per poll
+        if (ns < 256) ns <<= 1;  // backoff capped at 256 ns per poll
     }
     return true;
 }
@@ -242,7 +242,7 @@ struct IcArgs {
     const void* g;         // T [nv] right-hand side
     void* v;               // T [nv] forward result
     void* ip_out;          // T [nv] inverse pivots (compute mode)
-    double* face;          // FP64 pivot faces per tile
+    void* face;            // per-tile face buffer (pivots, v, p)
     // backward
     const void* vin;       // T [nv]
     const void* ipb;       // T [nv]
@@ -266,7 +266,7 @@ template <typename T> int ls_max_blocks_per_sm(const DataArgs& a);
 template <typename T> cudaError_t launch_ic_fwd(const IcArgs& a, int grid, cudaStream_t s);
 template <typename T> cudaError_t launch_ic_bwd(const IcArgs& a, int grid, cudaStream_t s);
 template <typename T> int ic_tz();
-template <typename T> size_t ic_smem_bytes();
+template <typename T> size_t ic_face_bytes_per_tile();
 template <typename T> int ic_max_blocks_per_sm();
 
 constexpr int kThreads = 256;     // data-term / stencil kernels

@@ -32,18 +32,17 @@ __device__ __forceinline__ double wrap_angle(double t) {
     return t - 6.283185307179586476925286766559 * rint(t * 0.15915494309189533576888376337251);
 }
 
-// sin(u)/u on [-pi, pi]: Taylor series sum_k (-u^2)^k / (2k+1)! through k = 8 (truncation
-// error below pi^18 / 19! ~ 7e-9, under float resolution).
+// sin(u)/u on the wrapped interval [-pi, pi] as a degree-6 polynomial in v = u^2: the
+// discrete minimax fit derived by csrc/sinc_poly.py (truncation error 7.7e-10, below float
+// rounding; 8.9e-8 overall in float Horner form).
 __device__ __forceinline__ float sinc_wrapped(float u) {
     const float v = u * u;
-    float p = 2.81145725434552076e-15f;     //  1/17!
-    p = fmaf(p, v, -7.64716373181981647e-13f);  // -1/15!
-    p = fmaf(p, v, 1.60590438368216146e-10f);   //  1/13!
-    p = fmaf(p, v, -2.50521083854417188e-08f);  // -1/11!
-    p = fmaf(p, v, 2.75573192239858907e-06f);   //  1/9!
-    p = fmaf(p, v, -1.98412698412698413e-04f);  // -1/7!
-    p = fmaf(p, v, 8.33333333333333333e-03f);   //  1/5!
-    p = fmaf(p, v, -1.66666666666666667e-01f);  // -1/3!
+    float p = 1.360021817387036e-10f;
+    p = fmaf(p, v, -2.4725343550358048e-08f);
+    p = fmaf(p, v, 2.753550461420673e-06f);
+    p = fmaf(p, v, -0.00019840517779812217f);
+    p = fmaf(p, v, 0.00833332072943449f);
+    p = fmaf(p, v, -0.1666666567325592f);
     return fmaf(p, v, 1.0f);
 }
 __device__ __forceinline__ double sinc_wrapped(double u) { return u == 0.0 ? 1.0 : sin(u) / u; }
@@ -115,6 +114,71 @@ __device__ __forceinline__ void eval_voxel(const DataArgs& a, long long j /* com
     curv = T(2) * d_acc;
 }
 
+// Same as eval_voxel for a compile-time echo count L: the pair loop is unrolled and every
+// pair and coil value of the voxel is loaded before the arithmetic starts.
+template <typename T, int NC, int L, bool COST, bool CURV>
+__device__ __forceinline__ void eval_voxel_fixed(const DataArgs& a, long long j /* compact index */, T w,
+                                                 T& cost, T& grad, T& curv) {
+    using T2 = typename V2<T>::t;
+    constexpr int P = L * (L - 1) / 2;
+    constexpr int NCL = (CURV && NC > 1) ? NC : 1;
+    const long long nv = a.geo.nv;
+    const T2* pairs = (const T2*)a.pairs;
+    const T2* coils = (const T2*)a.coils;
+    T2 R[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) R[p] = pairs[(size_t)p * nv + j];
+    T2 W[L][NCL];
+    if (CURV && NC > 1) {
+#pragma unroll
+        for (int m = 0; m < L; ++m)
+#pragma unroll
+            for (int c = 0; c < NCL; ++c) W[m][c] = coils[((size_t)m * NC + c) * nv + j];
+    }
+    T c_acc = 0, g_acc = 0, d_acc = 0;
+    int p = 0;
+#pragma unroll
+    for (int m = 0; m < L; ++m) {
+#pragma unroll
+        for (int n = m + 1; n < L; ++n, ++p) {
+            const T dt = (T)a.pr.dt[p];
+            const T th = R[p].y + w * dt;
+            T s, c;
+            sin_cos(th * T(0.5), &s, &c);
+            if (COST) c_acc += R[p].x * (s * s);
+            g_acc += dt * R[p].x * (s * c);
+            if (CURV) {
+                if (NC == 1) {
+                    d_acc += dt * dt * R[p].x * sinc_wrapped(wrap_angle(th));
+                } else {
+                    T psi[NCL];
+#pragma unroll
+                    for (int dd = 0; dd < NCL; ++dd) psi[dd] = W[n][dd].y + w * dt;
+                    T inner = 0;
+#pragma unroll
+                    for (int cc = 0; cc < NCL; ++cc) {
+                        T acc = 0;
+#pragma unroll
+                        for (int dd = 0; dd < NCL; ++dd) acc += W[n][dd].x * sinc_wrapped(wrap_angle(psi[dd] - W[m][cc].y));
+                        inner += W[m][cc].x * acc;
+                    }
+                    d_acc += dt * dt * inner;
+                }
+            }
+        }
+    }
+    cost = T(4) * c_acc;
+    grad = T(4) * g_acc;
+    curv = T(2) * d_acc;
+}
+
+// Dispatch to the unrolled three-echo path when it applies.
+template <typename T, int NC, bool COST, bool CURV>
+__device__ __forceinline__ void eval_any(const DataArgs& a, long long j, T w, T& cost, T& grad, T& curv) {
+    if (NC != 0 && a.L == 3) eval_voxel_fixed<T, (NC == 0 ? 1 : NC), 3, COST, CURV>(a, j, w, cost, grad, curv);
+    else eval_voxel<T, NC, COST, CURV>(a, j, w, cost, grad, curv);
+}
+
 // ------------------------------------------------------------------ gradient pass
 
 // w_out = w_in + alpha z (the previous iteration's update, Algorithm box), then at w_out:
@@ -150,7 +214,7 @@ __global__ void __launch_bounds__(kThreads) k_grad(DataArgs a) {
         if (b & NB_YP) { const T e = wj - upd(j + nx); lap += e; reg += e * e; }
         if (b & NB_ZP) { const T e = wj - upd(j + nxy); lap += e; reg += e * e; }
         T cst, gr, cu;
-        eval_voxel<T, NC, true, true>(a, k, wj, cst, gr, cu);
+        eval_any<T, NC, true, true>(a, k, wj, cst, gr, cu);
         if (g) g[j] = gr + beta * lap;
         if (d) d[j] = cu;
         acc += (double)cst + 0.5 * a.beta * (double)reg;
@@ -248,18 +312,19 @@ __global__ void __launch_bounds__(kThreads) k_ls(DataArgs a) {
     const long long nm = a.istate[I_NMASK];
     for (int step = 1; step < a.nls; ++step) {
         const T aT = (T)alpha;
-        double s1 = 0.0, s2 = 0.0;
+        // each thread sums its few voxels in the voxel type, then the block and the grid in FP64
+        T t1 = 0, t2 = 0;
         for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nm;
              k += (long long)gridDim.x * blockDim.x) {
             const long long j = a.vlist[k];
             const T zj = z[j];
             if (zj == T(0)) continue;
             T cst, gr, cu;
-            eval_voxel<T, NC, false, true>(a, k, w[j] + aT * zj, cst, gr, cu);
-            s1 += (double)(zj * gr);
-            s2 += (double)(zj * zj * cu);
+            eval_any<T, NC, false, true>(a, k, w[j] + aT * zj, cst, gr, cu);
+            t1 += zj * gr;
+            t2 += zj * zj * cu;
         }
-        double v[2] = {s1, s2};
+        double v[2] = {(double)t1, (double)t2};
         block_sum<2>(v, sbuf);
         double* part = a.partials + 4 * (size_t)nb + (size_t)(step & 1) * 2 * nb;
         if (threadIdx.x == 0) {

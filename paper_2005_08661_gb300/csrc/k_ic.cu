@@ -13,105 +13,102 @@
 // all grid neighbours: an outside neighbour contributes exactly 0.
 //
 // Parallel schedule: voxel (x, y, z) depends on (x-1, y, z), (x, y-1, z), (x, y, z-1), so
-// every hyperplane x + y + z = const is independent.  The grid is cut into 32 x 32 x 8
+// every hyperplane x + y + z = const is independent.  The grid is cut into 32 x 32 x TZ
 // tiles; a CTA claims tiles through an atomic ticket in a dependency-respecting order (a
 // tile's predecessors always hold smaller tickets, so no co-residency is assumed), starts
 // the asynchronous copy of the tile's inputs into shared memory, waits on the predecessors'
-// ready flags (bounded spin), and sweeps the tile's 70 local hyperplanes: lane = y,
+// ready flags (bounded spin), and sweeps the tile's 62 + TZ local hyperplanes: lane = y,
 // warp = z, and each thread walks its x row one step per hyperplane, taking the -y value
 // from the neighbouring lane by shuffle, the -z value from the warp below through shared
-// memory and the -x value from its own register.  Outputs are written back row-coalesced
-// and the tile's flag is released before the back sweep's dot products.
+// memory and the -x value from its own register.  The values on the tile's three outgoing
+// faces go to a per-tile face buffer as they are produced, so a tile is released right after
+// its sweep; the row-coalesced write-back of the whole tile follows.
 //
-// Pivot arithmetic: FP64 mode uses IEEE double.  FP32 mode carries the pivot recurrence
-// in double-float (an unevaluated sum hi + lo of two floats, about 46 significant bits)
-// on the FP32 pipes, because the GB300 FP64 pipe issues at about 1/64 of the FP32 rate and
-// sits on the sweep's critical path; the solves themselves run in float.
+// Pivot arithmetic.  FP64 mode uses IEEE double.  FP32 mode carries each inverse pivot as
+// an unevaluated pair a + b of floats (about 46 significant bits, like double-float), but
+// arranged so that the hi part a is exactly the float recurrence a_j = 1/fl(H - beta^2 sum a_k)
+// -- a short dependency chain -- while b, the first-order correction, is formed from
+// error-free residuals (two-sum / two-product) of that chain and the neighbours' b:
+//   pi = pi_f + dpi,  dpi = (rounding residuals of pi_f) + H_lo - beta^2 (sum b_k + sum errors),
+//   1/pi = a (1 + e_r - dpi a) + O(eps^2),  e_r = 1 - pi_f a  (exact by FMA),
+// so b = a (e_r - dpi a) with a relative truncation of order (dpi/pi)^2 ~ 1e-14.  The GB300
+// FP64 pipe issues at about 1/64 of the FP32 rate and would sit on the sweep's critical path.
 #include "fm_internal.h"
 
 namespace fm {
 
-constexpr int kTZ = 8;
-constexpr int kRows = kTZ * 32;  // rows of 32 x-values per tile (== threads per CTA)
-constexpr int kFaceN = 32 * kTZ + 32 * kTZ + 32 * 32;  // pivot values per tile: +x, +y, +z faces
+// ------------------------------------------------------------------ split pivot (FP32 mode)
 
-// ------------------------------------------------------------------ double-float
-
-struct DF {
-    float hi, lo;
+struct PF {
+    float a, b;  // inverse pivot = a + b
 };
 
-__device__ __forceinline__ DF df_two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return {s, e};
-}
-__device__ __forceinline__ DF df_quick(float a, float b) {  // requires |a| >= |b| or a == 0
-    const float s = __fadd_rn(a, b);
-    return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ DF df_add(DF x, DF y) {
-    const DF s = df_two_sum(x.hi, y.hi);
-    const DF t = df_two_sum(x.lo, y.lo);
-    DF u = df_quick(s.hi, __fadd_rn(s.lo, t.hi));
-    return df_quick(u.hi, __fadd_rn(u.lo, t.lo));
-}
-__device__ __forceinline__ DF df_mul(DF x, DF y) {
-    const float p = __fmul_rn(x.hi, y.hi);
-    float e = __fmaf_rn(x.hi, y.hi, -p);
-    e = __fmaf_rn(x.hi, y.lo, e);
-    e = __fmaf_rn(x.lo, y.hi, e);
-    return df_quick(p, e);
-}
-__device__ __forceinline__ DF df_from(double v) {
-    const float hi = (float)v;
-    return {hi, (float)(v - (double)hi)};
-}
-__device__ __forceinline__ DF df_neg(DF x) { return {-x.hi, -x.lo}; }
-// 1/x by one Newton step on the float reciprocal, carried in double-float
-__device__ __forceinline__ DF df_recip(DF x) {
-    const float r = __frcp_rn(x.hi);
-    // e = 1 - x r exactly enough: x.hi r + x.lo r in double-float
-    const float p = __fmul_rn(x.hi, r);
-    float pe = __fmaf_rn(x.hi, r, -p);
-    pe = __fmaf_rn(x.lo, r, pe);
-    const DF xr = df_quick(p, pe);
-    const DF e = df_add({1.0f, 0.0f}, df_neg(xr));
-    return df_add({r, 0.0f}, df_mul({r, 0.0f}, e));
+__device__ __forceinline__ void two_sum(float x, float y, float& s, float& e) {
+    s = __fadd_rn(x, y);
+    const float bb = __fsub_rn(s, x);
+    e = __fadd_rn(__fsub_rn(x, __fsub_rn(s, bb)), __fsub_rn(y, bb));
 }
 
-// Pivot arithmetic per precision mode: P is the carried type (double or DF, 8 bytes).
+struct PivScal {     // beta-derived constants of the pivot recurrence
+    float bh, bl;    // beta = bh + bl
+    float b2h, b2l;  // beta^2 = b2h + b2l
+};
+
 template <typename T> struct PivOps;
 template <> struct PivOps<double> {
     using P = double;
     static __device__ __forceinline__ P zero() { return 0.0; }
-    static __device__ __forceinline__ P add(P a, P b) { return a + b; }
-    // H_jj - beta^2 s with H_jj = d + beta n; returns 1/pi and whether pi > 0
-    static __device__ __forceinline__ P inv_pivot(double d, int n, double beta, P s, bool& ok) {
-        const double piv = d + beta * (double)n - beta * beta * s;
+    static __device__ __forceinline__ double hi(P x) { return x; }
+    // 1/pi_j from H_jj = d + beta n and the lower neighbours' inverse pivots
+    static __device__ __forceinline__ P inv_pivot(double d, int n, double beta, const PivScal&, P x, P y, P z,
+                                                  bool& ok) {
+        const double piv = d + beta * (double)n - beta * beta * ((x + y) + z);
         ok = piv > 0.0;
         return ok ? 1.0 / piv : 0.0;
     }
-    static __device__ __forceinline__ double to_T(P x) { return x; }
 };
 template <> struct PivOps<float> {
-    using P = DF;
+    using P = PF;
     static __device__ __forceinline__ P zero() { return {0.0f, 0.0f}; }
-    static __device__ __forceinline__ P add(P a, P b) { return df_add(a, b); }
-    static __device__ __forceinline__ P inv_pivot(float d, int n, double beta, P s, bool& ok) {
-        const DF b = df_from(beta), b2 = df_from(beta * beta);
-        const DF h = df_add({d, 0.0f}, df_mul(b, {(float)n, 0.0f}));
-        const DF piv = df_add(h, df_neg(df_mul(b2, s)));
-        ok = piv.hi > 0.0f;
-        return ok ? df_recip(piv) : DF{0.0f, 0.0f};
+    static __device__ __forceinline__ float hi(P x) { return x.a; }
+    static __device__ __forceinline__ P inv_pivot(float d, int n, double, const PivScal& c, P x, P y, P z,
+                                                  bool& ok) {
+        // H = d + beta n as hH + hL (n <= 6, so bh * n is exact up to one rounding)
+        const float fn = (float)n;
+        const float bn = __fmul_rn(c.bh, fn);
+        const float bn_e = __fmaf_rn(c.bh, fn, -bn);
+        float hH, hE;
+        two_sum(d, bn, hH, hE);
+        const float hL = __fadd_rn(hE, __fmaf_rn(c.bl, fn, bn_e));
+        // hi chain: S = (a_x + a_y) + a_z, pi_f = hH - b2h S, a = 1/pi_f
+        float s1, e1, S, e2;
+        two_sum(x.a, y.a, s1, e1);
+        two_sum(s1, z.a, S, e2);
+        const float th = __fmul_rn(c.b2h, S);
+        const float tl = __fmaf_rn(c.b2h, S, -th);
+        float pf, pe;
+        two_sum(hH, -th, pf, pe);
+        ok = pf > 0.0f;
+        if (!ok) return {0.0f, 0.0f};
+        const float a = __frcp_rn(pf);
+        const float er = __fmaf_rn(-pf, a, 1.0f);
+        // lo: dpi = pe + hL - tl - b2l S - b2h (e1 + e2 + sum b)
+        const float base = __fsub_rn(__fadd_rn(pe, hL), __fmaf_rn(c.b2l, S, tl));
+        const float sb = __fadd_rn(__fadd_rn(__fadd_rn(x.b, y.b), z.b), __fadd_rn(e1, e2));
+        const float dpi = __fmaf_rn(-c.b2h, sb, base);
+        const float b = __fmul_rn(a, __fmaf_rn(-dpi, a, er));
+        return {a, b};
     }
-    static __device__ __forceinline__ float to_T(P x) { return x.hi; }
 };
 
-// Pivot faces are written by other CTAs of the same launch: read them through L2.
-__device__ __forceinline__ double ld_face(const double* p) { return __ldcg(p); }
-__device__ __forceinline__ DF ld_face(const DF* p) {
+__device__ __forceinline__ double shfl_up(double v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ PF shfl_up(PF v) {
+    return {__shfl_up_sync(0xffffffffu, v.a, 1), __shfl_up_sync(0xffffffffu, v.b, 1)};
+}
+// Faces are written by other CTAs of the same launch: read them through L2.
+__device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ float ld_cg(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ PF ld_cg(const PF* p) {
     const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
     return {v.x, v.y};
 }
@@ -134,8 +131,8 @@ __device__ __forceinline__ void cp_wait_all() {
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
-// Start copying this thread's row (ly, lz) = (r & 31, r >> 5) of a T tile into s[r * 32 ..];
-// elements outside the grid are filled with `fill`.
+// Start copying row r = (ly, lz) = (r & 31, r >> 5) of a T tile into s[r * 32 ..]; elements
+// outside the grid are filled with `fill`.
 template <typename T>
 __device__ __forceinline__ void stage_row(T* s, const T* g, int r, int x0, int y0, int z0, const Geo& geo,
                                           T fill) {
@@ -188,34 +185,52 @@ __device__ __forceinline__ void stage_row_u8(uint8_t* s, const uint8_t* g, int r
     }
 }
 
+// ------------------------------------------------------------------ tile geometry per precision
+
+template <typename T> struct Tile;
+template <> struct Tile<float> { static constexpr int TZ = 16; };   // 512 threads
+template <> struct Tile<double> { static constexpr int TZ = 8; };   // 256 threads
+
+// Face layout per tile (counts of values): +x face [TZ][32] (lz, ly), +y face [TZ][32]
+// (lz, lx), +z face [32][32] (ly, lx).
+template <int TZ> struct FaceN {
+    static constexpr int x = 0, y = TZ * 32, z = 2 * TZ * 32, n = 2 * TZ * 32 + 1024;
+};
+
 template <typename T>
 struct FwdSmem {
+    static constexpr int TZ = Tile<T>::TZ;
     using P = typename PivOps<T>::P;
-    static constexpr size_t bytes = 2 * kRows * 32 * sizeof(T) + (kTZ * 32 * 2 + 1024 + 2 * kTZ * 32) * sizeof(P) +
-                                    (kTZ * 32 * 2 + 1024 + 2 * kTZ * 32) * sizeof(T) + kRows * 32;
+    static constexpr int nface = FaceN<TZ>::n + 2 * TZ * 32;  // faces in + z exchange
+    static constexpr size_t bytes = 2 * TZ * 1024 * sizeof(T) + nface * (sizeof(P) + sizeof(T)) + TZ * 1024;
 };
 template <typename T>
 struct BwdSmem {
-    static constexpr size_t bytes = 2 * kRows * 32 * sizeof(T) + (kTZ * 32 * 2 + 1024 + 2 * kTZ * 32) * sizeof(T);
+    static constexpr int TZ = Tile<T>::TZ;
+    static constexpr size_t bytes = 2 * TZ * 1024 * sizeof(T) + (FaceN<TZ>::n + 2 * TZ * 32) * sizeof(T);
 };
+
+// Per-tile face buffer (device): forward pivots [P][n], forward v [T][n], backward p [T][n].
+template <typename T>
+__host__ __device__ constexpr size_t face_bytes_per_tile() {
+    return (size_t)FaceN<Tile<T>::TZ>::n * (sizeof(typename PivOps<T>::P) + 2 * sizeof(T));
+}
 
 // mode 0: pivots from d (factor + forward); mode 1: stored 1/pi (forward only)
 template <typename T>
-__global__ void __launch_bounds__(32 * kTZ) k_ic_fwd(IcArgs a, int mode) {
+__global__ void __launch_bounds__(32 * Tile<T>::TZ) k_ic_fwd(IcArgs a, int mode, PivScal pc) {
+    constexpr int TZ = Tile<T>::TZ;
+    using FN = FaceN<TZ>;
     using Ops = PivOps<T>;
     using P = typename Ops::P;
     extern __shared__ __align__(16) unsigned char smem[];
-    T* sg = (T*)smem;                              // [kTZ][32][32]: g, then v
-    T* sd = sg + kRows * 32;                       // d (or stored 1/pi), then 1/pi
-    P* fx_ip = (P*)(sd + kRows * 32);              // [kTZ][32] (lz, ly)
-    P* fy_ip = fx_ip + kTZ * 32;                   // [kTZ][32] (lz, lx)
-    P* fz_ip = fy_ip + kTZ * 32;                   // [32][32]  (ly, lx)
-    P* zb_ip = fz_ip + 1024;                       // [2][kTZ][32]
-    T* fx_v = (T*)(zb_ip + 2 * kTZ * 32);
-    T* fy_v = fx_v + kTZ * 32;
-    T* fz_v = fy_v + kTZ * 32;
-    T* zb_v = fz_v + 1024;
-    uint8_t* snb = (uint8_t*)(zb_v + 2 * kTZ * 32);  // [kTZ][32][32]
+    T* sg = (T*)smem;                              // [TZ][32][32]: g, then v
+    T* sd = sg + TZ * 1024;                        // d (or stored 1/pi), then 1/pi
+    P* f_ip = (P*)(sd + TZ * 1024);                // incoming faces: x, y, z
+    P* zb_ip = f_ip + FN::n;                       // [2][TZ][32]
+    T* f_v = (T*)(zb_ip + 2 * TZ * 32);
+    T* zb_v = f_v + FN::n;
+    uint8_t* snb = (uint8_t*)(zb_v + 2 * TZ * 32); // [TZ][32][32]
     __shared__ int s_tile;
 
     const Geo geo = a.geo;
@@ -227,8 +242,10 @@ __global__ void __launch_bounds__(32 * kTZ) k_ic_fwd(IcArgs a, int mode) {
     const T* ipin = (const T*)a.ip_in;
     T* v = (T*)a.v;
     T* ipo = (T*)a.ip_out;
-    P* face = (P*)a.face;
+    unsigned char* faceb = (unsigned char*)a.face;
     const T betaT = (T)a.beta;
+    auto face_ip = [&](int t) { return (P*)(faceb + (size_t)t * face_bytes_per_tile<T>()); };
+    auto face_v = [&](int t) { return (T*)(face_ip(t) + FN::n); };
 
     for (;;) {
         if (tid == 0) {
@@ -239,7 +256,7 @@ __global__ void __launch_bounds__(32 * kTZ) k_ic_fwd(IcArgs a, int mode) {
         const int tile = s_tile;
         if (tile < 0) break;
         const int X = tile % a.ntx, Y = (tile / a.ntx) % a.nty, Z = tile / (a.ntx * a.nty);
-        const int x0 = X * 32, y0 = Y * 32, z0 = Z * kTZ;
+        const int x0 = X * 32, y0 = Y * 32, z0 = Z * TZ;
 
         // start the copies of this tile's inputs (they do not depend on other tiles)
         stage_row<T>(sg, g, tid, x0, y0, z0, geo, T(0));
@@ -252,42 +269,22 @@ __global__ void __launch_bounds__(32 * kTZ) k_ic_fwd(IcArgs a, int mode) {
             if (Y > 0) ok = spin_until(a.flags + tile - a.ntx, 1, a.spin_limit) && ok;
             if (Z > 0) ok = spin_until(a.flags + tile - a.ntx * a.nty, 1, a.spin_limit) && ok;
             if (!ok) set_err(a.istate, FM_ERR_TIMEOUT);
-            __threadfence();
         }
         __syncthreads();
-        // faces produced by the neighbour tiles in this launch (read through L2): thread tid
-        // owns x-face and y-face entry tid and z-face entries tid + 256 q
-        {
-            const int hi = tid >> 5, lo = tid & 31;
-            P ipx = Ops::zero(), ipy = Ops::zero(), ipz[4];
-            T vx = 0, vy = 0, vz[4];
-            if (X > 0 && y0 + lo < ny && z0 + hi < nz) {
-                vx = __ldcg(v + (long long)(z0 + hi) * nxy + (long long)(y0 + lo) * nx + (x0 - 1));
-                if (mode == 0) ipx = ld_face(face + (size_t)(tile - 1) * kFaceN + tid);
+        // incoming faces: the neighbours' outgoing +x, +y, +z faces
+        for (int i = tid; i < FN::n; i += 32 * TZ) {
+            P ip = Ops::zero();
+            T vv = 0;
+            int src = -1;
+            if (i < FN::y) { if (X > 0) src = tile - 1; }
+            else if (i < FN::z) { if (Y > 0) src = tile - a.ntx; }
+            else if (Z > 0) src = tile - a.ntx * a.nty;
+            if (src >= 0) {
+                vv = ld_cg(face_v(src) + i);
+                if (mode == 0) ip = ld_cg(face_ip(src) + i);
             }
-            if (Y > 0 && x0 + lo < nx && z0 + hi < nz) {
-                vy = __ldcg(v + (long long)(z0 + hi) * nxy + (long long)(y0 - 1) * nx + (x0 + lo));
-                if (mode == 0) ipy = ld_face(face + (size_t)(tile - a.ntx) * kFaceN + 32 * kTZ + tid);
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int i = tid + 256 * q, ly = i >> 5, lx = i & 31;
-                ipz[q] = Ops::zero();
-                vz[q] = 0;
-                if (Z > 0 && x0 + lx < nx && y0 + ly < ny) {
-                    vz[q] = __ldcg(v + (long long)(z0 - 1) * nxy + (long long)(y0 + ly) * nx + (x0 + lx));
-                    if (mode == 0) ipz[q] = ld_face(face + (size_t)(tile - a.ntx * a.nty) * kFaceN + 64 * kTZ + i);
-                }
-            }
-            fx_ip[tid] = ipx;
-            fx_v[tid] = vx;
-            fy_ip[tid] = ipy;
-            fy_v[tid] = vy;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                fz_ip[tid + 256 * q] = ipz[q];
-                fz_v[tid + 256 * q] = vz[q];
-            }
+            f_ip[i] = ip;
+            f_v[i] = vv;
         }
         cp_wait_all();
         __syncthreads();
@@ -297,88 +294,77 @@ __global__ void __launch_bounds__(32 * kTZ) k_ic_fwd(IcArgs a, int mode) {
         P out_ip = Ops::zero();
         T out_v = 0;
         bool bad = false;
-        P* myface = face + (size_t)tile * kFaceN;
-        for (int s = 0; s < 64 + kTZ - 2; ++s) {
-            P up_ip;
-            if constexpr (sizeof(P) == 8 && sizeof(T) == 8) {
-                up_ip = __shfl_up_sync(0xffffffffu, out_ip, 1);
-            } else {
-                DF o = *reinterpret_cast<DF*>(&out_ip);
-                DF u{__shfl_up_sync(0xffffffffu, o.hi, 1), __shfl_up_sync(0xffffffffu, o.lo, 1)};
-                up_ip = *reinterpret_cast<P*>(&u);
-            }
+        P* oip = face_ip(tile);
+        T* ov = face_v(tile);
+        for (int s = 0; s < 62 + TZ; ++s) {
+            const P up_ip = shfl_up(out_ip);
             const T up_v = __shfl_up_sync(0xffffffffu, out_v, 1);
             const int lx = s - ly - lz;
             if (lx >= 0 && lx < 32) {
                 const int i = (lz * 32 + ly) * 32 + lx;
+                const int q = ((s - 1) & 1) * TZ * 32 + (lz > 0 ? lz - 1 : 0) * 32 + ly;
+                const P xip = lx == 0 ? f_ip[FN::x + lz * 32 + ly] : out_ip;
+                const T xv = lx == 0 ? f_v[FN::x + lz * 32 + ly] : out_v;
+                const P yip = ly == 0 ? f_ip[FN::y + lz * 32 + lx] : up_ip;
+                const T yv = ly == 0 ? f_v[FN::y + lz * 32 + lx] : up_v;
+                const P zip = lz == 0 ? f_ip[FN::z + ly * 32 + lx] : zb_ip[q];
+                const T zv = lz == 0 ? f_v[FN::z + ly * 32 + lx] : zb_v[q];
                 P ipj = Ops::zero();
                 T vj = 0;
-                const P xip = lx == 0 ? fx_ip[lz * 32 + ly] : out_ip;
-                const T xv = lx == 0 ? fx_v[lz * 32 + ly] : out_v;
-                const P yip = ly == 0 ? fy_ip[lz * 32 + lx] : up_ip;
-                const T yv = ly == 0 ? fy_v[lz * 32 + lx] : up_v;
-                const int q = ((s - 1) & 1) * kTZ * 32 + (lz - 1) * 32 + ly;
-                const P zip = lz == 0 ? fz_ip[ly * 32 + lx] : zb_ip[q];
-                const T zv = lz == 0 ? fz_v[ly * 32 + lx] : zb_v[q];
                 if (mode == 0) {
                     const uint8_t b = snb[i];
                     if (b & NB_IN) {
                         bool ok;
-                        ipj = Ops::inv_pivot(sd[i], __popc((unsigned)(b >> 1) & 0x3fu), a.beta,
-                                             Ops::add(Ops::add(xip, yip), zip), ok);
+                        ipj = Ops::inv_pivot(sd[i], __popc((unsigned)(b >> 1) & 0x3fu), a.beta, pc, xip, yip, zip, ok);
                         bad |= !ok;
-                        vj = (sg[i] + betaT * ((xv + yv) + zv)) * (T)Ops::to_T(ipj);
+                        vj = (sg[i] + betaT * ((xv + yv) + zv)) * (T)Ops::hi(ipj);
                     }
-                    sd[i] = (T)Ops::to_T(ipj);
+                    sd[i] = (T)Ops::hi(ipj);
                 } else {
-                    const T ipt = sd[i];
-                    vj = (sg[i] + betaT * ((xv + yv) + zv)) * ipt;
+                    vj = (sg[i] + betaT * ((xv + yv) + zv)) * sd[i];
                 }
                 sg[i] = vj;
                 out_ip = ipj;
                 out_v = vj;
-                zb_ip[(s & 1) * kTZ * 32 + lz * 32 + ly] = ipj;
-                zb_v[(s & 1) * kTZ * 32 + lz * 32 + ly] = vj;
-                if (mode == 0) {
-                    if (lx == 31) myface[lz * 32 + ly] = ipj;
-                    if (ly == 31) myface[32 * kTZ + lz * 32 + lx] = ipj;
-                    if (lz == kTZ - 1) myface[64 * kTZ + ly * 32 + lx] = ipj;
-                }
+                zb_ip[(s & 1) * TZ * 32 + lz * 32 + ly] = ipj;
+                zb_v[(s & 1) * TZ * 32 + lz * 32 + ly] = vj;
+                if (lx == 31) { oip[FN::x + lz * 32 + ly] = ipj; ov[FN::x + lz * 32 + ly] = vj; }
+                if (ly == 31) { oip[FN::y + lz * 32 + lx] = ipj; ov[FN::y + lz * 32 + lx] = vj; }
+                if (lz == TZ - 1) { oip[FN::z + ly * 32 + lx] = ipj; ov[FN::z + ly * 32 + lx] = vj; }
             }
             __syncthreads();
         }
         if (bad) set_err(a.istate, FM_ERR_NOT_PD);
-
-        // write back row-coalesced (warp lz writes its 32 rows, lane = x), then publish
-        {
-            const int nvalid = min(32, nx - x0);
-            const int z = z0 + wz;
-            if (z < nz && lane < nvalid) {
-                for (int ly2 = 0; ly2 < 32 && y0 + ly2 < ny; ++ly2) {
-                    const long long j = (long long)z * nxy + (long long)(y0 + ly2) * nx + x0 + lane;
-                    const int i = (wz * 32 + ly2) * 32 + lane;
-                    v[j] = sg[i];
-                    if (mode == 0 && ipo) ipo[j] = sd[i];
-                }
-            }
-        }
-        __syncthreads();
+        // publish: the successors read only the face buffer
         if (tid == 0) {
             __threadfence();
             st_release(a.flags + tile, 1);
         }
+        // write back row-coalesced (warp lz writes its 32 rows, lane = x)
+        const int nvalid = min(32, nx - x0);
+        const int z = z0 + wz;
+        if (z < nz && lane < nvalid) {
+            for (int ly2 = 0; ly2 < 32 && y0 + ly2 < ny; ++ly2) {
+                const long long j = (long long)z * nxy + (long long)(y0 + ly2) * nx + x0 + lane;
+                const int i = (wz * 32 + ly2) * 32 + lane;
+                v[j] = sg[i];
+                if (mode == 0 && ipo) ipo[j] = sd[i];
+            }
+        }
+        __syncthreads();
     }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(32 * kTZ) k_ic_bwd(IcArgs a) {
+__global__ void __launch_bounds__(32 * Tile<T>::TZ) k_ic_bwd(IcArgs a) {
+    constexpr int TZ = Tile<T>::TZ;
+    using FN = FaceN<TZ>;
+    using P = typename PivOps<T>::P;
     extern __shared__ __align__(16) unsigned char smem[];
-    T* sv = (T*)smem;                 // [kTZ][32][32]: v, then p
-    T* sip = sv + kRows * 32;         // 1/pi
-    T* fx = sip + kRows * 32;         // [kTZ][32] (lz, ly) p at x0 + 32
-    T* fy = fx + kTZ * 32;            // [kTZ][32] (lz, lx) p at y0 + 32
-    T* fz = fy + kTZ * 32;            // [32][32] (ly, lx) p at z0 + kTZ
-    T* zb = fz + 1024;                // [2][kTZ][32]
+    T* sv = (T*)smem;                 // [TZ][32][32]: v, then p
+    T* sip = sv + TZ * 1024;          // 1/pi
+    T* f_p = sip + TZ * 1024;         // incoming faces (the successors' -x, -y, -z faces)
+    T* zb = f_p + FN::n;              // [2][TZ][32]
     __shared__ int s_tile;
     __shared__ bool s_last;
     __shared__ double sbuf[2 * 32];
@@ -393,6 +379,11 @@ __global__ void __launch_bounds__(32 * kTZ) k_ic_bwd(IcArgs a) {
     const T* gd = (const T*)a.gdot;
     const T* gpd = (const T*)a.gpdot;
     const T beta = (T)a.beta;
+    unsigned char* faceb = (unsigned char*)a.face;
+    // backward faces live after the forward pivot and v faces of each tile
+    auto face_p = [&](int t) {
+        return (T*)(faceb + (size_t)t * face_bytes_per_tile<T>() + (size_t)FN::n * (sizeof(P) + sizeof(T)));
+    };
 
     for (;;) {
         if (tid == 0) {
@@ -403,7 +394,7 @@ __global__ void __launch_bounds__(32 * kTZ) k_ic_bwd(IcArgs a) {
         const int tile = s_tile;
         if (tile < 0) break;
         const int X = tile % a.ntx, Y = (tile / a.ntx) % a.nty, Z = tile / (a.ntx * a.nty);
-        const int x0 = X * 32, y0 = Y * 32, z0 = Z * kTZ;
+        const int x0 = X * 32, y0 = Y * 32, z0 = Z * TZ;
 
         stage_row<T>(sv, vin, tid, x0, y0, z0, geo, T(0));
         stage_row<T>(sip, ipb, tid, x0, y0, z0, geo, T(0));
@@ -413,72 +404,63 @@ __global__ void __launch_bounds__(32 * kTZ) k_ic_bwd(IcArgs a) {
             if (Y + 1 < a.nty) ok = spin_until(a.flags + tile + a.ntx, 1, a.spin_limit) && ok;
             if (Z + 1 < a.ntz) ok = spin_until(a.flags + tile + a.ntx * a.nty, 1, a.spin_limit) && ok;
             if (!ok) set_err(a.istate, FM_ERR_TIMEOUT);
-            __threadfence();
         }
         __syncthreads();
-        {
-            const int hi = tid >> 5, lo = tid & 31;
-            T qx = 0, qy = 0, qz[4];
-            if (X + 1 < a.ntx && y0 + lo < ny && z0 + hi < nz)
-                qx = __ldcg(p + (long long)(z0 + hi) * nxy + (long long)(y0 + lo) * nx + (x0 + 32));
-            if (Y + 1 < a.nty && x0 + lo < nx && z0 + hi < nz)
-                qy = __ldcg(p + (long long)(z0 + hi) * nxy + (long long)(y0 + 32) * nx + (x0 + lo));
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int i = tid + 256 * q, ly = i >> 5, lx = i & 31;
-                qz[q] = 0;
-                if (Z + 1 < a.ntz && x0 + lx < nx && y0 + ly < ny)
-                    qz[q] = __ldcg(p + (long long)(z0 + kTZ) * nxy + (long long)(y0 + ly) * nx + (x0 + lx));
-            }
-            fx[tid] = qx;
-            fy[tid] = qy;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) fz[tid + 256 * q] = qz[q];
+        // incoming faces: the +x / +y / +z neighbours' outgoing low faces (lx = 0, ly = 0, lz = 0)
+        for (int i = tid; i < FN::n; i += 32 * TZ) {
+            T q = 0;
+            int src = -1;
+            if (i < FN::y) { if (X + 1 < a.ntx) src = tile + 1; }
+            else if (i < FN::z) { if (Y + 1 < a.nty) src = tile + a.ntx; }
+            else if (Z + 1 < a.ntz) src = tile + a.ntx * a.nty;
+            if (src >= 0) q = ld_cg(face_p(src) + i);
+            f_p[i] = q;
         }
         cp_wait_all();
         __syncthreads();
 
         const int ly = lane, lz = wz;
         T out = 0;
-        for (int s = 64 + kTZ - 3; s >= 0; --s) {
+        T* op = face_p(tile);
+        for (int s = 61 + TZ; s >= 0; --s) {
             const T dn = __shfl_down_sync(0xffffffffu, out, 1);
             const int lx = s - ly - lz;
             if (lx >= 0 && lx < 32) {
                 const int i = (lz * 32 + ly) * 32 + lx;
-                const T px = lx == 31 ? fx[lz * 32 + ly] : out;
-                const T py = ly == 31 ? fy[lz * 32 + lx] : dn;
-                const T pz = lz == kTZ - 1 ? fz[ly * 32 + lx] : zb[((s + 1) & 1) * kTZ * 32 + (lz + 1) * 32 + ly];
+                const T px = lx == 31 ? f_p[FN::x + lz * 32 + ly] : out;
+                const T py = ly == 31 ? f_p[FN::y + lz * 32 + lx] : dn;
+                const T pz = lz == TZ - 1 ? f_p[FN::z + ly * 32 + lx]
+                                          : zb[((s + 1) & 1) * TZ * 32 + (lz < TZ - 1 ? lz + 1 : lz) * 32 + ly];
                 const T pj = sv[i] + beta * sip[i] * ((px + py) + pz);
                 sv[i] = pj;
                 out = pj;
-                zb[(s & 1) * kTZ * 32 + lz * 32 + ly] = pj;
+                zb[(s & 1) * TZ * 32 + lz * 32 + ly] = pj;
+                if (lx == 0) op[FN::x + lz * 32 + ly] = pj;
+                if (ly == 0) op[FN::y + lz * 32 + lx] = pj;
+                if (lz == 0) op[FN::z + ly * 32 + lx] = pj;
             }
             __syncthreads();
         }
-
-        // write back, publish, then the dot products (off the wavefront's critical path)
-        const int nvalid = min(32, nx - x0);
-        const int z = z0 + wz;
-        const bool zin = z < nz && lane < nvalid;
-        if (zin) {
-            for (int ly2 = 0; ly2 < 32 && y0 + ly2 < ny; ++ly2)
-                p[(long long)z * nxy + (long long)(y0 + ly2) * nx + x0 + lane] = sv[(wz * 32 + ly2) * 32 + lane];
-        }
-        __syncthreads();
         if (tid == 0) {
             __threadfence();
             st_release(a.flags + tile, 1);
         }
-        if (a.tile_part) {
-            double acc[2] = {0.0, 0.0};
-            if (zin) {
-                for (int ly2 = 0; ly2 < 32 && y0 + ly2 < ny; ++ly2) {
-                    const long long j = (long long)z * nxy + (long long)(y0 + ly2) * nx + x0 + lane;
-                    const T pj = sv[(wz * 32 + ly2) * 32 + lane];
-                    if (gd) acc[0] += (double)(gd[j] * pj);
-                    if (gpd) acc[1] += (double)(gpd[j] * pj);
-                }
+
+        // write back, then the dot products (off the wavefront's critical path)
+        const int nvalid = min(32, nx - x0);
+        const int z = z0 + wz;
+        const bool zin = z < nz && lane < nvalid;
+        double acc[2] = {0.0, 0.0};
+        if (zin) {
+            for (int ly2 = 0; ly2 < 32 && y0 + ly2 < ny; ++ly2) {
+                const long long j = (long long)z * nxy + (long long)(y0 + ly2) * nx + x0 + lane;
+                const T pj = sv[(wz * 32 + ly2) * 32 + lane];
+                p[j] = pj;
+                if (gd) acc[0] += (double)(gd[j] * pj);
+                if (gpd) acc[1] += (double)(gpd[j] * pj);
             }
+        }
+        if (a.tile_part) {
             block_sum<2>(acc, sbuf);
             if (tid == 0) {
                 a.tile_part[tile] = acc[0];
@@ -503,10 +485,8 @@ __global__ void __launch_bounds__(32 * kTZ) k_ic_bwd(IcArgs a) {
     }
 }
 
-template <typename T> int ic_tz() { return kTZ; }
-template <typename T> size_t ic_smem_bytes() {
-    return FwdSmem<T>::bytes > BwdSmem<T>::bytes ? FwdSmem<T>::bytes : BwdSmem<T>::bytes;
-}
+template <typename T> int ic_tz() { return Tile<T>::TZ; }
+template <typename T> size_t ic_face_bytes_per_tile() { return face_bytes_per_tile<T>(); }
 
 template <typename T>
 static cudaError_t prep() {
@@ -525,18 +505,29 @@ template <typename T>
 int ic_max_blocks_per_sm() {
     if (prep<T>() != cudaSuccess) return 0;
     int a = 0, b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_ic_fwd<T>, 32 * kTZ, FwdSmem<T>::bytes) != cudaSuccess)
+    const int nt = 32 * Tile<T>::TZ;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_ic_fwd<T>, nt, FwdSmem<T>::bytes) != cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ic_bwd<T>, 32 * kTZ, BwdSmem<T>::bytes) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ic_bwd<T>, nt, BwdSmem<T>::bytes) != cudaSuccess)
         return 0;
     return a < b ? a : b;
+}
+
+static PivScal piv_scal(double beta) {
+    PivScal c;
+    c.bh = (float)beta;
+    c.bl = (float)(beta - (double)c.bh);
+    const double b2 = beta * beta;
+    c.b2h = (float)b2;
+    c.b2l = (float)(b2 - (double)c.b2h);
+    return c;
 }
 
 template <typename T>
 cudaError_t launch_ic_fwd(const IcArgs& a, int grid, cudaStream_t s) {
     cudaError_t e = prep<T>();
     if (e != cudaSuccess) return e;
-    k_ic_fwd<T><<<grid, 32 * kTZ, FwdSmem<T>::bytes, s>>>(a, a.d ? 0 : 1);
+    k_ic_fwd<T><<<grid, 32 * Tile<T>::TZ, FwdSmem<T>::bytes, s>>>(a, a.d ? 0 : 1, piv_scal(a.beta));
     return cudaGetLastError();
 }
 
@@ -544,7 +535,7 @@ template <typename T>
 cudaError_t launch_ic_bwd(const IcArgs& a, int grid, cudaStream_t s) {
     cudaError_t e = prep<T>();
     if (e != cudaSuccess) return e;
-    k_ic_bwd<T><<<grid, 32 * kTZ, BwdSmem<T>::bytes, s>>>(a);
+    k_ic_bwd<T><<<grid, 32 * Tile<T>::TZ, BwdSmem<T>::bytes, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -552,7 +543,7 @@ cudaError_t launch_ic_bwd(const IcArgs& a, int grid, cudaStream_t s) {
     template cudaError_t launch_ic_fwd<T>(const IcArgs&, int, cudaStream_t);  \
     template cudaError_t launch_ic_bwd<T>(const IcArgs&, int, cudaStream_t);  \
     template int ic_tz<T>();                                                  \
-    template size_t ic_smem_bytes<T>();                                       \
+    template size_t ic_face_bytes_per_tile<T>();                              \
     template int ic_max_blocks_per_sm<T>();
 FM_INST(float)
 FM_INST(double)
