@@ -13,16 +13,16 @@
 // all grid neighbours: an outside neighbour contributes exactly 0.
 //
 // Parallel schedule: voxel (x, y, z) depends on (x-1, y, z), (x, y-1, z), (x, y, z-1), so
-// every hyperplane x + y + z = const is independent.  The grid is cut into 32 x 32 x TZ
+// every hyperplane x + y + z = const is independent.  The grid is cut into 32 x 32 x 8
 // tiles; a CTA claims tiles through an atomic ticket in a dependency-respecting order (a
 // tile's predecessors always hold smaller tickets, so no co-residency is assumed), starts
-// the asynchronous copy of the tile's inputs into shared memory, waits on the predecessors'
-// ready flags (bounded spin), and sweeps the tile's 62 + TZ local hyperplanes: lane = y,
-// warp = z, and each thread walks its x row one step per hyperplane, taking the -y value
-// from the neighbouring lane by shuffle, the -z value from the warp below through shared
-// memory and the -x value from its own register.  The values on the tile's three outgoing
-// faces go to a per-tile face buffer as they are produced, so a tile is released right after
-// its sweep; the row-coalesced write-back of the whole tile follows.
+// the asynchronous copy of the tile's inputs into shared memory, forms H_jj, waits on the
+// predecessors' ready flags (bounded spin), and sweeps the tile's 70 local hyperplanes:
+// lane = y, warp = z, and each thread walks its x row one step per hyperplane, taking the -y
+// value from the neighbouring lane by shuffle, the -z value from the warp below through
+// shared memory and the -x value from its own register; warps outside their 63 busy steps
+// only join the barrier.  The tile's three outgoing faces then go to a per-tile face buffer
+// and the tile is released; the row-coalesced write-back of the whole tile follows.
 //
 // Pivot arithmetic.  FP64 mode uses IEEE double.  FP32 mode carries each inverse pivot as
 // an unevaluated pair a + b of floats (about 46 significant bits, like double-float), but
@@ -49,38 +49,58 @@ __device__ __forceinline__ void two_sum(float x, float y, float& s, float& e) {
     e = __fadd_rn(__fsub_rn(x, __fsub_rn(s, bb)), __fsub_rn(y, bb));
 }
 
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 struct PivScal {     // beta-derived constants of the pivot recurrence
     float bh, bl;    // beta = bh + bl
     float b2h, b2l;  // beta^2 = b2h + b2l
 };
 
+// Per precision: H_jj = d_j + beta n_j is formed once per voxel while the tile is staged
+// (stored as hi in the d slot, -1 outside the mask, and, in FP32 mode, its low part in a
+// second array); the sweep then only needs 1/pi_j = 1/(H_jj - beta^2 sum_k 1/pi_k).
 template <typename T> struct PivOps;
 template <> struct PivOps<double> {
     using P = double;
+    static constexpr bool kLo = false;
     static __device__ __forceinline__ P zero() { return 0.0; }
     static __device__ __forceinline__ double hi(P x) { return x; }
-    // 1/pi_j from H_jj = d + beta n and the lower neighbours' inverse pivots
-    static __device__ __forceinline__ P inv_pivot(double d, int n, double beta, const PivScal&, P x, P y, P z,
+    static __device__ __forceinline__ double lo(P) { return 0.0; }
+    static __device__ __forceinline__ P make(double a, double) { return a; }
+    static __device__ __forceinline__ void form_h(double d, int n, double beta, const PivScal&, double& hH,
+                                                  double&) {
+        hH = d + beta * (double)n;
+    }
+    static __device__ __forceinline__ P inv_pivot(double hH, double, double beta, const PivScal&, P x, P y, P z,
                                                   bool& ok) {
-        const double piv = d + beta * (double)n - beta * beta * ((x + y) + z);
+        const double piv = hH - beta * beta * ((x + y) + z);
         ok = piv > 0.0;
         return ok ? 1.0 / piv : 0.0;
     }
 };
 template <> struct PivOps<float> {
     using P = PF;
+    static constexpr bool kLo = true;
     static __device__ __forceinline__ P zero() { return {0.0f, 0.0f}; }
     static __device__ __forceinline__ float hi(P x) { return x.a; }
-    static __device__ __forceinline__ P inv_pivot(float d, int n, double, const PivScal& c, P x, P y, P z,
-                                                  bool& ok) {
-        // H = d + beta n as hH + hL (n <= 6, so bh * n is exact up to one rounding)
+    static __device__ __forceinline__ float lo(P x) { return x.b; }
+    static __device__ __forceinline__ P make(float a, float b) { return {a, b}; }
+    // H = d + beta n as hH + hL (n <= 6, so bh * n has one rounding, recovered by FMA)
+    static __device__ __forceinline__ void form_h(float d, int n, double, const PivScal& c, float& hH, float& hL) {
         const float fn = (float)n;
         const float bn = __fmul_rn(c.bh, fn);
         const float bn_e = __fmaf_rn(c.bh, fn, -bn);
-        float hH, hE;
+        float hE;
         two_sum(d, bn, hH, hE);
-        const float hL = __fadd_rn(hE, __fmaf_rn(c.bl, fn, bn_e));
-        // hi chain: S = (a_x + a_y) + a_z, pi_f = hH - b2h S, a = 1/pi_f
+        hL = __fadd_rn(hE, __fmaf_rn(c.bl, fn, bn_e));
+    }
+    static __device__ __forceinline__ P inv_pivot(float hH, float hL, double, const PivScal& c, P x, P y, P z,
+                                                  bool& ok) {
+        // hi chain: S = (a_x + a_y) + a_z, pi_f = hH - b2h S, a ~ 1/pi_f
         float s1, e1, S, e2;
         two_sum(x.a, y.a, s1, e1);
         two_sum(s1, z.a, S, e2);
@@ -89,22 +109,17 @@ template <> struct PivOps<float> {
         float pf, pe;
         two_sum(hH, -th, pf, pe);
         ok = pf > 0.0f;
-        if (!ok) return {0.0f, 0.0f};
-        const float a = __frcp_rn(pf);
-        const float er = __fmaf_rn(-pf, a, 1.0f);
+        const float a = rcp_approx(pf);
+        const float er = __fmaf_rn(-pf, a, 1.0f);  // exact residual of the reciprocal
         // lo: dpi = pe + hL - tl - b2l S - b2h (e1 + e2 + sum b)
         const float base = __fsub_rn(__fadd_rn(pe, hL), __fmaf_rn(c.b2l, S, tl));
         const float sb = __fadd_rn(__fadd_rn(__fadd_rn(x.b, y.b), z.b), __fadd_rn(e1, e2));
         const float dpi = __fmaf_rn(-c.b2h, sb, base);
         const float b = __fmul_rn(a, __fmaf_rn(-dpi, a, er));
-        return {a, b};
+        return ok ? P{a, b} : P{0.0f, 0.0f};
     }
 };
 
-__device__ __forceinline__ double shfl_up(double v) { return __shfl_up_sync(0xffffffffu, v, 1); }
-__device__ __forceinline__ PF shfl_up(PF v) {
-    return {__shfl_up_sync(0xffffffffu, v.a, 1), __shfl_up_sync(0xffffffffu, v.b, 1)};
-}
 // Faces are written by other CTAs of the same launch: read them through L2.
 __device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ float ld_cg(const float* p) { return __ldcg(p); }
@@ -185,52 +200,64 @@ __device__ __forceinline__ void stage_row_u8(uint8_t* s, const uint8_t* g, int r
     }
 }
 
-// ------------------------------------------------------------------ tile geometry per precision
+// ------------------------------------------------------------------ tile geometry
 
-template <typename T> struct Tile;
-template <> struct Tile<float> { static constexpr int TZ = 16; };   // 512 threads
-template <> struct Tile<double> { static constexpr int TZ = 8; };   // 256 threads
+constexpr int kTZ = 8;         // tile = 32 x 32 x 8 voxels, 8 warps
+constexpr int kSteps = 62 + kTZ;
 
-// Face layout per tile (counts of values): +x face [TZ][32] (lz, ly), +y face [TZ][32]
-// (lz, lx), +z face [32][32] (ly, lx).
-template <int TZ> struct FaceN {
-    static constexpr int x = 0, y = TZ * 32, z = 2 * TZ * 32, n = 2 * TZ * 32 + 1024;
+// Face layout per tile (counts of values): x face [TZ][32] (lz, ly), y face [TZ][32]
+// (lz, lx), z face [32][32] (ly, lx).
+struct FN {
+    static constexpr int x = 0, y = kTZ * 32, z = 2 * kTZ * 32, n = 2 * kTZ * 32 + 1024;
 };
 
 template <typename T>
 struct FwdSmem {
-    static constexpr int TZ = Tile<T>::TZ;
     using P = typename PivOps<T>::P;
-    static constexpr int nface = FaceN<TZ>::n + 2 * TZ * 32;  // faces in + z exchange
-    static constexpr size_t bytes = 2 * TZ * 1024 * sizeof(T) + nface * (sizeof(P) + sizeof(T)) + TZ * 1024;
+    static constexpr int nface = FN::n + 2 * kTZ * 32;  // incoming faces + z exchange
+    static constexpr size_t bytes = (PivOps<T>::kLo ? 3 : 2) * kTZ * 1024 * sizeof(T) +
+                                    nface * (sizeof(P) + sizeof(T)) + kTZ * 1024;
 };
 template <typename T>
 struct BwdSmem {
-    static constexpr int TZ = Tile<T>::TZ;
-    static constexpr size_t bytes = 2 * TZ * 1024 * sizeof(T) + (FaceN<TZ>::n + 2 * TZ * 32) * sizeof(T);
+    static constexpr size_t bytes = 2 * kTZ * 1024 * sizeof(T) + (FN::n + 2 * kTZ * 32) * sizeof(T);
 };
+
+__device__ __forceinline__ double shfl_up(double v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ PF shfl_up(PF v) {
+    return {__shfl_up_sync(0xffffffffu, v.a, 1), __shfl_up_sync(0xffffffffu, v.b, 1)};
+}
 
 // Per-tile face buffer (device): forward pivots [P][n], forward v [T][n], backward p [T][n].
 template <typename T>
 __host__ __device__ constexpr size_t face_bytes_per_tile() {
-    return (size_t)FaceN<Tile<T>::TZ>::n * (sizeof(typename PivOps<T>::P) + 2 * sizeof(T));
+    return (size_t)FN::n * (sizeof(typename PivOps<T>::P) + 2 * sizeof(T));
+}
+
+// smem index of voxel (lx, ly, lz) and of each outgoing face entry i
+__device__ __forceinline__ int vox(int lx, int ly, int lz) { return (lz * 32 + ly) * 32 + lx; }
+__device__ __forceinline__ int out_face_vox(int i, bool fwd) {
+    // forward: the +x (lx = 31), +y (ly = 31) and +z (lz = TZ-1) faces; backward: lx = 0, ly = 0, lz = 0
+    if (i < FN::y) return vox(fwd ? 31 : 0, i & 31, i >> 5);
+    if (i < FN::z) { const int k = i - FN::y; return vox(k & 31, fwd ? 31 : 0, k >> 5); }
+    const int k = i - FN::z;
+    return vox(k & 31, k >> 5, fwd ? kTZ - 1 : 0);
 }
 
 // mode 0: pivots from d (factor + forward); mode 1: stored 1/pi (forward only)
 template <typename T>
-__global__ void __launch_bounds__(32 * Tile<T>::TZ) k_ic_fwd(IcArgs a, int mode, PivScal pc) {
-    constexpr int TZ = Tile<T>::TZ;
-    using FN = FaceN<TZ>;
+__global__ void __launch_bounds__(32 * kTZ) k_ic_fwd(IcArgs a, int mode, PivScal pc) {
     using Ops = PivOps<T>;
     using P = typename Ops::P;
     extern __shared__ __align__(16) unsigned char smem[];
     T* sg = (T*)smem;                              // [TZ][32][32]: g, then v
-    T* sd = sg + TZ * 1024;                        // d (or stored 1/pi), then 1/pi
-    P* f_ip = (P*)(sd + TZ * 1024);                // incoming faces: x, y, z
+    T* sd = sg + kTZ * 1024;                       // d -> H_hi (-1 outside) -> 1/pi hi; or stored 1/pi
+    T* sl = sd + kTZ * 1024;                       // FP32: H_lo -> 1/pi lo
+    P* f_ip = (P*)(sd + (Ops::kLo ? 2 : 1) * kTZ * 1024);  // incoming faces: x, y, z
     P* zb_ip = f_ip + FN::n;                       // [2][TZ][32]
-    T* f_v = (T*)(zb_ip + 2 * TZ * 32);
+    T* f_v = (T*)(zb_ip + 2 * kTZ * 32);
     T* zb_v = f_v + FN::n;
-    uint8_t* snb = (uint8_t*)(zb_v + 2 * TZ * 32); // [TZ][32][32]
+    uint8_t* snb = (uint8_t*)(zb_v + 2 * kTZ * 32);  // [TZ][32][32]
     __shared__ int s_tile;
 
     const Geo geo = a.geo;
@@ -256,12 +283,26 @@ __global__ void __launch_bounds__(32 * Tile<T>::TZ) k_ic_fwd(IcArgs a, int mode,
         const int tile = s_tile;
         if (tile < 0) break;
         const int X = tile % a.ntx, Y = (tile / a.ntx) % a.nty, Z = tile / (a.ntx * a.nty);
-        const int x0 = X * 32, y0 = Y * 32, z0 = Z * TZ;
+        const int x0 = X * 32, y0 = Y * 32, z0 = Z * kTZ;
 
-        // start the copies of this tile's inputs (they do not depend on other tiles)
+        // stage this tile's inputs and form H while the predecessors may still be running
         stage_row<T>(sg, g, tid, x0, y0, z0, geo, T(0));
         stage_row<T>(sd, mode == 0 ? d : ipin, tid, x0, y0, z0, geo, T(0));
         if (mode == 0) stage_row_u8(snb, a.nb, tid, x0, y0, z0, geo);
+        cp_wait_all();
+        if (mode == 0) {
+            T* dr = sd + tid * 32;
+            T* lr = sl + tid * 32;
+            const uint8_t* br = snb + tid * 32;
+#pragma unroll 4
+            for (int i = 0; i < 32; ++i) {
+                const uint8_t b = br[i];
+                T hH = T(-1), hL = T(0);
+                if (b & NB_IN) Ops::form_h(dr[i], __popc((unsigned)(b >> 1) & 0x3fu), a.beta, pc, hH, hL);
+                dr[i] = hH;
+                if (Ops::kLo) lr[i] = hL;
+            }
+        }
         // wait for the -x, -y, -z neighbour tiles
         if (tid == 0) {
             bool ok = true;
@@ -272,7 +313,7 @@ __global__ void __launch_bounds__(32 * Tile<T>::TZ) k_ic_fwd(IcArgs a, int mode,
         }
         __syncthreads();
         // incoming faces: the neighbours' outgoing +x, +y, +z faces
-        for (int i = tid; i < FN::n; i += 32 * TZ) {
+        for (int i = tid; i < FN::n; i += 32 * kTZ) {
             P ip = Ops::zero();
             T vv = 0;
             int src = -1;
@@ -286,60 +327,72 @@ __global__ void __launch_bounds__(32 * Tile<T>::TZ) k_ic_fwd(IcArgs a, int mode,
             f_ip[i] = ip;
             f_v[i] = vv;
         }
-        cp_wait_all();
         __syncthreads();
 
-        // sweep the local hyperplanes s = lx + ly + lz
-        const int ly = lane, lz = wz;
+        // sweep the local hyperplanes s = lx + ly + lz; warp lz is busy for s in [lz, lz + 62]
+        const int ly = lane, lz = wz, l0 = ly + lz;
+        const int row = (lz * 32 + ly) * 32;
+        const P fx_ip = f_ip[FN::x + lz * 32 + ly];
+        const T fx_v = f_v[FN::x + lz * 32 + ly];
+        const P* fy_ip = f_ip + FN::y + lz * 32;
+        const T* fy_v = f_v + FN::y + lz * 32;
+        const P* fz_ip = f_ip + FN::z + ly * 32;
+        const T* fz_v = f_v + FN::z + ly * 32;
+        const int zr = (lz > 0 ? lz - 1 : 0) * 32 + ly, zw = lz * 32 + ly;
         P out_ip = Ops::zero();
         T out_v = 0;
         bool bad = false;
-        P* oip = face_ip(tile);
-        T* ov = face_v(tile);
-        for (int s = 0; s < 62 + TZ; ++s) {
-            const P up_ip = shfl_up(out_ip);
-            const T up_v = __shfl_up_sync(0xffffffffu, out_v, 1);
-            const int lx = s - ly - lz;
-            if (lx >= 0 && lx < 32) {
-                const int i = (lz * 32 + ly) * 32 + lx;
-                const int q = ((s - 1) & 1) * TZ * 32 + (lz > 0 ? lz - 1 : 0) * 32 + ly;
-                const P xip = lx == 0 ? f_ip[FN::x + lz * 32 + ly] : out_ip;
-                const T xv = lx == 0 ? f_v[FN::x + lz * 32 + ly] : out_v;
-                const P yip = ly == 0 ? f_ip[FN::y + lz * 32 + lx] : up_ip;
-                const T yv = ly == 0 ? f_v[FN::y + lz * 32 + lx] : up_v;
-                const P zip = lz == 0 ? f_ip[FN::z + ly * 32 + lx] : zb_ip[q];
-                const T zv = lz == 0 ? f_v[FN::z + ly * 32 + lx] : zb_v[q];
-                P ipj = Ops::zero();
-                T vj = 0;
-                if (mode == 0) {
-                    const uint8_t b = snb[i];
-                    if (b & NB_IN) {
-                        bool ok;
-                        ipj = Ops::inv_pivot(sd[i], __popc((unsigned)(b >> 1) & 0x3fu), a.beta, pc, xip, yip, zip, ok);
+        for (int s = 0; s < kSteps; ++s) {
+            if (s >= lz && s <= lz + 62) {
+                const P up_ip = shfl_up(out_ip);
+                const T up_v = __shfl_up_sync(0xffffffffu, out_v, 1);
+                const int lx = s - l0;
+                if ((unsigned)lx < 32u) {
+                    const int i = row + lx;
+                    const int par = (s & 1) * kTZ * 32;
+                    const P xip = lx == 0 ? fx_ip : out_ip;
+                    const T xv = lx == 0 ? fx_v : out_v;
+                    const P yip = ly == 0 ? fy_ip[lx] : up_ip;
+                    const T yv = ly == 0 ? fy_v[lx] : up_v;
+                    const P zip = lz == 0 ? fz_ip[lx] : zb_ip[(kTZ * 32 - par) + zr];
+                    const T zv = lz == 0 ? fz_v[lx] : zb_v[(kTZ * 32 - par) + zr];
+                    P ipj;
+                    T vj;
+                    if (mode == 0) {
+                        const T hH = sd[i];
+                        bool ok = true;
+                        ipj = hH >= T(0) ? Ops::inv_pivot(hH, Ops::kLo ? sl[i] : T(0), a.beta, pc, xip, yip, zip, ok)
+                                         : Ops::zero();
                         bad |= !ok;
                         vj = (sg[i] + betaT * ((xv + yv) + zv)) * (T)Ops::hi(ipj);
+                        sd[i] = (T)Ops::hi(ipj);
+                        if (Ops::kLo) sl[i] = (T)Ops::lo(ipj);
+                    } else {
+                        ipj = Ops::zero();
+                        vj = (sg[i] + betaT * ((xv + yv) + zv)) * sd[i];
                     }
-                    sd[i] = (T)Ops::hi(ipj);
-                } else {
-                    vj = (sg[i] + betaT * ((xv + yv) + zv)) * sd[i];
+                    sg[i] = vj;
+                    out_ip = ipj;
+                    out_v = vj;
+                    zb_ip[par + zw] = ipj;
+                    zb_v[par + zw] = vj;
                 }
-                sg[i] = vj;
-                out_ip = ipj;
-                out_v = vj;
-                zb_ip[(s & 1) * TZ * 32 + lz * 32 + ly] = ipj;
-                zb_v[(s & 1) * TZ * 32 + lz * 32 + ly] = vj;
-                if (lx == 31) { oip[FN::x + lz * 32 + ly] = ipj; ov[FN::x + lz * 32 + ly] = vj; }
-                if (ly == 31) { oip[FN::y + lz * 32 + lx] = ipj; ov[FN::y + lz * 32 + lx] = vj; }
-                if (lz == TZ - 1) { oip[FN::z + ly * 32 + lx] = ipj; ov[FN::z + ly * 32 + lx] = vj; }
             }
             __syncthreads();
         }
         if (bad) set_err(a.istate, FM_ERR_NOT_PD);
-        // publish: the successors read only the face buffer
-        if (tid == 0) {
-            __threadfence();
-            st_release(a.flags + tile, 1);
+        // outgoing faces from shared memory, then publish (release after the CTA barrier)
+        {
+            P* oip = face_ip(tile);
+            T* ov = face_v(tile);
+            for (int i = tid; i < FN::n; i += 32 * kTZ) {
+                const int k = out_face_vox(i, true);
+                ov[i] = sg[k];
+                if (mode == 0) oip[i] = Ops::make(sd[k], Ops::kLo ? sl[k] : T(0));
+            }
         }
+        __syncthreads();
+        if (tid == 0) st_release(a.flags + tile, 1);
         // write back row-coalesced (warp lz writes its 32 rows, lane = x)
         const int nvalid = min(32, nx - x0);
         const int z = z0 + wz;
@@ -356,14 +409,12 @@ __global__ void __launch_bounds__(32 * Tile<T>::TZ) k_ic_fwd(IcArgs a, int mode,
 }
 
 template <typename T>
-__global__ void __launch_bounds__(32 * Tile<T>::TZ) k_ic_bwd(IcArgs a) {
-    constexpr int TZ = Tile<T>::TZ;
-    using FN = FaceN<TZ>;
+__global__ void __launch_bounds__(32 * kTZ) k_ic_bwd(IcArgs a) {
     using P = typename PivOps<T>::P;
     extern __shared__ __align__(16) unsigned char smem[];
     T* sv = (T*)smem;                 // [TZ][32][32]: v, then p
-    T* sip = sv + TZ * 1024;          // 1/pi
-    T* f_p = sip + TZ * 1024;         // incoming faces (the successors' -x, -y, -z faces)
+    T* sip = sv + kTZ * 1024;         // 1/pi
+    T* f_p = sip + kTZ * 1024;        // incoming faces (the successors' -x, -y, -z faces)
     T* zb = f_p + FN::n;              // [2][TZ][32]
     __shared__ int s_tile;
     __shared__ bool s_last;
@@ -394,7 +445,7 @@ __global__ void __launch_bounds__(32 * Tile<T>::TZ) k_ic_bwd(IcArgs a) {
         const int tile = s_tile;
         if (tile < 0) break;
         const int X = tile % a.ntx, Y = (tile / a.ntx) % a.nty, Z = tile / (a.ntx * a.nty);
-        const int x0 = X * 32, y0 = Y * 32, z0 = Z * TZ;
+        const int x0 = X * 32, y0 = Y * 32, z0 = Z * kTZ;
 
         stage_row<T>(sv, vin, tid, x0, y0, z0, geo, T(0));
         stage_row<T>(sip, ipb, tid, x0, y0, z0, geo, T(0));
@@ -407,7 +458,7 @@ __global__ void __launch_bounds__(32 * Tile<T>::TZ) k_ic_bwd(IcArgs a) {
         }
         __syncthreads();
         // incoming faces: the +x / +y / +z neighbours' outgoing low faces (lx = 0, ly = 0, lz = 0)
-        for (int i = tid; i < FN::n; i += 32 * TZ) {
+        for (int i = tid; i < FN::n; i += 32 * kTZ) {
             T q = 0;
             int src = -1;
             if (i < FN::y) { if (X + 1 < a.ntx) src = tile + 1; }
@@ -419,32 +470,38 @@ __global__ void __launch_bounds__(32 * Tile<T>::TZ) k_ic_bwd(IcArgs a) {
         cp_wait_all();
         __syncthreads();
 
-        const int ly = lane, lz = wz;
+        // sweep in reverse; warp lz is busy for s in [lz, lz + 62]
+        const int ly = lane, lz = wz, l0 = ly + lz;
+        const int row = (lz * 32 + ly) * 32;
+        const T fx = f_p[FN::x + lz * 32 + ly];
+        const T* fy = f_p + FN::y + lz * 32;
+        const T* fz = f_p + FN::z + ly * 32;
+        const int zr = (lz < kTZ - 1 ? lz + 1 : lz) * 32 + ly, zw = lz * 32 + ly;
         T out = 0;
-        T* op = face_p(tile);
-        for (int s = 61 + TZ; s >= 0; --s) {
-            const T dn = __shfl_down_sync(0xffffffffu, out, 1);
-            const int lx = s - ly - lz;
-            if (lx >= 0 && lx < 32) {
-                const int i = (lz * 32 + ly) * 32 + lx;
-                const T px = lx == 31 ? f_p[FN::x + lz * 32 + ly] : out;
-                const T py = ly == 31 ? f_p[FN::y + lz * 32 + lx] : dn;
-                const T pz = lz == TZ - 1 ? f_p[FN::z + ly * 32 + lx]
-                                          : zb[((s + 1) & 1) * TZ * 32 + (lz < TZ - 1 ? lz + 1 : lz) * 32 + ly];
-                const T pj = sv[i] + beta * sip[i] * ((px + py) + pz);
-                sv[i] = pj;
-                out = pj;
-                zb[(s & 1) * TZ * 32 + lz * 32 + ly] = pj;
-                if (lx == 0) op[FN::x + lz * 32 + ly] = pj;
-                if (ly == 0) op[FN::y + lz * 32 + lx] = pj;
-                if (lz == 0) op[FN::z + ly * 32 + lx] = pj;
+        for (int s = kSteps - 1; s >= 0; --s) {
+            if (s >= lz && s <= lz + 62) {
+                const T dn = __shfl_down_sync(0xffffffffu, out, 1);
+                const int lx = s - l0;
+                if ((unsigned)lx < 32u) {
+                    const int i = row + lx;
+                    const int par = (s & 1) * kTZ * 32;
+                    const T px = lx == 31 ? fx : out;
+                    const T py = ly == 31 ? fy[lx] : dn;
+                    const T pz = lz == kTZ - 1 ? fz[lx] : zb[(kTZ * 32 - par) + zr];
+                    const T pj = sv[i] + beta * sip[i] * ((px + py) + pz);
+                    sv[i] = pj;
+                    out = pj;
+                    zb[par + zw] = pj;
+                }
             }
             __syncthreads();
         }
-        if (tid == 0) {
-            __threadfence();
-            st_release(a.flags + tile, 1);
+        {
+            T* op = face_p(tile);
+            for (int i = tid; i < FN::n; i += 32 * kTZ) op[i] = sv[out_face_vox(i, false)];
         }
+        __syncthreads();
+        if (tid == 0) st_release(a.flags + tile, 1);
 
         // write back, then the dot products (off the wavefront's critical path)
         const int nvalid = min(32, nx - x0);
@@ -485,7 +542,7 @@ __global__ void __launch_bounds__(32 * Tile<T>::TZ) k_ic_bwd(IcArgs a) {
     }
 }
 
-template <typename T> int ic_tz() { return Tile<T>::TZ; }
+template <typename T> int ic_tz() { return kTZ; }
 template <typename T> size_t ic_face_bytes_per_tile() { return face_bytes_per_tile<T>(); }
 
 template <typename T>
@@ -505,7 +562,7 @@ template <typename T>
 int ic_max_blocks_per_sm() {
     if (prep<T>() != cudaSuccess) return 0;
     int a = 0, b = 0;
-    const int nt = 32 * Tile<T>::TZ;
+    const int nt = 32 * kTZ;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_ic_fwd<T>, nt, FwdSmem<T>::bytes) != cudaSuccess)
         return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ic_bwd<T>, nt, BwdSmem<T>::bytes) != cudaSuccess)
@@ -527,7 +584,7 @@ template <typename T>
 cudaError_t launch_ic_fwd(const IcArgs& a, int grid, cudaStream_t s) {
     cudaError_t e = prep<T>();
     if (e != cudaSuccess) return e;
-    k_ic_fwd<T><<<grid, 32 * Tile<T>::TZ, FwdSmem<T>::bytes, s>>>(a, a.d ? 0 : 1, piv_scal(a.beta));
+    k_ic_fwd<T><<<grid, 32 * kTZ, FwdSmem<T>::bytes, s>>>(a, a.d ? 0 : 1, piv_scal(a.beta));
     return cudaGetLastError();
 }
 
@@ -535,7 +592,7 @@ template <typename T>
 cudaError_t launch_ic_bwd(const IcArgs& a, int grid, cudaStream_t s) {
     cudaError_t e = prep<T>();
     if (e != cudaSuccess) return e;
-    k_ic_bwd<T><<<grid, 32 * Tile<T>::TZ, BwdSmem<T>::bytes, s>>>(a);
+    k_ic_bwd<T><<<grid, 32 * kTZ, BwdSmem<T>::bytes, s>>>(a);
     return cudaGetLastError();
 }
 
