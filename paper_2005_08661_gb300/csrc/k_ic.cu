@@ -20,8 +20,8 @@
 // predecessors' ready flags (bounded spin), and sweeps the tile's 70 local hyperplanes:
 // lane = y, warp = z, and each thread walks its x row one step per hyperplane, taking the -y
 // value from the neighbouring lane by shuffle, the -z value from the warp below through
-// shared memory and the -x value from its own register; warps outside their 63 busy steps
-// only join the barrier.  The tile's three outgoing faces then go to a per-tile face buffer
+// shared memory and the -x value from its own register.  The step body is branch-free
+// (divergent branches cost more per step than the idle lanes' arithmetic).  The tile's three outgoing faces then go to a per-tile face buffer
 // and the tile is released; the row-coalesced write-back of the whole tile follows.
 //
 // Pivot arithmetic.  FP64 mode uses IEEE double.  FP32 mode carries each inverse pivot as
@@ -329,7 +329,9 @@ __global__ void __launch_bounds__(32 * kTZ) k_ic_fwd(IcArgs a, int mode, PivScal
         }
         __syncthreads();
 
-        // sweep the local hyperplanes s = lx + ly + lz; warp lz is busy for s in [lz, lz + 62]
+        // sweep the local hyperplanes s = lx + ly + lz.  The body is branch-free: a lane outside
+        // its row (lx not in [0, 32)) computes on the wrapped index lx & 31 -- every lane keeps its
+        // own shared-memory bank -- and only active lanes store.
         const int ly = lane, lz = wz, l0 = ly + lz;
         const int row = (lz * 32 + ly) * 32;
         const P fx_ip = f_ip[FN::x + lz * 32 + ly];
@@ -343,40 +345,46 @@ __global__ void __launch_bounds__(32 * kTZ) k_ic_fwd(IcArgs a, int mode, PivScal
         T out_v = 0;
         bool bad = false;
         for (int s = 0; s < kSteps; ++s) {
-            if (s >= lz && s <= lz + 62) {
-                const P up_ip = shfl_up(out_ip);
-                const T up_v = __shfl_up_sync(0xffffffffu, out_v, 1);
-                const int lx = s - l0;
-                if ((unsigned)lx < 32u) {
-                    const int i = row + lx;
-                    const int par = (s & 1) * kTZ * 32;
-                    const P xip = lx == 0 ? fx_ip : out_ip;
-                    const T xv = lx == 0 ? fx_v : out_v;
-                    const P yip = ly == 0 ? fy_ip[lx] : up_ip;
-                    const T yv = ly == 0 ? fy_v[lx] : up_v;
-                    const P zip = lz == 0 ? fz_ip[lx] : zb_ip[(kTZ * 32 - par) + zr];
-                    const T zv = lz == 0 ? fz_v[lx] : zb_v[(kTZ * 32 - par) + zr];
-                    P ipj;
-                    T vj;
-                    if (mode == 0) {
-                        const T hH = sd[i];
-                        bool ok = true;
-                        ipj = hH >= T(0) ? Ops::inv_pivot(hH, Ops::kLo ? sl[i] : T(0), a.beta, pc, xip, yip, zip, ok)
-                                         : Ops::zero();
-                        bad |= !ok;
-                        vj = (sg[i] + betaT * ((xv + yv) + zv)) * (T)Ops::hi(ipj);
-                        sd[i] = (T)Ops::hi(ipj);
-                        if (Ops::kLo) sl[i] = (T)Ops::lo(ipj);
-                    } else {
-                        ipj = Ops::zero();
-                        vj = (sg[i] + betaT * ((xv + yv) + zv)) * sd[i];
-                    }
-                    sg[i] = vj;
-                    out_ip = ipj;
-                    out_v = vj;
-                    zb_ip[par + zw] = ipj;
-                    zb_v[par + zw] = vj;
+            const P up_ip = shfl_up(out_ip);
+            const T up_v = __shfl_up_sync(0xffffffffu, out_v, 1);
+            const int lx = s - l0;
+            const bool act = (unsigned)lx < 32u;
+            const int lw = lx & 31;
+            const int i = row + lw;
+            const int par = (s & 1) * kTZ * 32;
+            const P fyp = fy_ip[lw], fzp = fz_ip[lw], zbp = zb_ip[(kTZ * 32 - par) + zr];
+            const T fyq = fy_v[lw], fzq = fz_v[lw], zbq = zb_v[(kTZ * 32 - par) + zr];
+            const P xip = lx == 0 ? fx_ip : out_ip;
+            const T xv = lx == 0 ? fx_v : out_v;
+            const P yip = ly == 0 ? fyp : up_ip;
+            const T yv = ly == 0 ? fyq : up_v;
+            const P zip = lz == 0 ? fzp : zbp;
+            const T zv = lz == 0 ? fzq : zbq;
+            const T hH = sd[i];
+            const T rhs = sg[i] + betaT * ((xv + yv) + zv);
+            P ipj = Ops::zero();
+            T vj;
+            bool ok = true;
+            if (mode == 0) {
+                const bool inm = hH >= T(0);  // H_jj, or -1 outside the mask
+                ipj = Ops::inv_pivot(hH, Ops::kLo ? sl[i] : T(0), a.beta, pc, xip, yip, zip, ok);
+                if (!inm) ipj = Ops::zero();
+                ok = ok || !inm;
+                vj = rhs * (T)Ops::hi(ipj);
+            } else {
+                vj = rhs * hH;  // stored 1/pi
+            }
+            if (act) {
+                bad |= !ok;
+                if (mode == 0) {
+                    sd[i] = (T)Ops::hi(ipj);
+                    if (Ops::kLo) sl[i] = (T)Ops::lo(ipj);
                 }
+                sg[i] = vj;
+                out_ip = ipj;
+                out_v = vj;
+                zb_ip[par + zw] = ipj;
+                zb_v[par + zw] = vj;
             }
             __syncthreads();
         }
@@ -470,7 +478,7 @@ __global__ void __launch_bounds__(32 * kTZ) k_ic_bwd(IcArgs a) {
         cp_wait_all();
         __syncthreads();
 
-        // sweep in reverse; warp lz is busy for s in [lz, lz + 62]
+        // sweep in reverse, branch-free as in the forward kernel
         const int ly = lane, lz = wz, l0 = ly + lz;
         const int row = (lz * 32 + ly) * 32;
         const T fx = f_p[FN::x + lz * 32 + ly];
@@ -479,20 +487,21 @@ __global__ void __launch_bounds__(32 * kTZ) k_ic_bwd(IcArgs a) {
         const int zr = (lz < kTZ - 1 ? lz + 1 : lz) * 32 + ly, zw = lz * 32 + ly;
         T out = 0;
         for (int s = kSteps - 1; s >= 0; --s) {
-            if (s >= lz && s <= lz + 62) {
-                const T dn = __shfl_down_sync(0xffffffffu, out, 1);
-                const int lx = s - l0;
-                if ((unsigned)lx < 32u) {
-                    const int i = row + lx;
-                    const int par = (s & 1) * kTZ * 32;
-                    const T px = lx == 31 ? fx : out;
-                    const T py = ly == 31 ? fy[lx] : dn;
-                    const T pz = lz == kTZ - 1 ? fz[lx] : zb[(kTZ * 32 - par) + zr];
-                    const T pj = sv[i] + beta * sip[i] * ((px + py) + pz);
-                    sv[i] = pj;
-                    out = pj;
-                    zb[par + zw] = pj;
-                }
+            const T dn = __shfl_down_sync(0xffffffffu, out, 1);
+            const int lx = s - l0;
+            const bool act = (unsigned)lx < 32u;
+            const int lw = lx & 31;
+            const int i = row + lw;
+            const int par = (s & 1) * kTZ * 32;
+            const T fyv = fy[lw], fzv = fz[lw], zbv = zb[(kTZ * 32 - par) + zr];
+            const T px = lx == 31 ? fx : out;
+            const T py = ly == 31 ? fyv : dn;
+            const T pz = lz == kTZ - 1 ? fzv : zbv;
+            const T pj = sv[i] + beta * sip[i] * ((px + py) + pz);
+            if (act) {
+                sv[i] = pj;
+                out = pj;
+                zb[par + zw] = pj;
             }
             __syncthreads();
         }
