@@ -55,6 +55,7 @@ typedef struct {
     long nm;             /* number of mask voxels */
     double *rabs, *rang; /* [nm][T] modulus and angle of r_cdmnj */
     double *dt;          /* [T] t_m - t_n of each tuple */
+    int curv_mode;       /* 0: literal Eq. 10 sum; 1: coil-combined pair weights (labelled variant) */
 } orc_t;
 
 static const double TWO_PI = 6.283185307179586476925286766559;
@@ -243,12 +244,38 @@ void orc_grad_phi(const orc_t *h, const double *w, double *g) {
     }
 }
 
-/* curvature d_j of Eq. 10 at w; zero outside the mask */
+/* Labelled variant of the curvature: Huber's curvature of the coil-combined pair terms,
+ * sum_{m,n} |R_mn| (t_m - t_n)^2 sinc(wrap(angle R_mn + w (t_m - t_n))), R_mn = sum_{c,d} r_cdmn.
+ * Because Phi_j = const + sum_{m,n} |R_mn| (1 - cos(angle R_mn + w (t_m - t_n))) exactly, it is
+ * also a majoriser curvature.  Identical to Eq. 10 for one coil. */
+static double voxel_curv_combined(const orc_t *h, const double *rabs, const double *rang, double w) {
+    int L = h->L, nc = h->nc;
+    double acc = 0.0;
+    for (int m = 0; m < L; ++m)
+        for (int n = 0; n < L; ++n) {
+            double rr = 0.0, ri = 0.0;
+            for (int c = 0; c < nc; ++c)
+                for (int d = 0; d < nc; ++d) {
+                    long t = (((long)c * nc + d) * L + m) * L + n;
+                    rr += rabs[t] * cos(rang[t]);
+                    ri += rabs[t] * sin(rang[t]);
+                }
+            double dt = h->te[m] - h->te[n];
+            double Ra = hypot(rr, ri), Rg = atan2(ri, rr);
+            acc += Ra * dt * dt * sinc(wrap_angle(Rg + w * dt));
+        }
+    return acc;
+}
+
+void orc_set_curvature(orc_t *h, int mode) { h->curv_mode = mode; }
+
+/* curvature d_j of Eq. 10 at w (or the combined variant); zero outside the mask */
 void orc_curv(const orc_t *h, const double *w, double *d) {
     for (long j = 0; j < h->nv; ++j) {
         long k = h->slot[j];
         if (k < 0) { d[j] = 0.0; continue; }
-        voxel_terms(h->T, h->rabs + k * h->T, h->rang + k * h->T, h->dt, w[j], NULL, NULL, d + j);
+        if (h->curv_mode == 1) d[j] = voxel_curv_combined(h, h->rabs + k * h->T, h->rang + k * h->T, w[j]);
+        else voxel_terms(h->T, h->rabs + k * h->T, h->rang + k * h->T, h->dt, w[j], NULL, NULL, d + j);
     }
 }
 

@@ -56,6 +56,8 @@ def _lib():
             getattr(lib, name).argtypes = [vp, _dp, _dp]
             getattr(lib, name).restype = None
         lib.orc_init.argtypes = [vp, _dp]
+        lib.orc_set_curvature.argtypes = [vp, C.c_int]
+        lib.orc_set_curvature.restype = None
         lib.orc_num_unknowns.argtypes = [vp]
         lib.orc_num_unknowns.restype = C.c_long
         lib.orc_precondition.argtypes = [vp, _dp, _dp, _dp]
@@ -113,6 +115,10 @@ class Oracle:
     @classmethod
     def from_volume(cls, vol):
         return cls(vol.y, vol.smap, vol.te, vol.mask, vol.beta)
+
+    def set_curvature(self, mode):
+        """'literal' (Eq. 10, default) or 'combined' (the labelled coil-combined variant)."""
+        self._lib.orc_set_curvature(self._h, {"literal": 0, "combined": 1}[mode])
 
     def close(self):
         if getattr(self, "_h", None):

@@ -255,23 +255,21 @@ __global__ void __launch_bounds__(kThreads) k_dir(DataArgs a) {
     const T* d = (const T*)a.d;
     auto zval = [&](long long k) -> T { return -p[k] + muT * zo[k]; };
     const long long nm = a.istate[I_NMASK];
-    double s_cz2 = 0.0, s_czw = 0.0, s_zg = 0.0, s_zzd = 0.0;
+    // each thread sums its few voxels in the voxel type; blocks and the grid sum in FP64
+    T s_cz2 = 0, s_czw = 0, s_zg = 0, s_zzd = 0;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nm;
          k += (long long)gridDim.x * blockDim.x) {
         const long long j = a.vlist[k];
         const uint8_t b = a.nb[j];
         const T zj = zval(j), wj = w[j];
         zn[j] = zj;
-        T cz2 = 0, czw = 0;
-        if (b & NB_XP) { const T e = zj - zval(j + 1), f = wj - w[j + 1]; cz2 += e * e; czw += e * f; }
-        if (b & NB_YP) { const T e = zj - zval(j + nx), f = wj - w[j + nx]; cz2 += e * e; czw += e * f; }
-        if (b & NB_ZP) { const T e = zj - zval(j + nxy), f = wj - w[j + nxy]; cz2 += e * e; czw += e * f; }
-        s_cz2 += (double)cz2;
-        s_czw += (double)czw;
-        s_zg += (double)(zj * g[j]);
-        s_zzd += (double)(zj * zj * d[j]);
+        if (b & NB_XP) { const T e = zj - zval(j + 1), f = wj - w[j + 1]; s_cz2 += e * e; s_czw += e * f; }
+        if (b & NB_YP) { const T e = zj - zval(j + nx), f = wj - w[j + nx]; s_cz2 += e * e; s_czw += e * f; }
+        if (b & NB_ZP) { const T e = zj - zval(j + nxy), f = wj - w[j + nxy]; s_cz2 += e * e; s_czw += e * f; }
+        s_zg += zj * g[j];
+        s_zzd += zj * zj * d[j];
     }
-    double v[4] = {s_cz2, s_czw, s_zg, s_zzd}, out[4];
+    double v[4] = {(double)s_cz2, (double)s_czw, (double)s_zg, (double)s_zzd}, out[4];
     if (last_block_reduce<4>(v, a.partials, (unsigned*)(a.istate + I_DONE0), out, sbuf)) {
         if (threadIdx.x == 0) {
             a.scal[S_CZ2] = out[0];

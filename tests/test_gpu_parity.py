@@ -238,3 +238,22 @@ def test_binding_rejects_wrong_dtypes():
     with pytest.raises(TypeError):
         fm.set_data(y, s, vol.te, m, vol.beta)
     fm.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_combined_curvature_variant_matches_oracle(prec):
+    """FM_CURV_COMBINED (labelled variant): the same solve with the coil-combined curvature."""
+    vol = _vol(40, 34, 9, 3, seed=17)
+    o = Oracle.from_volume(vol)
+    o.set_curvature("combined")
+    w = _omega(o, vol, seed=2)
+    fm = open_fm(vol, prec, curvature="combined")
+    _, g, d = fm.cost_grad(to_dev(w, prec))
+    d_ref = o.curv(w)
+    tol = TOL[prec]
+    np.testing.assert_allclose(to_np(d), d_ref, rtol=tol["d"], atol=tol["d"] * np.abs(d_ref).max())
+    if prec == "fp64":
+        r = o.solve(niter=6, nls=5)
+        _, cost = fm.solve(niter=6)
+        np.testing.assert_allclose(cost, r["cost"], rtol=1e-10)
+    fm.close()

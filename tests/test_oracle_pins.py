@@ -105,9 +105,11 @@ def _one_voxel(te, y, s, beta=0.0):
                   None, beta)
 
 
+@pytest.mark.parametrize("curv", ["literal", "combined"])
 @pytest.mark.parametrize("nc,L", [(1, 2), (1, 3), (2, 3), (3, 4)])
-def test_huber_curvature_gives_a_majoriser(nc, L):
-    """q(w) = Phi(w0) + Phi'(w0)(w - w0) + d(w0)/2 (w - w0)^2 >= Phi(w) for all w."""
+def test_huber_curvature_gives_a_majoriser(nc, L, curv):
+    """q(w) = Phi(w0) + Phi'(w0)(w - w0) + d(w0)/2 (w - w0)^2 >= Phi(w) for all w, for the
+    literal curvature of Eq. 10 and for the coil-combined variant."""
     rng = np.random.default_rng(100 + 10 * nc + L)
     te = np.concatenate([[0.0], np.sort(rng.uniform(0.5, 4.0, L - 1))])
     grid = np.linspace(-25.0, 25.0, 20001)
@@ -115,6 +117,7 @@ def test_huber_curvature_gives_a_majoriser(nc, L):
         y = _rand_c(rng, L, nc)
         s = _rand_c(rng, nc) if nc > 1 else None
         o = _one_voxel(te, y, s)
+        o.set_curvature(curv)
         w0 = rng.uniform(-8.0, 8.0)
         f0, g0, d0 = o.phi([w0]), o.grad_phi([w0])[0, 0, 0], o.curv([w0])[0, 0, 0]
         ws = w0 + grid
@@ -387,3 +390,21 @@ def test_zero_beta_solve_reaches_the_brute_force_per_voxel_minimiser():
     o = Oracle.from_volume(vol)
     r = o.solve(w0=ybest + 0.02 * m, niter=40, nls=5)
     np.testing.assert_allclose(r["w"][m], ybest[m], atol=1e-7)
+
+
+def test_combined_curvature_is_tighter_and_equal_for_one_coil():
+    """The coil-combined curvature never exceeds the literal one (|sum| <= sum of moduli,
+    sinc <= 1 on the wrapped angle) and equals it for one coil."""
+    rng = np.random.default_rng(31)
+    for nc in (1, 3):
+        vol = make_volume(8, 7, 5, ncoil=nc, snr_db=10.0, seed=40 + nc)
+        o = Oracle.from_volume(vol)
+        w = o.init() + 0.1 * rng.standard_normal(vol.mask.shape) * vol.mask
+        lit = o.curv(w)
+        o.set_curvature("combined")
+        comb = o.curv(w)
+        if nc == 1:
+            np.testing.assert_allclose(comb, lit, rtol=1e-12, atol=1e-14)
+        else:
+            assert np.all(comb <= lit * (1 + 1e-12) + 1e-14)
+            assert np.any(comb < lit * (1 - 1e-6))
