@@ -35,9 +35,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-# ncu DRAM bytes per launch of the roofline kernel, scaled to the full workload (see
-# profiles/); None when the kernel changed since the counters were taken.
-NCU_TRAFFIC_BYTES = {}
+# ncu DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch, by (workload,
+# kernel), from one capture of the full workload (profiles/traffic_full_256x256x128_c8.md);
+# an entry is removed when its kernel changes.
+NCU_TRAFFIC_BYTES = {
+    ("full", "ls"): 1944825856 + 177280,
+    ("full", "grad"): 504680704 + 21979008,
+    ("full", "ic_fwd"): 75533824 + 34291968,
+    ("full", "ic_bwd"): 134266496 + 17990656,
+    ("full", "dir"): 64359680 + 1216640,
+}
 
 WORKLOADS = {
     "full": dict(desc="256x256x128 voxels, 8 coils, 3 echoes (0/2/10 ms), SNR 15 dB, beta=2^-3, "
@@ -46,6 +53,9 @@ WORKLOADS = {
                        "50 NCG iterations, N_ls=5, IC(0)", niter=50),
     "medium": dict(desc="128x128x64 voxels, 8 coils, 3 echoes (0/2/10 ms), SNR 20 dB, beta=2^-3, "
                         "100 NCG iterations, N_ls=5, IC(0)", niter=100),
+    "batch": dict(desc="32 independent volumes from 64x64x16 to 192x192x96, 1 or 8 coils, 3 echoes "
+                       "(0/2/10 ms), SNR 10-25 dB, beta=2^-3, 50 NCG iterations each, N_ls=5, IC(0), one "
+                       "CUDA graph launch per two iterations of all volumes", niter=50),
 }
 CPU_SAMPLE = (32, 32, 16)  # oracle sample: centred sub-volume of the same acquisition
 
@@ -339,7 +349,7 @@ def run_ours(args, world, rank, local):
                     "frac": ach / peaks["fp32_tflops"], "peak_src": "derived: 2 flops x 128 FP32 lanes x "
                     f"{nsm} SMs x {sm_max:.0f} MHz", "ms_per_launch": ms,
                     "algorithmic_flops_per_launch": flops,
-                    "traffic": NCU_TRAFFIC_BYTES.get(dom)}
+                    "traffic": NCU_TRAFFIC_BYTES.get((args.workload, dom))}
         else:
             ts = 4 if prec == "fp32" else 8
             if evals:
@@ -348,12 +358,12 @@ def run_ours(args, world, rank, local):
                 byts = nv * (1 + 2 * ts + 2 * ts)
             elif dom == "ic_bwd":
                 byts = nv * (1 + 2 * ts + 3 * ts)
-            else:
-                byts = nv * (1 + 7 * ts)
+            else:  # direction pass over the mask list: index, bits, p, z, w, g, d in, z out
+                byts = nmask * (4 + 1 + 6 * ts)
             ach = byts / (ms * 1e-3) / 1e9
             roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": ach / peaks["hbm_gbs"], "peak_src": peaks["hbm_src"], "ms_per_launch": ms,
-                    "algorithmic_bytes_per_launch": byts, "traffic": NCU_TRAFFIC_BYTES.get(dom)}
+                    "algorithmic_bytes_per_launch": byts, "traffic": NCU_TRAFFIC_BYTES.get((args.workload, dom))}
     kernels = {k: {"ms_per_launch": v[0], "share_of_iteration": (v[0] / sum(per_iter.values()) if per_iter else None)}
                for k, v in kt.items() if v[1] > 0}
 
@@ -385,6 +395,83 @@ def run_ours(args, world, rank, local):
     if rank == 0:
         print(json.dumps(line), flush=True)
     fm.close()
+    return 0
+
+
+def run_batch(args, world, rank, local):
+    """Config-4 form: aggregate voxel-NCG-iters/s of 32 uneven volumes solved together,
+    against the same 32 volumes solved one after another with fm_solve."""
+    import torch
+    from paper_2005_08661_gb300 import FieldMap, FieldMapBatch, build as fm_build
+    from synth import batch_configs, make_volume
+    import ctypes as C
+    fm_build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    niter = args.niter or WORKLOADS["batch"]["niter"]
+    cfgs = batch_configs(32, seed=1004 + rank)
+    vols = [make_volume(c["nx"], c["ny"], c["nz"], ncoil=c["ncoil"], snr_db=c["snr_db"], seed=c["seed"],
+                        fmax_hz=200.0, nblobs=4) for c in cfgs]
+    cd = torch.complex64 if args.precision == "fp32" else torch.complex128
+    dev_in = []
+    for v in vols:
+        y = torch.from_numpy(v.y).to(dev).to(cd)
+        s = torch.from_numpy(v.smap).to(dev).to(cd) if v.smap is not None else None
+        m = torch.from_numpy(v.mask).to(dev)
+        dev_in.append((y, s, m))
+    stream = torch.cuda.Stream(dev)
+    nvox = sum(v.nvox for v in vols)
+    b = FieldMapBatch([(v.nx, v.ny, v.nz, v.ncoil, v.necho) for v in vols], precision=args.precision, device=local,
+                      stream=stream)
+    for k, v in enumerate(vols):
+        b.set_data(k, dev_in[k][0], dev_in[k][1], v.te, dev_in[k][2], v.beta)
+    frac, _ = b.autotune(niter_probe=4)
+    ws = [b.empty(k) for k in range(len(vols))]
+    ptrs = (C.c_void_p * len(vols))(*[w.data_ptr() for w in ws])
+
+    def step_batch():
+        for k, v in enumerate(vols):
+            b.set_data(k, dev_in[k][0], dev_in[k][1], v.te, dev_in[k][2], v.beta)
+        b.solve_into(ptrs, True, niter)
+
+    singles = [FieldMap(v.nx, v.ny, v.nz, ncoil=v.ncoil, necho=v.necho, precision=args.precision, device=local,
+                        stream=stream) for v in vols]
+
+    def step_seq():
+        for k, v in enumerate(vols):
+            singles[k].set_data(dev_in[k][0], dev_in[k][1], v.te, dev_in[k][2], v.beta)
+            singles[k].solve_into(ws[k], True, niter)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / 1000.0 / args.steps
+
+    clocks = ClockSampler(local)
+    t_b = max_over_ranks(timed(step_batch), world, dev)
+    clk = clocks.stop()
+    t_s = max_over_ranks(timed(step_seq), world, dev)
+    line = {"metric": "voxel-NCG-iters/s", "value": world * nvox * niter / t_b, "unit": "voxel-iter/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t_b,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS["batch"]["desc"], "volumes": len(vols), "voxels": nvox, "niter": niter,
+                       "grid_fraction": frac, "parallelism": f"replicas{world}"},
+            "sequential": {"value": world * nvox * niter / t_s, "ms_per_step": 1000 * t_s,
+                           "what": "the same 32 volumes, fm_set_data + fm_solve one after another"},
+            "speedup_vs_sequential": t_s / t_b, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for f in singles:
+        f.close()
+    b.close()
     return 0
 
 
@@ -454,6 +541,8 @@ def main():
     try:
         if args.impl == "reference":
             return run_reference(args, world, rank)
+        if args.workload == "batch":
+            return run_batch(args, world, rank, local)
         return run_ours(args, world, rank, local)
     finally:
         if world > 1:
