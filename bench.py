@@ -56,6 +56,9 @@ WORKLOADS = {
     "batch": dict(desc="32 independent volumes from 64x64x16 to 192x192x96, 1 or 8 coils, 3 echoes "
                        "(0/2/10 ms), SNR 10-25 dB, beta=2^-3, 50 NCG iterations each, N_ls=5, IC(0), one "
                        "CUDA graph launch per two iterations of all volumes", niter=50),
+    "diff": dict(desc="128x128x64 voxels, 8 coils, 3 echoes (0/2/10 ms), SNR 20 dB, beta=2^-3: "
+                      "torch.autograd forward (100 NCG iterations) + backward (IC(0)-preconditioned adjoint "
+                      "CG to 1e-6, dl/dbeta and dl/dy) of l = ||w^ - w_true||^2", niter=100),
 }
 CPU_SAMPLE = (32, 32, 16)  # oracle sample: centred sub-volume of the same acquisition
 
@@ -475,6 +478,90 @@ def run_batch(args, world, rank, local):
     return 0
 
 
+def run_diff(args, world, rank, local):
+    """Differentiation form: forward solve + implicit-gradient backward through
+    torch.autograd, FP32 timed, with the FP64 GPU path as the accuracy reference."""
+    import torch
+    from paper_2005_08661_gb300 import FieldMap, build as fm_build, field_map_solve
+    from synth import diff_config
+    fm_build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    niter = args.niter or WORKLOADS["diff"]["niter"]
+    vol = diff_config(seed=1005 + rank)
+    nv = vol.nvox
+    stream = torch.cuda.Stream(dev)
+
+    def setup(prec):
+        cd = torch.complex64 if prec == "fp32" else torch.complex128
+        rd = torch.float32 if prec == "fp32" else torch.float64
+        y = torch.from_numpy(vol.y).to(dev).to(cd).contiguous()
+        s = torch.from_numpy(vol.smap).to(dev).to(cd).contiguous()
+        m = torch.from_numpy(vol.mask).to(dev)
+        tgt = torch.from_numpy(vol.omega_true * vol.mask).to(dev).to(rd)
+        fm = FieldMap(vol.nx, vol.ny, vol.nz, ncoil=vol.ncoil, necho=vol.necho, precision=prec, device=local,
+                      stream=stream)
+        return fm, y, s, m, tgt
+
+    def fwd_bwd(fm, y, s, m, tgt, ev=None):
+        yv = y.clone().requires_grad_(True)
+        beta = torch.tensor(vol.beta, dtype=torch.float64, requires_grad=True)
+        w = field_map_solve(yv, beta, fm, s, vol.te, m, niter=niter)
+        loss = ((w - tgt) ** 2 * m).sum()
+        if ev is not None:
+            ev[0].record(stream)
+        dy, db = torch.autograd.grad(loss, (yv, beta))
+        if ev is not None:
+            ev[1].record(stream)
+        return w, dy, db
+
+    res = {}
+    with torch.cuda.stream(stream):
+        for prec in ("fp64", "fp32"):
+            fm, y, s, m, tgt = setup(prec)
+            steps = args.steps if prec == "fp32" else 1
+            for _ in range(args.warmup if prec == "fp32" else 1):
+                fwd_bwd(fm, y, s, m, tgt)
+            torch.cuda.synchronize(dev)
+            clocks = ClockSampler(local) if prec == "fp32" else None
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            em = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(steps)]
+            e0.record(stream)
+            out = None
+            for k in range(steps):
+                out = fwd_bwd(fm, y, s, m, tgt, em[k])
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            clk = clocks.stop() if clocks else None
+            total = e0.elapsed_time(e1) / steps
+            bwd = sum(a.elapsed_time(b) for a, b in em) / steps
+            res[prec] = dict(ms=total, bwd_ms=bwd, w=out[0].detach().double(), dy=out[1].to(torch.complex128),
+                             db=float(out[2]), adj=dict(fm.last_adjoint), clk=clk)
+            fm.close()
+    t_s = max_over_ranks(res["fp32"]["ms"] / 1000.0, world, dev)
+    r32, r64 = res["fp32"], res["fp64"]
+    err = {"dl_dbeta_rel": abs(r32["db"] - r64["db"]) / abs(r64["db"]),
+           "dl_dy_rel_l2": float((r32["dy"] - r64["dy"]).norm() / r64["dy"].norm()),
+           "w_hat_rms_hz": float(((r32["w"] - r64["w"]) ** 2 * torch.from_numpy(vol.mask).to(dev)).sum().div(
+               float(vol.mask.sum())).sqrt()) * 1000.0 / (2 * math.pi)}
+    line = {"metric": "voxel-NCG-iters/s", "value": world * nv * niter / t_s, "unit": "voxel-iter/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t_s,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS["diff"]["desc"], "voxels": nv, "mask_voxels": int(vol.mask.sum()),
+                       "niter": niter, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (0.4 GB of pair/coil data streamed per evaluation)"},
+            "backward": {"ms": r32["bwd_ms"], "adjoint_cg_iterations": r32["adj"]["iterations"],
+                         "adjoint_relres": r32["adj"]["relres"],
+                         "ms_per_cg_iteration": r32["bwd_ms"] / max(1, r32["adj"]["iterations"])},
+            "fp64_gpu": {"ms_per_step": r64["ms"], "backward_ms": r64["bwd_ms"],
+                         "adjoint_cg_iterations": r64["adj"]["iterations"], "adjoint_relres": r64["adj"]["relres"]},
+            "fp32_error_vs_fp64_gpu": err, "clocks": r32["clk"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def time_to_oracle_cost(prec, stream):
     """FP32/FP64 solve of the 64x64x16 workload: seconds until the cost first falls to the
     FP64 oracle's 50-iteration cost x (1 + 1e-6)."""
@@ -543,6 +630,8 @@ def main():
             return run_reference(args, world, rank)
         if args.workload == "batch":
             return run_batch(args, world, rank, local)
+        if args.workload == "diff":
+            return run_diff(args, world, rank, local)
         return run_ours(args, world, rank, local)
     finally:
         if world > 1:

@@ -173,6 +173,142 @@ FM_API int fm_solve(fm_ctx *ctx, void *omega, int init_from_data, int niter, dou
  */
 FM_API int fm_get_history(fm_ctx *ctx, double *alpha_hist, double *mu_hist, int n);
 
+/* ---------------------------------------------------------------------------------
+ * Water-fat model (Sec. II: x_l = m_w + m_f sum_p a_p e^{i 2 pi f_p t_l}; Eq. gamma).
+ * ------------------------------------------------------------------------------- */
+
+/*
+ * Select the water-fat model for the next fm_set_data: npeak fat peaks with relative
+ * amplitudes rel_amp (host double [npeak]; the paper's sum to 1) and frequency offsets
+ * freq (host double [npeak], cycles per unit of the echo times: kHz when te is in ms).
+ * fm_set_data then uses Gamma = gamma (gamma^H gamma)^{-1} gamma^H with gamma = [1, phi],
+ * phi_l = sum_p rel_amp_p e^{i 2 pi freq_p t_l}, in Eq. 3 instead of 1/L; cost, gradient,
+ * curvature, IC(0) and the solver are unchanged in form.  npeak = 0 restores the
+ * field-map model.  Invalidates the loaded data: call fm_set_data again.
+ * Errors: FM_ERR_ARG (npeak outside 0..64, NULL arrays, non-finite values); fm_set_data
+ * returns FM_ERR_ARG if phi is collinear with the ones vector at the echo times.
+ */
+FM_API int fm_set_fat_model(fm_ctx *ctx, int npeak, const double *rel_amp, const double *freq);
+
+/*
+ * Voxel-wise initialisation of the water-fat case (Sec. III-A): for every mask voxel,
+ * Phi_j (Eq. 2) at nsweep equally spaced values w_lo + (w_hi - w_lo) q / (nsweep - 1),
+ * q = 0 .. nsweep - 1; the first value with the smallest cost goes to omega_tilde (device
+ * [nz][ny][nx], voxel type; 0 outside the mask).  The paper sweeps 100 values over
+ * [-|Delta_f / 2|, |Delta_f / 2|] (in rad per unit of te: pi |f| for a peak at f).
+ * Errors: FM_ERR_ARG (nsweep < 1, non-finite bounds), FM_ERR_STATE.
+ */
+FM_API int fm_wf_sweep(fm_ctx *ctx, int nsweep, double w_lo, double w_hi, void *omega_tilde);
+
+/*
+ * PWLS initialisation (Eq. w0_wf): niter conjugate-gradient iterations (no preconditioner;
+ * the paper uses 10) on (2 diag(rho) + beta C'C) w = 2 rho omega_tilde, starting from
+ * omega_tilde, with rho_j = sum_{c,d,m,n} |r_cdmnj| from fm_set_data.  omega_tilde, omega0:
+ * device [nz][ny][nx] of the voxel type (may alias).  Dot products in double.
+ * Overwrites the solver's work buffers (and drops an fm_ic_factor result).  Synchronises.
+ * Errors: FM_ERR_ARG, FM_ERR_STATE, FM_ERR_NOT_PD, FM_ERR_NONFINITE.
+ */
+FM_API int fm_pwls_init(fm_ctx *ctx, const void *omega_tilde, int niter, void *omega0);
+
+/*
+ * Water and fat components at the field map omega by the closed form of Eq. wf:
+ * [m_w, m_f]_j = ((gamma diag(e^{i w_j t})) kron s_j)^+ y_j.  y and smap are the arrays
+ * given to fm_set_data (smap NULL only with one coil); water and fat: device complex
+ * [nz][ny][nx] of the image type (0 outside the mask and where sum_c |s_c|^2 = 0).
+ * Errors: FM_ERR_ARG, FM_ERR_STATE (no fat model, or fm_set_data missing).
+ */
+FM_API int fm_wf_amplitudes(fm_ctx *ctx, const void *y, const void *smap, const void *omega, void *water,
+                            void *fat);
+
+/* ---------------------------------------------------------------------------------
+ * Differentiation of the converged field map.  The paper has no counterpart; these
+ * calls rest on its first-order condition at the solution, grad Psi(w^) = 0 (Eq. 5, 8).
+ * Differentiating that identity gives, for a scalar loss l(w^) with b = dl/dw^,
+ *     lambda = H_true^{-1} b,          H_true = diag(h(w^)) + beta C'C,
+ *     dl/dbeta = -lambda' C'C w^,      dl/dy = -(d grad Phi / dy)' lambda,
+ * where h is the exact second derivative of Phi (below), not the Huber majoriser d of
+ * Eq. 10-11.  The gradient with respect to w of Psi itself is fm_cost_grad's grad.
+ * ------------------------------------------------------------------------------- */
+
+/*
+ * h_j = d^2 Phi_j / dw_j^2 = sum_{c,d,m,n} |r| (t_m - t_n)^2 cos(angle r + w_j (t_m - t_n))
+ * (the derivative of Eq. 8) at omega, into h (device [nz][ny][nx], voxel type; 0 outside
+ * the mask).  h can be negative where a phase residual exceeds pi/2.
+ * Errors: FM_ERR_ARG, FM_ERR_STATE before fm_set_data.
+ */
+FM_API int fm_true_curv(fm_ctx *ctx, const void *omega, void *h);
+
+/*
+ * Solve H_true lambda = rhs on the mask voxels by conjugate gradients preconditioned with
+ * the IC(0) factor of the majoriser H(omega_hat) = diag(d) + beta C'C (Eq. 9, 12), the
+ * factor the solver uses.  omega_hat, rhs, lambda: device [nz][ny][nx] of the voxel type
+ * (rhs outside the mask is ignored; lambda is 0 there).  Stops when ||r|| <= tol ||rhs||
+ * (the recursively updated residual; dot products in double) or after maxiter iterations;
+ * iters and relres (host, nullable) receive the count and ||r|| / ||rhs||.  Reaching
+ * maxiter is not an error: check relres.  Leaves the preconditioner factor of omega_hat in
+ * the context (as fm_ic_factor would) and overwrites the solver's work buffers.
+ * Synchronises.  Errors: FM_ERR_ARG (tol < 0, maxiter < 0), FM_ERR_STATE, FM_ERR_NOT_PD
+ * (p' H_true p <= 0: omega_hat is not a strict local minimum), FM_ERR_NONFINITE,
+ * FM_ERR_TIMEOUT.
+ */
+FM_API int fm_adjoint_solve(fm_ctx *ctx, const void *omega_hat, const void *rhs, void *lambda, double tol,
+                            int maxiter, int *iters, double *relres);
+
+/*
+ * Given lambda from fm_adjoint_solve, the derivatives of the loss through the solution:
+ *   dl_dy    device complex [necho][ncoil][nz][ny][nx] (nullable; the image type): the
+ *            real-pair gradient d l / d Re y + i d l / d Im y, 0 outside the mask;
+ *   dl_dbeta host double (nullable; synchronises): -lambda' C'C omega_hat.
+ * y and smap must be the arrays given to fm_set_data (smap NULL only with one coil).
+ * Errors: FM_ERR_ARG, FM_ERR_STATE (also: dl_dy under the water-fat model, not
+ * implemented).
+ */
+FM_API int fm_implicit_grad(fm_ctx *ctx, const void *y, const void *smap, const void *omega_hat,
+                            const void *lambda, void *dl_dy, double *dl_dbeta);
+
+/* ---------------------------------------------------------------------------------
+ * Batched form: many independent volumes (possibly of different sizes and coil counts)
+ * solved together.  Each volume is its own context (same options) on its own stream;
+ * fm_batch_solve captures one outer iteration of every volume as parallel branches of a
+ * single CUDA graph (the two-iteration ping-pong body, as in fm_solve) and replays it, so
+ * one graph launch advances all volumes and their kernels fill the GPU together.  The
+ * per-volume arithmetic is exactly fm_solve's.
+ * ------------------------------------------------------------------------------- */
+typedef struct fm_batch fm_batch;
+
+/* Create a batch of n volumes; dims is a host int array [n][5] of (nx, ny, nz, ncoil,
+ * necho).  opts as for fm_create (shared by every volume).  cuda_stream: the stream the
+ * batch orders itself after and completes on (NULL: legacy default stream).
+ * Errors: FM_ERR_ARG (n < 1, bad sizes or options), FM_ERR_CUDA, FM_ERR_OOM. */
+FM_API int fm_batch_create(fm_batch **out, int n, const int *dims, const fm_opts *opts, int device,
+                           void *cuda_stream);
+
+/* fm_set_data for volume k (same argument rules).  Errors: FM_ERR_ARG (k out of range). */
+FM_API int fm_batch_set_data(fm_batch *b, int k, const void *y, const void *smap, const double *te,
+                             const uint8_t *mask, double beta);
+
+/* fm_solve on every volume: omega is a host array of n device pointers (in/out, each of its
+ * volume's size and voxel type); cost_hist is a host array of n host pointers (each
+ * [niter + 1] doubles) or NULL.  Synchronises.  Errors: as fm_solve; the first failing
+ * volume's status is returned. */
+FM_API int fm_batch_solve(fm_batch *b, void *const *omega, int init_from_data, int niter,
+                          double *const *cost_hist);
+
+/* Choose, by timing short solves of niter_probe iterations, the fraction of its own
+ * full-GPU grid each volume's kernels use while the volumes run side by side (candidates
+ * 1, 1/2, 1/4, 1/8).  best_ms (host, nullable) receives the winning probe time.  Requires
+ * fm_batch_set_data on every volume.  The fraction stays in effect until changed. */
+FM_API int fm_batch_autotune(fm_batch *b, int niter_probe, double *best_fraction, double *best_ms);
+
+/* Set the grid fraction directly (0 < fraction <= 1). */
+FM_API int fm_batch_set_fraction(fm_batch *b, double fraction);
+
+/* Context of volume k (for fm_cost_grad, fm_get_history, ...; owned by the batch). */
+FM_API fm_ctx *fm_batch_ctx(fm_batch *b, int k);
+
+/* Release the batch and its contexts.  NULL-safe. */
+FM_API int fm_batch_destroy(fm_batch *b);
+
 /* Kernel classes timed by fm_kernel_times. */
 #define FM_K_GRAD 0   /* data term + stencil gradient pass (fused update of the previous step) */
 #define FM_K_IC_FWD 1 /* IC(0) pivots + forward substitution wavefront */

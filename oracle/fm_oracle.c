@@ -11,7 +11,9 @@
  * What it computes, in the paper's order and notation (units: t in the caller's
  * unit, w in radians per that unit):
  *   Eq. 3  r_cdmnj = Gamma_mn / (sum_c' |s_c'j|^2) * s_cj * conj(s_dj) * conj(y_cmj) * y_dnj,
- *          Gamma_mn = 1/L (field-map case).  Precomputed once (Algorithm box).
+ *          Gamma_mn = 1/L (field-map case), or the complex L x L projector
+ *          gamma (gamma^H gamma)^{-1} gamma^H of the water-fat model (Eq. gamma), set by
+ *          orc_set_gamma.  Precomputed once (Algorithm box).
  *   Eq. 2  Phi(w) = sum_j sum_{c,d,m,n} |r| (1 - cos(angle(r) + w_j (t_m - t_n))), literal
  *          (all ordered tuples, including m = n).
  *   Eq. 5  Psi = Phi + beta/2 ||C w||^2, C = non-periodic first-order differences between
@@ -56,6 +58,8 @@ typedef struct {
     double *rabs, *rang; /* [nm][T] modulus and angle of r_cdmnj */
     double *dt;          /* [T] t_m - t_n of each tuple */
     int curv_mode;       /* 0: literal Eq. 10 sum; 1: coil-combined pair weights (labelled variant) */
+    int has_gam;         /* 0: Gamma_mn = 1/L; 1: gam holds a complex L x L Gamma */
+    double gam[2 * ORC_MAXL * ORC_MAXL];
 } orc_t;
 
 static const double TWO_PI = 6.283185307179586476925286766559;
@@ -65,21 +69,34 @@ static double wrap_angle(double th) { return th - TWO_PI * nearbyint(th / TWO_PI
 
 static double sinc(double u) { return u == 0.0 ? 1.0 : sin(u) / u; }
 
-/* Eq. 3 for one voxel: y_vox[(l*nc + c)*2 + {0,1}], s_vox[c*2 + {0,1}] (NULL: s = 1). */
+/* Gamma_mn (Eq. 3, Eq. gamma): 1/L, or the stored complex projector entry */
+static void gamma_mn(const double *gam, int L, int m, int n, double *gr, double *gi) {
+    if (gam) {
+        *gr = gam[2 * (m * L + n)];
+        *gi = gam[2 * (m * L + n) + 1];
+    } else {
+        *gr = 1.0 / (double)L;
+        *gi = 0.0;
+    }
+}
+
+/* Eq. 3 for one voxel: y_vox[(l*nc + c)*2 + {0,1}], s_vox[c*2 + {0,1}] (NULL: s = 1);
+ * gam: complex L x L Gamma or NULL (1/L). */
 static void pair_weights(int nc, int L, const double *y_vox, long ystride, const double *s_vox,
-                         long sstride, double *rabs, double *rang) {
+                         long sstride, const double *gam, double *rabs, double *rang) {
     double S = 0.0;
     for (int c = 0; c < nc; ++c) {
         double sr = s_vox ? s_vox[c * sstride] : 1.0, si = s_vox ? s_vox[c * sstride + 1] : 0.0;
         S += sr * sr + si * si;
     }
-    const double G = 1.0 / (double)L;
     long t = 0;
     for (int c = 0; c < nc; ++c)
         for (int d = 0; d < nc; ++d)
             for (int m = 0; m < L; ++m)
                 for (int n = 0; n < L; ++n, ++t) {
                     if (S == 0.0) { rabs[t] = 0.0; rang[t] = 0.0; continue; }
+                    double Gr, Gi;
+                    gamma_mn(gam, L, m, n, &Gr, &Gi);
                     double scr = s_vox ? s_vox[c * sstride] : 1.0, sci = s_vox ? s_vox[c * sstride + 1] : 0.0;
                     double sdr = s_vox ? s_vox[d * sstride] : 1.0, sdi = s_vox ? -s_vox[d * sstride + 1] : 0.0; /* conj(s_d) */
                     const double *ycm = y_vox + (long)(m * nc + c) * ystride;
@@ -91,9 +108,9 @@ static void pair_weights(int nc, int L, const double *y_vox, long ystride, const
                     /* * conj(y_cm) */
                     double qr = pr * ar - pi_ * ai, qi = pr * ai + pi_ * ar;
                     /* * y_dn */
-                    double rr = qr * br - qi * bi, ri = qr * bi + qi * br;
-                    rr *= G / S;
-                    ri *= G / S;
+                    double ur = qr * br - qi * bi, ui = qr * bi + qi * br;
+                    /* * Gamma_mn / S */
+                    double rr = (Gr * ur - Gi * ui) / S, ri = (Gr * ui + Gi * ur) / S;
                     rabs[t] = hypot(rr, ri);
                     rang[t] = atan2(ri, rr);
                 }
@@ -159,7 +176,7 @@ int orc_create(orc_t **out, int nx, int ny, int nz, int nc, int L, const double 
     for (long j = 0; j < h->nv; ++j) {
         long k = h->slot[j];
         if (k < 0) continue;
-        pair_weights(nc, L, h->y + 2 * j, 2 * h->nv, h->s ? h->s + 2 * j : NULL, 2 * h->nv,
+        pair_weights(nc, L, h->y + 2 * j, 2 * h->nv, h->s ? h->s + 2 * j : NULL, 2 * h->nv, NULL,
                      h->rabs + k * h->T, h->rang + k * h->T);
     }
     *out = h;
@@ -277,6 +294,204 @@ void orc_curv(const orc_t *h, const double *w, double *d) {
         if (h->curv_mode == 1) d[j] = voxel_curv_combined(h, h->rabs + k * h->T, h->rang + k * h->T, w[j]);
         else voxel_terms(h->T, h->rabs + k * h->T, h->rang + k * h->T, h->dt, w[j], NULL, NULL, d + j);
     }
+}
+
+/* Second derivative of Phi_j (Eq. 2) at w: sum |r| (t_m - t_n)^2 cos(angle r + w (t_m - t_n)),
+ * the diagonal of the true Hessian of the data term (used for implicit differentiation of the
+ * converged field map, not by the solver).  Zero outside the mask. */
+void orc_hess_diag(const orc_t *h, const double *w, double *out) {
+    for (long j = 0; j < h->nv; ++j) {
+        long k = h->slot[j];
+        if (k < 0) { out[j] = 0.0; continue; }
+        const double *ra = h->rabs + k * h->T, *rg = h->rang + k * h->T;
+        double acc = 0.0;
+        for (long t = 0; t < h->T; ++t) acc += ra[t] * h->dt[t] * h->dt[t] * cos(rg[t] + w[j] * h->dt[t]);
+        out[j] = acc;
+    }
+}
+
+/* Directional derivative of (grad Phi)_j (Eq. 8) with respect to the images y in the complex
+ * direction dy ([L][nc][nv], interleaved): product rule on Eq. 3,
+ * d r_cdmn = Gamma_mn/S s_c conj(s_d) (conj(dy_cm) y_dn + conj(y_cm) dy_dn), and
+ * d (grad Phi)_j = sum (t_m - t_n) Im(d r e^{i w (t_m - t_n)}).  Zero outside the mask. */
+void orc_dgrad_dy(const orc_t *h, const double *w, const double *dy, double *out) {
+    const int nc = h->nc, L = h->L;
+    const double *gam = h->has_gam ? h->gam : NULL;
+    for (long j = 0; j < h->nv; ++j) {
+        if (!h->mask[j]) { out[j] = 0.0; continue; }
+        double S = 0.0;
+        for (int c = 0; c < nc; ++c) {
+            double sr = h->s ? h->s[2 * (c * h->nv + j)] : 1.0, si = h->s ? h->s[2 * (c * h->nv + j) + 1] : 0.0;
+            S += sr * sr + si * si;
+        }
+        if (S == 0.0) { out[j] = 0.0; continue; }
+        double acc = 0.0;
+        for (int c = 0; c < nc; ++c)
+            for (int d = 0; d < nc; ++d)
+                for (int m = 0; m < L; ++m)
+                    for (int n = 0; n < L; ++n) {
+                        double scr = h->s ? h->s[2 * (c * h->nv + j)] : 1.0, sci = h->s ? h->s[2 * (c * h->nv + j) + 1] : 0.0;
+                        double sdr = h->s ? h->s[2 * (d * h->nv + j)] : 1.0, sdi = h->s ? -h->s[2 * (d * h->nv + j) + 1] : 0.0;
+                        double pr = scr * sdr - sci * sdi, pi_ = scr * sdi + sci * sdr; /* s_c conj(s_d) */
+                        const double *ycm = h->y + 2 * ((long)(m * nc + c) * h->nv + j);
+                        const double *ydn = h->y + 2 * ((long)(n * nc + d) * h->nv + j);
+                        const double *dcm = dy + 2 * ((long)(m * nc + c) * h->nv + j);
+                        const double *ddn = dy + 2 * ((long)(n * nc + d) * h->nv + j);
+                        /* conj(dy_cm) y_dn + conj(y_cm) dy_dn */
+                        double ar = dcm[0] * ydn[0] + dcm[1] * ydn[1], ai = dcm[0] * ydn[1] - dcm[1] * ydn[0];
+                        double br = ycm[0] * ddn[0] + ycm[1] * ddn[1], bi = ycm[0] * ddn[1] - ycm[1] * ddn[0];
+                        double qr = ar + br, qi = ai + bi;
+                        double Gr, Gi;
+                        gamma_mn(gam, L, m, n, &Gr, &Gi);
+                        double er = pr * Gr - pi_ * Gi, ei = pr * Gi + pi_ * Gr; /* Gamma_mn s_c conj(s_d) */
+                        double rr = (er * qr - ei * qi) / S, ri = (er * qi + ei * qr) / S;
+                        double dt = h->te[m] - h->te[n];
+                        double th = w[j] * dt;
+                        acc += dt * (rr * sin(th) + ri * cos(th)); /* Im(dr e^{i th}) */
+                    }
+        out[j] = acc;
+    }
+}
+
+/* Adjoint of orc_dgrad_dy: out = sum_j lam_j grad_y (grad Phi)_j as a complex array
+ * [L][nc][nv] (interleaved), in the convention out = d/dRe y + i d/dIm y.  Each term
+ * f = (t_m - t_n) Im(A conj(y_cm) y_dn), A = Gamma/S s_c conj(s_d) e^{i w (t_m - t_n)},
+ * contributes -i (t_m - t_n) A y_dn to y_cm and i (t_m - t_n) conj(A) y_cm to y_dn. */
+void orc_dgrad_dy_adj(const orc_t *h, const double *w, const double *lam, double *out) {
+    const int nc = h->nc, L = h->L;
+    const double *gam = h->has_gam ? h->gam : NULL;
+    for (long i = 0; i < 2L * L * nc * h->nv; ++i) out[i] = 0.0;
+    for (long j = 0; j < h->nv; ++j) {
+        if (!h->mask[j] || lam[j] == 0.0) continue;
+        double S = 0.0;
+        for (int c = 0; c < nc; ++c) {
+            double sr = h->s ? h->s[2 * (c * h->nv + j)] : 1.0, si = h->s ? h->s[2 * (c * h->nv + j) + 1] : 0.0;
+            S += sr * sr + si * si;
+        }
+        if (S == 0.0) continue;
+        for (int c = 0; c < nc; ++c)
+            for (int d = 0; d < nc; ++d)
+                for (int m = 0; m < L; ++m)
+                    for (int n = 0; n < L; ++n) {
+                        double dt = h->te[m] - h->te[n];
+                        if (dt == 0.0) continue;
+                        double scr = h->s ? h->s[2 * (c * h->nv + j)] : 1.0, sci = h->s ? h->s[2 * (c * h->nv + j) + 1] : 0.0;
+                        double sdr = h->s ? h->s[2 * (d * h->nv + j)] : 1.0, sdi = h->s ? -h->s[2 * (d * h->nv + j) + 1] : 0.0;
+                        double pr = scr * sdr - sci * sdi, pi_ = scr * sdi + sci * sdr; /* s_c conj(s_d) */
+                        double th = w[j] * dt, ct = cos(th), st = sin(th);
+                        double Gr, Gi;
+                        gamma_mn(gam, L, m, n, &Gr, &Gi);
+                        double er = pr * Gr - pi_ * Gi, ei = pr * Gi + pi_ * Gr; /* Gamma_mn s_c conj(s_d) */
+                        double Ar = (er * ct - ei * st) / S, Ai = (er * st + ei * ct) / S;
+                        const double *ycm = h->y + 2 * ((long)(m * nc + c) * h->nv + j);
+                        const double *ydn = h->y + 2 * ((long)(n * nc + d) * h->nv + j);
+                        double *ocm = out + 2 * ((long)(m * nc + c) * h->nv + j);
+                        double *odn = out + 2 * ((long)(n * nc + d) * h->nv + j);
+                        double k = lam[j] * dt;
+                        /* -i A y_dn */
+                        double ur = Ar * ydn[0] - Ai * ydn[1], ui = Ar * ydn[1] + Ai * ydn[0];
+                        ocm[0] += k * ui;
+                        ocm[1] -= k * ur;
+                        /* i conj(A) y_cm */
+                        double vr = Ar * ycm[0] + Ai * ycm[1], vi = Ar * ycm[1] - Ai * ycm[0];
+                        odn[0] -= k * vi;
+                        odn[1] += k * vr;
+                    }
+    }
+}
+
+/* Water-fat model (Eq. gamma): replace Gamma_mn = 1/L by the complex L x L matrix gam
+ * (interleaved, row m, column n) and recompute every r_cdmnj (Eq. 3). */
+int orc_set_gamma(orc_t *h, const double *gam) {
+    if (!h || !gam) return ORC_ERR_ARG;
+    const int L = h->L;
+    for (int i = 0; i < 2 * L * L; ++i) h->gam[i] = gam[i];
+    h->has_gam = 1;
+    for (long j = 0; j < h->nv; ++j) {
+        long k = h->slot[j];
+        if (k < 0) continue;
+        pair_weights(h->nc, L, h->y + 2 * j, 2 * h->nv, h->s ? h->s + 2 * j : NULL, 2 * h->nv, h->gam,
+                     h->rabs + k * h->T, h->rang + k * h->T);
+    }
+    return ORC_OK;
+}
+
+/* Spatial weights of the PWLS initialisation (Eq. w0_wf): rho_j = sum_{c,d,m,n} |r_cdmnj|. */
+void orc_rho(const orc_t *h, double *out) {
+    for (long j = 0; j < h->nv; ++j) {
+        long k = h->slot[j];
+        double acc = 0.0;
+        if (k >= 0)
+            for (long t = 0; t < h->T; ++t) acc += h->rabs[k * h->T + t];
+        out[j] = acc;
+    }
+}
+
+/* Voxel-wise initialisation of the water-fat case (Sec. III-A): evaluate Phi_j (Eq. 2) at
+ * nsweep equally spaced values from wlo to whi (both included) and keep the first value
+ * with the smallest cost.  Zero outside the mask. */
+void orc_wf_sweep(const orc_t *h, int nsweep, double wlo, double whi, double *out) {
+    for (long j = 0; j < h->nv; ++j) {
+        long k = h->slot[j];
+        if (k < 0) { out[j] = 0.0; continue; }
+        double best = 0.0, best_phi = 0.0;
+        for (int q = 0; q < nsweep; ++q) {
+            double w = nsweep > 1 ? wlo + (whi - wlo) * (double)q / (double)(nsweep - 1) : wlo;
+            double phi;
+            voxel_terms(h->T, h->rabs + k * h->T, h->rang + k * h->T, h->dt, w, &phi, NULL, NULL);
+            if (q == 0 || phi < best_phi) { best_phi = phi; best = w; }
+        }
+        out[j] = best;
+    }
+}
+
+/* A x with A = 2 diag(rho) + beta C'C on the mask (the Hessian of Eq. w0_wf); 0 outside. */
+static void pwls_apply(const orc_t *h, const double *rho, const double *x, double *ax) {
+    for (long j = 0; j < h->nv; ++j) {
+        if (!h->mask[j]) { ax[j] = 0.0; continue; }
+        double lap = 0.0;
+        for (int axis = 0; axis < 3; ++axis) {
+            long f = fwd_nbr(h, j, axis), b = bwd_nbr(h, j, axis);
+            if (f >= 0) lap += x[j] - x[f];
+            if (b >= 0) lap += x[j] - x[b];
+        }
+        ax[j] = 2.0 * rho[j] * x[j] + h->beta * lap;
+    }
+}
+
+/* PWLS initialisation (Eq. w0_wf): niter iterations of conjugate gradients on
+ * (2 diag(rho) + beta C'C) w = 2 rho wt, starting from w = wt (the sweep's map). */
+int orc_pwls(const orc_t *h, const double *wt, int niter, double *out) {
+    const long nv = h->nv;
+    double *rho = (double *)malloc(sizeof(double) * nv), *r = (double *)malloc(sizeof(double) * nv);
+    double *p = (double *)malloc(sizeof(double) * nv), *q = (double *)malloc(sizeof(double) * nv);
+    if (!rho || !r || !p || !q) { free(rho); free(r); free(p); free(q); return ORC_ERR_OOM; }
+    orc_rho(h, rho);
+    for (long j = 0; j < nv; ++j) out[j] = h->mask[j] ? wt[j] : 0.0;
+    pwls_apply(h, rho, out, q);
+    double rr = 0.0;
+    for (long j = 0; j < nv; ++j) {
+        r[j] = h->mask[j] ? 2.0 * rho[j] * wt[j] - q[j] : 0.0;
+        p[j] = r[j];
+        rr += r[j] * r[j];
+    }
+    for (int it = 0; it < niter && rr > 0.0; ++it) {
+        pwls_apply(h, rho, p, q);
+        double pq = 0.0;
+        for (long j = 0; j < nv; ++j) pq += p[j] * q[j];
+        if (!(pq > 0.0)) break;
+        double alpha = rr / pq, rr_new = 0.0;
+        for (long j = 0; j < nv; ++j) {
+            out[j] += alpha * p[j];
+            r[j] -= alpha * q[j];
+            rr_new += r[j] * r[j];
+        }
+        double b = rr_new / rr;
+        for (long j = 0; j < nv; ++j) p[j] = r[j] + b * p[j];
+        rr = rr_new;
+    }
+    free(rho); free(r); free(p); free(q);
+    return ORC_OK;
 }
 
 /* Eq. 6: initial field map from the first two echoes; zero outside the mask */
@@ -475,7 +690,7 @@ int orc_voxel(int nc, int L, const double *te, const double *y_vox, const double
     double *ra = (double *)malloc(sizeof(double) * T), *rg = (double *)malloc(sizeof(double) * T);
     double *dt = (double *)malloc(sizeof(double) * T);
     if (!ra || !rg || !dt) { free(ra); free(rg); free(dt); return ORC_ERR_OOM; }
-    pair_weights(nc, L, y_vox, 2, s_vox, 2, ra, rg);
+    pair_weights(nc, L, y_vox, 2, s_vox, 2, NULL, ra, rg);
     tuple_dt(nc, L, te, dt);
     voxel_terms(T, ra, rg, dt, w, out, out + 1, out + 2);
     free(ra); free(rg); free(dt);
@@ -485,6 +700,6 @@ int orc_voxel(int nc, int L, const double *te, const double *y_vox, const double
 /* raw r_cdmnj of Eq. 3 for one voxel (modulus, angle), T = nc*nc*L*L, order c,d,m,n */
 int orc_voxel_r(int nc, int L, const double *y_vox, const double *s_vox, double *rabs, double *rang) {
     if (nc < 1 || L < 2 || L > ORC_MAXL) return ORC_ERR_ARG;
-    pair_weights(nc, L, y_vox, 2, s_vox, 2, rabs, rang);
+    pair_weights(nc, L, y_vox, 2, s_vox, 2, NULL, rabs, rang);
     return ORC_OK;
 }

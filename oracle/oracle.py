@@ -56,6 +56,20 @@ def _lib():
             getattr(lib, name).argtypes = [vp, _dp, _dp]
             getattr(lib, name).restype = None
         lib.orc_init.argtypes = [vp, _dp]
+        lib.orc_hess_diag.argtypes = [vp, _dp, _dp]
+        lib.orc_hess_diag.restype = None
+        lib.orc_dgrad_dy.argtypes = [vp, _dp, _dp, _dp]
+        lib.orc_dgrad_dy.restype = None
+        lib.orc_dgrad_dy_adj.argtypes = [vp, _dp, _dp, _dp]
+        lib.orc_dgrad_dy_adj.restype = None
+        lib.orc_set_gamma.argtypes = [vp, _dp]
+        lib.orc_set_gamma.restype = C.c_int
+        lib.orc_rho.argtypes = [vp, _dp]
+        lib.orc_rho.restype = None
+        lib.orc_wf_sweep.argtypes = [vp, C.c_int, C.c_double, C.c_double, _dp]
+        lib.orc_wf_sweep.restype = None
+        lib.orc_pwls.argtypes = [vp, _dp, C.c_int, _dp]
+        lib.orc_pwls.restype = C.c_int
         lib.orc_set_curvature.argtypes = [vp, C.c_int]
         lib.orc_set_curvature.restype = None
         lib.orc_num_unknowns.argtypes = [vp]
@@ -101,6 +115,7 @@ class Oracle:
         self.beta = float(beta)
         self.te = np.ascontiguousarray(te, dtype=np.float64)
         self._y = _c128(y)
+        self._yshape = y.shape
         self._s = _c128(smap) if smap is not None else None
         self._mask = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
         self.mask = (np.ones(self.shape, np.uint8) if mask is None else self._mask.reshape(self.shape))
@@ -115,6 +130,60 @@ class Oracle:
     @classmethod
     def from_volume(cls, vol):
         return cls(vol.y, vol.smap, vol.te, vol.mask, vol.beta)
+
+    def set_gamma(self, G):
+        """Water-fat model (Eq. gamma): use the complex L x L matrix G in place of 1/L in
+        Eq. 3 (see wf_gamma)."""
+        G = np.ascontiguousarray(G, dtype=np.complex128)
+        assert G.shape == (self.L, self.L)
+        st = self._lib.orc_set_gamma(self._h, G.view(np.float64).reshape(-1))
+        if st != ORC_OK:
+            raise RuntimeError(f"orc_set_gamma failed: {st}")
+        self.gamma = G
+
+    def rho(self):
+        """PWLS weights rho_j = sum |r_cdmnj| (Eq. w0_wf)."""
+        out = np.zeros(int(np.prod(self.shape)), np.float64)
+        self._lib.orc_rho(self._h, out)
+        return out.reshape(self.shape)
+
+    def wf_sweep(self, nsweep, wlo, whi):
+        """Voxel-wise minimiser of Phi_j over nsweep equally spaced values in [wlo, whi]."""
+        out = np.zeros(int(np.prod(self.shape)), np.float64)
+        self._lib.orc_wf_sweep(self._h, int(nsweep), float(wlo), float(whi), out)
+        return out.reshape(self.shape)
+
+    def pwls(self, wt, niter):
+        """niter CG iterations on the PWLS initialisation (Eq. w0_wf) from wt."""
+        out = np.zeros(int(np.prod(self.shape)), np.float64)
+        st = self._lib.orc_pwls(self._h, self._w(wt), int(niter), out)
+        if st != ORC_OK:
+            raise RuntimeError(f"orc_pwls failed: {st}")
+        return out.reshape(self.shape)
+
+    def wf_amplitudes(self, w, gamma_cols):
+        """Water and fat components by the closed form of Eq. wf: per mask voxel, the least-
+        squares solution u of ((gamma diag(e^{i w t})) kron s_j) u = y_j, with the matrix
+        formed literally and solved by numpy's pseudo-inverse.  Returns (m_w, m_f)."""
+        gcols = np.asarray(gamma_cols, dtype=np.complex128)
+        L, nc = self.L, self.nc
+        w = np.asarray(w, dtype=np.float64).reshape(-1)
+        m = self.mask.reshape(-1).astype(bool)
+        idx = np.nonzero(m)[0]
+        y = self._y.view(np.complex128).reshape(L, nc, -1)[:, :, idx]  # [L][nc][nm]
+        s = (self._s.view(np.complex128).reshape(nc, -1)[:, idx] if self._s is not None
+             else np.ones((nc, idx.size), np.complex128))
+        ph = np.exp(1j * w[idx][None, :] * self.te[:, None])  # [L][nm]
+        # B[j, (l, c), k] = e^{i w_j t_l} gamma_lk s_cj
+        B = (ph[:, None, None, :] * gcols[:, None, :, None] * s[None, :, None, :])  # [L][nc][2][nm]
+        B = np.moveaxis(B, 3, 0).reshape(idx.size, L * nc, gcols.shape[1])
+        yv = np.moveaxis(y, 2, 0).reshape(idx.size, L * nc)
+        u = np.einsum("jkq,jq->jk", np.linalg.pinv(B), yv)
+        out_w = np.zeros(m.size, np.complex128)
+        out_f = np.zeros(m.size, np.complex128)
+        out_w[idx] = u[:, 0]
+        out_f[idx] = u[:, 1]
+        return out_w.reshape(self.shape), out_f.reshape(self.shape)
 
     def set_curvature(self, mode):
         """'literal' (Eq. 10, default) or 'combined' (the labelled coil-combined variant)."""
@@ -159,6 +228,61 @@ class Oracle:
     def curv(self, w):
         return self._vec("orc_curv", w)
 
+    def hess_diag(self, w):
+        """Diagonal of the data term's true Hessian (second derivative of Eq. 2)."""
+        return self._vec("orc_hess_diag", w)
+
+    def dgrad_dy(self, w, dy):
+        """Directional derivative of grad Phi (Eq. 8) with respect to the images, direction dy."""
+        out = np.zeros(int(np.prod(self.shape)), np.float64)
+        d = _c128(dy).reshape(-1)
+        assert d.size == self._y.size
+        self._lib.orc_dgrad_dy(self._h, self._w(w), d, out)
+        return out.reshape(self.shape)
+
+    def dgrad_dy_adj(self, w, lam):
+        """sum_j lam_j grad_y (grad Phi)_j, complex [L][Nc][z][y][x] (d/dRe y + i d/dIm y)."""
+        out = np.zeros(self._y.size, np.float64)
+        self._lib.orc_dgrad_dy_adj(self._h, self._w(w), self._w(lam), out)
+        return out.view(np.complex128).reshape(self._yshape)
+
+    def laplacian(self):
+        """C'C over the mask voxels as a scipy sparse matrix on the grid (identity rows outside)."""
+        import scipy.sparse as sp
+        nz, ny, nx = self.shape
+        m = self.mask.reshape(-1).astype(bool)
+        idx = np.arange(m.size).reshape(self.shape)
+        rows, cols = [], []
+        for ax, n in ((2, nx), (1, ny), (0, nz)):
+            a = np.take(idx, np.arange(n - 1), axis=ax).reshape(-1)
+            b = np.take(idx, np.arange(1, n), axis=ax).reshape(-1)
+            keep = m[a] & m[b]
+            rows.append(a[keep])
+            cols.append(b[keep])
+        r = np.concatenate(rows)
+        c = np.concatenate(cols)
+        A = sp.coo_matrix((np.ones(r.size), (r, c)), shape=(m.size, m.size)).tocsr()
+        A = A + A.T
+        deg = np.asarray(A.sum(axis=1)).ravel()
+        return (sp.diags(deg) - A).tocsr()
+
+    def implicit_gradient(self, w_hat, dl_dw):
+        """Implicit differentiation of the converged map: solve H lam = dl/dw with the true
+        Hessian H = diag(hess_diag) + beta C'C on the mask voxels (scipy direct solve);
+        returns (lam, dl/dbeta = -lam' C'C w_hat, dl/dy = -sum_j lam_j grad_y (grad Phi)_j)."""
+        import scipy.sparse as sp
+        import scipy.sparse.linalg as spla
+        m = self.mask.reshape(-1).astype(bool)
+        Lap = self.laplacian()
+        H = (sp.diags(self.hess_diag(w_hat).reshape(-1)) + self.beta * Lap).tocsr()
+        Hm = H[m][:, m].tocsc()
+        v = np.ascontiguousarray(dl_dw, dtype=np.float64).reshape(-1)
+        lam = np.zeros(m.size)
+        lam[m] = spla.spsolve(Hm, v[m])
+        dl_dbeta = -float(lam @ (Lap @ np.ascontiguousarray(w_hat, np.float64).reshape(-1)))
+        lam = lam.reshape(self.shape)
+        return lam, dl_dbeta, -self.dgrad_dy_adj(w_hat, lam)
+
     def init(self):
         out = np.zeros(int(np.prod(self.shape)), np.float64)
         self._lib.orc_init(self._h, out)
@@ -186,6 +310,17 @@ class Oracle:
         if inner:
             out["inner"] = inn[: niter * nls].reshape(niter, nls)
         return out
+
+
+def wf_gamma(te, amps, freqs):
+    """The water-fat basis of Eq. gamma and its projector: gamma = [1, sum_p a_p
+    e^{i 2 pi f_p t}] (L x 2; freqs in cycles per unit of te) and
+    Gamma = gamma (gamma^H gamma)^{-1} gamma^H.  Returns (gamma, Gamma)."""
+    t = np.asarray(te, dtype=np.float64)
+    fat = np.exp(2j * np.pi * np.outer(t, np.asarray(freqs, np.float64))) @ np.asarray(amps, np.float64)
+    g = np.stack([np.ones_like(fat), fat], axis=1)
+    G = g @ np.linalg.inv(g.conj().T @ g) @ g.conj().T
+    return g, G
 
 
 def ic0_factor(shape, mask, d, beta):

@@ -3,6 +3,7 @@
 // (Algorithm box), replayed from a captured CUDA graph.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -25,6 +26,12 @@ struct fm_ctx {
     double beta = 0.0;
     double te[FM_MAX_ECHO] = {};
     Pairs pr{};
+    // water-fat model (Eq. gamma); set by fm_set_fat_model, applied by fm_set_data
+    bool wf = false;
+    std::vector<double> fat_amp, fat_freq;
+    double fat_re[FM_MAX_ECHO] = {}, fat_im[FM_MAX_ECHO] = {};  // phi_l = sum_p a_p e^{i 2 pi f_p t_l}
+    double ginv[8] = {};                                         // (gamma^H gamma)^{-1}
+    void* rho = nullptr;                                         // T compact [nv]: sum |r_cdmn|
     // device buffers
     void *pairs = nullptr, *coils = nullptr, *w0 = nullptr;
     uint8_t* nb = nullptr;
@@ -35,13 +42,18 @@ struct fm_ctx {
     void* face = nullptr;
     double *hist_cost = nullptr, *hist_alpha = nullptr, *hist_mu = nullptr;
     int hist_cap = 0;
+    int hist_gen = 0;      // bumped when the history buffers move (captured graphs hold them)
     int* istate = nullptr;
     int* icint = nullptr;  // [0] fwd ticket, [1] bwd ticket, [2] bwd done, [3] pad, flags fwd[nt], flags bwd[nt]
     int* order = nullptr;
     int ntx = 0, nty = 0, ntz = 0, ntiles = 0;
     int nsm = 0, grid_data = 0, grid_ls = 0, grid_ic = 0;
+    int base_data = 0, base_ls = 0, base_ic = 0;  // grids chosen at creation (batch autotuning scales them)
     int last_niter = 0;
     cudaGraphExec_t gexec = nullptr;
+    cudaGraphExec_t cg_gexec = nullptr;  // adjoint CG iterations (tolerance and limit are arguments)
+    double cg_tol2 = -1.0;
+    int cg_maxiter = -1;
     bool profiling = false;
     cudaEvent_t ev[2][FM_NKERNEL][2] = {};
     bool ev_rec[2][FM_NKERNEL] = {};
@@ -87,12 +99,13 @@ cudaError_t dalloc(P** ptr, size_t bytes) {
 
 void free_all(fm_ctx* c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->cg_gexec) cudaGraphExecDestroy(c->cg_gexec);
     for (auto& a : c->ev)
         for (auto& b : a)
             for (cudaEvent_t& e : b)
                 if (e) cudaEventDestroy(e);
     void* bufs[] = {c->pairs, c->coils, c->w0, c->nb, c->vlist, c->chunk_off, c->w[0], c->w[1], c->z[0], c->z[1], c->g[0],
-                    c->g[1], c->d, c->p, c->v, c->ip, c->scal, c->partials, c->face, c->tile_part,
+                    c->g[1], c->d, c->p, c->v, c->ip, c->scal, c->partials, c->face, c->tile_part, c->rho,
                     c->hist_cost, c->hist_alpha, c->hist_mu, c->istate, c->icint, c->order};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -124,6 +137,7 @@ DataArgs base_args(fm_ctx* c) {
     a.pr = c->pr;
     a.beta = c->beta;
     a.literal = c->literal ? 1 : 0;
+    a.wf = c->wf ? 1 : 0;
     a.pairs = c->pairs;
     a.coils = c->coils;
     a.nb = c->nb;
@@ -268,8 +282,9 @@ cudaError_t iteration(fm_ctx* c, int cur) {
     return e;
 }
 
+// Enqueue everything a solve needs before its first outer iteration.
 template <typename T>
-int solve_t(fm_ctx* c, void* omega, int init, int niter, double* cost_hist) {
+int solve_begin(fm_ctx* c, void* omega, int init, int niter) {
     if (niter + 1 > c->hist_cap) {
         if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
         cudaFree(c->hist_cost); cudaFree(c->hist_alpha); cudaFree(c->hist_mu);
@@ -280,6 +295,7 @@ int solve_t(fm_ctx* c, void* omega, int init, int niter, double* cost_hist) {
         FM_CK(dalloc(&c->hist_alpha, cap * sizeof(double)), "allocate history");
         FM_CK(dalloc(&c->hist_mu, cap * sizeof(double)), "allocate history");
         c->hist_cap = cap;
+        c->hist_gen++;
     }
     const size_t vb = (size_t)c->nv * c->ts;
     cudaStream_t s = c->stream;
@@ -299,6 +315,29 @@ int solve_t(fm_ctx* c, void* omega, int init, int niter, double* cost_hist) {
     FM_CK(cudaMemsetAsync(c->scal + S_ALPHA, 0, sizeof(double), s), "reset step");
     FM_CK(cudaMemsetAsync(c->scal + S_GP, 0, 4 * sizeof(double), s), "reset dots");
     FM_CK(cudaMemsetAsync(c->istate + I_ITER, 0, sizeof(int), s), "reset counter");
+    return FM_OK;
+}
+
+// Enqueue the last update, the copy of the field map out and of the cost history.
+template <typename T>
+int solve_end(fm_ctx* c, void* omega, int niter, double* cost_hist) {
+    const size_t vb = (size_t)c->nv * c->ts;
+    cudaStream_t s = c->stream;
+    const int cur = niter & 1;
+    FM_CK(run_grad<T>(c, c->w[cur], c->z[cur], c->w[cur ^ 1], c->g[cur], c->d, c->hist_cost), "final update");
+    FM_CK(cudaMemcpyAsync(omega, c->w[cur ^ 1], vb, cudaMemcpyDeviceToDevice, s), "copy omega out");
+    if (cost_hist)
+        FM_CK(cudaMemcpyAsync(cost_hist, c->hist_cost, (niter + 1) * sizeof(double), cudaMemcpyDeviceToHost, s),
+              "copy cost history");
+    c->last_niter = niter;
+    return FM_OK;
+}
+
+template <typename T>
+int solve_t(fm_ctx* c, void* omega, int init, int niter, double* cost_hist) {
+    int rc = solve_begin<T>(c, omega, init, niter);
+    if (rc != FM_OK) return rc;
+    cudaStream_t s = c->stream;
     int i = 0;
     if (c->o.use_graph && niter >= 2) {
         if (!c->gexec) {
@@ -316,14 +355,183 @@ int solve_t(fm_ctx* c, void* omega, int init, int niter, double* cost_hist) {
         for (; i + 2 <= niter; i += 2) FM_CK(cudaGraphLaunch(c->gexec, s), "launch graph");
     }
     for (; i < niter; ++i) FM_CK(iteration<T>(c, i & 1), "launch iteration");
-    const int cur = niter & 1;
-    FM_CK(run_grad<T>(c, c->w[cur], c->z[cur], c->w[cur ^ 1], c->g[cur], c->d, c->hist_cost), "final update");
-    FM_CK(cudaMemcpyAsync(omega, c->w[cur ^ 1], vb, cudaMemcpyDeviceToDevice, s), "copy omega out");
-    if (cost_hist)
-        FM_CK(cudaMemcpyAsync(cost_hist, c->hist_cost, (niter + 1) * sizeof(double), cudaMemcpyDeviceToHost, s),
-              "copy cost history");
-    c->last_niter = niter;
+    rc = solve_end<T>(c, omega, niter, cost_hist);
+    if (rc != FM_OK) return rc;
     return check_dev(c);
+}
+
+// ------------------------------------------------------------------ implicit differentiation
+
+AdjArgs adj_args(fm_ctx* c) {
+    AdjArgs a{};
+    a.geo = Geo{c->nx, c->ny, c->nz, c->nv};
+    a.nc = c->nc;
+    a.L = c->L;
+    a.pr = c->pr;
+    a.beta = c->beta;
+    for (int l = 0; l < FM_MAX_ECHO; ++l) a.te[l] = l < c->L ? c->te[l] : 0.0;
+    for (int l = 0; l < FM_MAX_ECHO; ++l) { a.fat_re[l] = c->fat_re[l]; a.fat_im[l] = c->fat_im[l]; }
+    for (int k = 0; k < 8; ++k) a.ginv[k] = c->ginv[k];
+    a.rho = c->rho;
+    a.pairs = c->pairs;
+    a.nb = c->nb;
+    a.vlist = c->vlist;
+    a.scal = c->scal;
+    a.partials = c->partials;
+    a.istate = c->istate;
+    return a;
+}
+
+constexpr int kCgPerGraph = 8;  // CG iterations per graph replay (even: the p buffers ping-pong)
+
+// Buffers of the adjoint CG (the solver's, which fm_solve re-initialises): x = w[0],
+// r = g[0], z = p, p ping-pong = z[0] / z[1], q = g[1], h = w[1].
+template <typename T>
+cudaError_t cg_iteration(fm_ctx* c, double tol2, int maxiter, int par) {
+    AdjArgs a = adj_args(c);
+    a.tol2 = tol2;
+    a.maxiter = maxiter;
+    a.x = c->w[0];
+    a.r = c->g[0];
+    a.z = c->p;
+    a.p_old = c->z[par];
+    a.p_new = c->z[par ^ 1];
+    a.q = c->g[1];
+    a.h = c->w[1];
+    cudaError_t e = launch_cg_dir<T>(a, c->grid_data, c->stream);
+    if (e == cudaSuccess) e = launch_cg_upd<T>(a, c->grid_data, c->stream);
+    if (e == cudaSuccess) e = run_ic<T>(c, nullptr, c->g[0], c->p, c->g[0], nullptr);
+    return e;
+}
+
+template <typename T>
+int adjoint_t(fm_ctx* c, const void* w_hat, const void* rhs, void* lambda, double tol, int maxiter, int* iters,
+              double* relres) {
+    cudaStream_t s = c->stream;
+    const size_t vb = (size_t)c->nv * c->ts;
+    const double tol2 = tol * tol;
+    FM_CK(cudaMemsetAsync(c->istate + I_ERR, 0, sizeof(int), s), "reset");
+    // majoriser curvature d(w_hat) for the preconditioner (Eq. 9-12)
+    FM_CK(run_grad<T>(c, w_hat, nullptr, c->w[1], c->g[1], c->d, nullptr), "curvature");
+    void* zero[] = {c->w[0], c->g[0], c->z[0], c->z[1], c->g[1]};
+    for (void* b : zero) FM_CK(cudaMemsetAsync(b, 0, vb, s), "clear CG vectors");
+    AdjArgs a = adj_args(c);
+    a.w = w_hat;
+    a.rhs = rhs;
+    a.h = c->w[1];
+    a.r = c->g[0];
+    a.maxiter = maxiter;
+    a.tol2 = tol2;
+    FM_CK(launch_cg_init<T>(a, c->grid_data, s), "CG start");
+    FM_CK(run_ic<T>(c, c->d, c->g[0], c->p, c->g[0], nullptr), "IC(0) factor");  // z_0 and r_0'z_0
+    c->have_factor = true;
+    if (c->cg_gexec && (c->cg_tol2 != tol2 || c->cg_maxiter != maxiter)) {
+        cudaGraphExecDestroy(c->cg_gexec);
+        c->cg_gexec = nullptr;
+    }
+    if (c->o.use_graph && !c->cg_gexec) {
+        cudaGraph_t graph = nullptr;
+        FM_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; i < kCgPerGraph && e == cudaSuccess; ++i) e = cg_iteration<T>(c, tol2, maxiter, i & 1);
+        cudaError_t ee = cudaStreamEndCapture(s, &graph);
+        if (e != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(c, e, "capture CG"); }
+        FM_CK(ee, "end capture");
+        cudaError_t ei = cudaGraphInstantiate(&c->cg_gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        FM_CK(ei, "instantiate graph");
+        c->cg_tol2 = tol2;
+        c->cg_maxiter = maxiter;
+    }
+    // every batch of kCgPerGraph iterations ends with a look at the device stop flag; the
+    // kernels themselves stop at convergence or at maxiter
+    const int nbatch = (maxiter + kCgPerGraph - 1) / kCgPerGraph;
+    for (int k = 0; k < nbatch; ++k) {
+        int st[2] = {0, 0};
+        FM_CK(cudaMemcpyAsync(st, c->istate + I_CG_IT, 2 * sizeof(int), cudaMemcpyDeviceToHost, s), "read state");
+        FM_CK(cudaStreamSynchronize(s), "synchronise");
+        if (st[1] != 0) break;
+        if (c->cg_gexec) {
+            FM_CK(cudaGraphLaunch(c->cg_gexec, s), "launch CG graph");
+        } else {
+            for (int i = 0; i < kCgPerGraph; ++i) FM_CK(cg_iteration<T>(c, tol2, maxiter, i & 1), "CG iteration");
+        }
+    }
+    FM_CK(cudaMemcpyAsync(lambda, c->w[0], vb, cudaMemcpyDeviceToDevice, s), "copy lambda");
+    int it = 0;
+    double sc[2] = {0.0, 0.0};
+    FM_CK(cudaMemcpyAsync(&it, c->istate + I_CG_IT, sizeof(int), cudaMemcpyDeviceToHost, s), "read state");
+    FM_CK(cudaMemcpyAsync(sc, c->scal + S_CG_RR, 2 * sizeof(double), cudaMemcpyDeviceToHost, s), "read state");
+    int rc = check_dev(c);
+    if (iters) *iters = it;
+    if (relres) *relres = sc[1] > 0.0 ? std::sqrt(sc[0] / sc[1]) : 0.0;
+    return rc;
+}
+
+template <typename T>
+int implicit_t(fm_ctx* c, const void* y, const void* smap, const void* w_hat, const void* lam, void* dl_dy,
+               double* dl_dbeta) {
+    AdjArgs a = adj_args(c);
+    a.w = w_hat;
+    a.lam = lam;
+    a.y = y;
+    a.smap = smap;
+    a.dldy = dl_dy;
+    FM_CK(cudaMemsetAsync(c->istate + I_ERR, 0, sizeof(int), c->stream), "reset");
+    if (dl_dy) FM_CK(launch_dldy<T>(a, c->grid_data, c->stream), "image derivative kernel");
+    if (dl_dbeta) {
+        FM_CK(launch_lap_dot<T>(a, c->grid_data, c->stream), "beta derivative kernel");
+        double dot = 0.0;
+        FM_CK(cudaMemcpyAsync(&dot, c->scal + S_ADJ_DOT, sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+              "copy");
+        int rc = check_dev(c);
+        if (rc != FM_OK) return rc;
+        *dl_dbeta = -dot;
+    }
+    return FM_OK;
+}
+
+// Cooperative line-search grid: every block must be co-resident, so the grid follows the
+// occupancy of the kernel variant the context launches.
+template <typename T>
+int pwls_t(fm_ctx* c, const void* wt, int niter, void* w0) {
+    cudaStream_t s = c->stream;
+    const size_t vb = (size_t)c->nv * c->ts;
+    FM_CK(cudaMemsetAsync(c->istate + I_ERR, 0, sizeof(int), s), "reset");
+    void* zero[] = {c->w[0], c->g[0], c->z[0], c->z[1], c->g[1]};
+    for (void* b : zero) FM_CK(cudaMemsetAsync(b, 0, vb, s), "clear CG vectors");
+    AdjArgs a = adj_args(c);
+    a.x0 = wt;
+    a.h = c->w[1];
+    a.x = c->w[0];
+    a.r = c->g[0];
+    a.z = c->g[0];  // no preconditioner: z = r
+    a.q = c->g[1];
+    a.maxiter = niter;
+    a.tol2 = 0.0;   // a fixed number of iterations (stops early only at r = 0)
+    a.identity_pc = 1;
+    FM_CK(launch_pwls_init<T>(a, c->grid_data, s), "PWLS start");
+    for (int i = 0; i < niter; ++i) {
+        a.p_old = c->z[i & 1];
+        a.p_new = c->z[(i & 1) ^ 1];
+        FM_CK(launch_cg_dir<T>(a, c->grid_data, s), "PWLS direction");
+        FM_CK(launch_cg_upd<T>(a, c->grid_data, s), "PWLS update");
+    }
+    FM_CK(cudaMemcpyAsync(w0, c->w[0], vb, cudaMemcpyDeviceToDevice, s), "copy omega");
+    return check_dev(c);
+}
+
+bool set_ls_grid(fm_ctx* c) {
+    DataArgs probe{};
+    probe.nc = c->nc;
+    probe.literal = c->literal;
+    probe.wf = c->wf;
+    const int occ = c->o.precision == FM_FP64 ? ls_max_blocks_per_sm<double>(probe) : ls_max_blocks_per_sm<float>(probe);
+    if (occ < 1) return false;
+    const long long nblk = (c->nv + kThreads - 1) / kThreads;
+    c->grid_ls = (int)std::max(1LL, std::min<long long>(nblk, (long long)occ * c->nsm));
+    c->base_ls = c->grid_ls;
+    return true;
 }
 
 bool valid_opts(const fm_opts& o) {
@@ -395,14 +603,7 @@ int fm_create(fm_ctx** out, int nx, int ny, int nz, int ncoil, int necho, const 
     if (cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return bail(FM_ERR_CUDA);
     const long long nblk = (c->nv + kThreads - 1) / kThreads;
     c->grid_data = (int)std::max(1LL, std::min<long long>(nblk, 4LL * c->nsm));
-    {
-        DataArgs probe{};
-        probe.nc = ncoil;
-        probe.literal = c->literal;
-        const int occ = o.precision == FM_FP64 ? ls_max_blocks_per_sm<double>(probe) : ls_max_blocks_per_sm<float>(probe);
-        if (occ < 1) return bail(FM_ERR_CUDA);
-        c->grid_ls = (int)std::max(1LL, std::min<long long>(nblk, (long long)occ * c->nsm));
-    }
+    if (!set_ls_grid(c)) return bail(FM_ERR_CUDA);
     c->ntx = (nx + kTileX - 1) / kTileX;
     c->nty = (ny + kTileY - 1) / kTileY;
     const int tz = o.precision == FM_FP64 ? ic_tz<double>() : ic_tz<float>();
@@ -413,6 +614,9 @@ int fm_create(fm_ctx** out, int nx, int ny, int nz, int ncoil, int necho, const 
         if (occ < 1) return bail(FM_ERR_CUDA);
         c->grid_ic = std::max(1, std::min(c->ntiles, occ * c->nsm));
     }
+    c->base_data = c->grid_data;
+    c->base_ls = c->grid_ls;
+    c->base_ic = c->grid_ic;
     const size_t vb = (size_t)c->nv * c->ts;
     const int P = necho * (necho - 1) / 2;
     bool ok = true;
@@ -425,7 +629,7 @@ int fm_create(fm_ctx** out, int nx, int ny, int nz, int ncoil, int necho, const 
     A(&c->chunk_off, (size_t)nchunks * sizeof(int));
     A(&c->w0, vb);
     for (int k = 0; k < 2; ++k) { A(&c->w[k], vb); A(&c->z[k], vb); A(&c->g[k], vb); }
-    A(&c->d, vb); A(&c->p, vb); A(&c->v, vb); A(&c->ip, vb);
+    A(&c->d, vb); A(&c->p, vb); A(&c->v, vb); A(&c->ip, vb); A(&c->rho, vb);
     A(&c->scal, S_NSCAL * sizeof(double));
     A(&c->partials, std::max<size_t>(8 * (size_t)std::max(c->grid_data, c->grid_ls), nchunks) * sizeof(double));
     A(&c->face, (size_t)c->ntiles *
@@ -475,16 +679,53 @@ int fm_set_data(fm_ctx* c, const void* y, const void* smap, const double* te, co
     DevGuard guard(c->device);
     c->beta = beta;
     for (int l = 0; l < c->L; ++l) c->te[l] = te[l];
+    // Eq. gamma: Gamma = 1/L, or gamma (gamma^H gamma)^{-1} gamma^H with gamma = [1, phi]
+    std::vector<std::complex<double>> lgam((size_t)c->L * c->L, std::complex<double>(1.0, 0.0));
+    if (c->wf) {
+        using cd = std::complex<double>;
+        std::vector<cd> phi(c->L);
+        for (int l = 0; l < c->L; ++l) {
+            cd acc(0.0, 0.0);
+            for (size_t q = 0; q < c->fat_amp.size(); ++q)
+                acc += c->fat_amp[q] * std::polar(1.0, 6.283185307179586476925286766559 * c->fat_freq[q] * te[l]);
+            phi[l] = acc;
+            c->fat_re[l] = acc.real();
+            c->fat_im[l] = acc.imag();
+        }
+        cd g01(0.0, 0.0);
+        double g11 = 0.0;
+        for (int l = 0; l < c->L; ++l) {
+            g01 += phi[l];
+            g11 += std::norm(phi[l]);
+        }
+        const double g00 = (double)c->L, det = g00 * g11 - std::norm(g01);
+        if (!(det > 1e-12 * g00 * g11)) return fail(c, FM_ERR_ARG, "fat basis is collinear with water at these echo times");
+        const cd i00 = g11 / det, i01 = -g01 / det, i10 = -std::conj(g01) / det, i11 = g00 / det;
+        const cd gi[4] = {i00, i01, i10, i11};
+        for (int k = 0; k < 4; ++k) { c->ginv[2 * k] = gi[k].real(); c->ginv[2 * k + 1] = gi[k].imag(); }
+        for (int m = 0; m < c->L; ++m)
+            for (int n = 0; n < c->L; ++n) {
+                // Gamma_mn = sum_{k,k'} gamma_mk Ginv_kk' conj(gamma_nk'), gamma_l0 = 1, gamma_l1 = phi_l
+                const cd gm[2] = {cd(1.0, 0.0), phi[m]}, gn[2] = {cd(1.0, 0.0), phi[n]};
+                cd acc(0.0, 0.0);
+                for (int k = 0; k < 2; ++k)
+                    for (int kk = 0; kk < 2; ++kk) acc += gm[k] * gi[2 * k + kk] * std::conj(gn[kk]);
+                lgam[(size_t)m * c->L + n] = (double)c->L * acc;
+            }
+    }
     Pairs pr{};
     for (int m = 0; m < c->L; ++m)
         for (int n = m + 1; n < c->L; ++n) {
             pr.m[pr.P] = m;
             pr.n[pr.P] = n;
             pr.dt[pr.P] = te[m] - te[n];
+            pr.gmag[pr.P] = std::abs(lgam[(size_t)m * c->L + n]);
+            pr.gph[pr.P] = c->wf ? std::arg(lgam[(size_t)m * c->L + n]) : 0.0;
             ++pr.P;
         }
     c->pr = pr;
     if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }  // beta / dt are graph arguments
+    if (c->cg_gexec) { cudaGraphExecDestroy(c->cg_gexec); c->cg_gexec = nullptr; }
     SetupArgs a{};
     a.geo = Geo{c->nx, c->ny, c->nz, c->nv};
     a.nc = c->nc;
@@ -495,6 +736,13 @@ int fm_set_data(fm_ctx* c, const void* y, const void* smap, const double* te, co
     a.mask = mask;
     a.te0 = te[0];
     a.te1 = te[1];
+    a.wf = c->wf ? 1 : 0;
+    for (int m = 0; m < c->L; ++m)
+        for (int n = 0; n < c->L; ++n) {
+            a.lgam[2 * (m * c->L + n)] = lgam[(size_t)m * c->L + n].real();
+            a.lgam[2 * (m * c->L + n) + 1] = lgam[(size_t)m * c->L + n].imag();
+        }
+    a.rho = c->rho;
     a.pairs = c->pairs;
     a.coils = c->coils;
     a.nb = c->nb;
@@ -582,6 +830,112 @@ int fm_solve(fm_ctx* c, void* omega, int init_from_data, int niter, double* cost
                                      : solve_t<float>(c, omega, init_from_data, niter, cost_hist);
 }
 
+int fm_true_curv(fm_ctx* c, const void* omega, void* h) {
+    if (!c) return FM_ERR_ARG;
+    if (!omega || !h) return fail(c, FM_ERR_ARG, "omega and h are required");
+    if (!c->have_data) return fail(c, FM_ERR_STATE, "fm_set_data first");
+    DevGuard guard(c->device);
+    FM_CK(cudaMemsetAsync(h, 0, (size_t)c->nv * c->ts, c->stream), "clear");
+    AdjArgs a = adj_args(c);
+    a.w = omega;
+    a.h = h;
+    cudaError_t e = c->o.precision == FM_FP64 ? launch_true_curv<double>(a, c->grid_data, c->stream)
+                                              : launch_true_curv<float>(a, c->grid_data, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "true curvature kernel");
+    return FM_OK;
+}
+
+int fm_adjoint_solve(fm_ctx* c, const void* omega_hat, const void* rhs, void* lambda, double tol, int maxiter,
+                     int* iters, double* relres) {
+    if (!c) return FM_ERR_ARG;
+    if (!omega_hat || !rhs || !lambda) return fail(c, FM_ERR_ARG, "omega_hat, rhs and lambda are required");
+    if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(c, FM_ERR_ARG, "tol must be finite and >= 0");
+    if (maxiter < 0) return fail(c, FM_ERR_ARG, "maxiter must be >= 0");
+    if (!c->have_data) return fail(c, FM_ERR_STATE, "fm_set_data first");
+    DevGuard guard(c->device);
+    return c->o.precision == FM_FP64 ? adjoint_t<double>(c, omega_hat, rhs, lambda, tol, maxiter, iters, relres)
+                                     : adjoint_t<float>(c, omega_hat, rhs, lambda, tol, maxiter, iters, relres);
+}
+
+int fm_implicit_grad(fm_ctx* c, const void* y, const void* smap, const void* omega_hat, const void* lambda,
+                     void* dl_dy, double* dl_dbeta) {
+    if (!c) return FM_ERR_ARG;
+    if (!omega_hat || !lambda) return fail(c, FM_ERR_ARG, "omega_hat and lambda are required");
+    if (dl_dy && !y) return fail(c, FM_ERR_ARG, "dl_dy needs y");
+    if (dl_dy && !smap && c->nc != 1) return fail(c, FM_ERR_ARG, "smap may be NULL only with one coil");
+    if (dl_dy && c->wf) return fail(c, FM_ERR_STATE, "dl_dy is implemented for the field-map model only");
+    if (!c->have_data) return fail(c, FM_ERR_STATE, "fm_set_data first");
+    DevGuard guard(c->device);
+    return c->o.precision == FM_FP64 ? implicit_t<double>(c, y, smap, omega_hat, lambda, dl_dy, dl_dbeta)
+                                     : implicit_t<float>(c, y, smap, omega_hat, lambda, dl_dy, dl_dbeta);
+}
+
+int fm_set_fat_model(fm_ctx* c, int npeak, const double* rel_amp, const double* freq) {
+    if (!c) return FM_ERR_ARG;
+    if (npeak < 0 || npeak > 64) return fail(c, FM_ERR_ARG, "npeak must be in 0..64");
+    if (npeak > 0 && (!rel_amp || !freq)) return fail(c, FM_ERR_ARG, "rel_amp and freq are required");
+    for (int q = 0; q < npeak; ++q)
+        if (!std::isfinite(rel_amp[q]) || !std::isfinite(freq[q]))
+            return fail(c, FM_ERR_ARG, "fat amplitudes and frequencies must be finite");
+    DevGuard guard(c->device);
+    c->wf = npeak > 0;
+    c->fat_amp.assign(rel_amp, rel_amp + npeak);
+    c->fat_freq.assign(freq, freq + npeak);
+    for (int l = 0; l < FM_MAX_ECHO; ++l) c->fat_re[l] = c->fat_im[l] = 0.0;
+    for (double& g : c->ginv) g = 0.0;
+    if (!set_ls_grid(c)) return fail(c, FM_ERR_CUDA, "occupancy query");
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    if (c->cg_gexec) { cudaGraphExecDestroy(c->cg_gexec); c->cg_gexec = nullptr; }
+    c->have_data = false;  // the pair weights depend on Gamma: fm_set_data again
+    c->have_factor = false;
+    return FM_OK;
+}
+
+int fm_wf_sweep(fm_ctx* c, int nsweep, double w_lo, double w_hi, void* omega_tilde) {
+    if (!c) return FM_ERR_ARG;
+    if (!omega_tilde) return fail(c, FM_ERR_ARG, "omega_tilde is required");
+    if (nsweep < 1 || !std::isfinite(w_lo) || !std::isfinite(w_hi))
+        return fail(c, FM_ERR_ARG, "nsweep >= 1 and finite bounds are required");
+    if (!c->have_data) return fail(c, FM_ERR_STATE, "fm_set_data first");
+    DevGuard guard(c->device);
+    FM_CK(cudaMemsetAsync(omega_tilde, 0, (size_t)c->nv * c->ts, c->stream), "clear");
+    AdjArgs a = adj_args(c);
+    a.x = omega_tilde;
+    cudaError_t e = c->o.precision == FM_FP64 ? launch_wf_sweep<double>(a, nsweep, w_lo, w_hi, c->grid_data, c->stream)
+                                              : launch_wf_sweep<float>(a, nsweep, w_lo, w_hi, c->grid_data, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "sweep kernel");
+    return FM_OK;
+}
+
+int fm_pwls_init(fm_ctx* c, const void* omega_tilde, int niter, void* omega0) {
+    if (!c) return FM_ERR_ARG;
+    if (!omega_tilde || !omega0) return fail(c, FM_ERR_ARG, "omega_tilde and omega0 are required");
+    if (niter < 0) return fail(c, FM_ERR_ARG, "niter must be >= 0");
+    if (!c->have_data) return fail(c, FM_ERR_STATE, "fm_set_data first");
+    DevGuard guard(c->device);
+    c->have_factor = false;  // the solver's work buffers are reused
+    return c->o.precision == FM_FP64 ? pwls_t<double>(c, omega_tilde, niter, omega0)
+                                     : pwls_t<float>(c, omega_tilde, niter, omega0);
+}
+
+int fm_wf_amplitudes(fm_ctx* c, const void* y, const void* smap, const void* omega, void* water, void* fat) {
+    if (!c) return FM_ERR_ARG;
+    if (!y || !omega || !water || !fat) return fail(c, FM_ERR_ARG, "y, omega, water and fat are required");
+    if (!smap && c->nc != 1) return fail(c, FM_ERR_ARG, "smap may be NULL only with one coil");
+    if (!c->have_data || !c->wf) return fail(c, FM_ERR_STATE, "fm_set_fat_model and fm_set_data first");
+    DevGuard guard(c->device);
+    AdjArgs a = adj_args(c);
+    a.y = y;
+    a.smap = smap;
+    a.w = omega;
+    a.water = water;
+    a.fat = fat;
+    cudaError_t e = c->o.precision == FM_FP64 ? launch_wf_amp<double>(a, c->grid_data, c->stream)
+                                              : launch_wf_amp<float>(a, c->grid_data, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "amplitude kernel");
+    return FM_OK;
+}
+
 int fm_set_profiling(fm_ctx* c, int on) {
     if (!c) return FM_ERR_ARG;
     DevGuard guard(c->device);
@@ -632,6 +986,256 @@ int fm_get_history(fm_ctx* c, double* alpha_hist, double* mu_hist, int n) {
     if (mu_hist)
         FM_CK(cudaMemcpyAsync(mu_hist, c->hist_mu, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy");
     FM_CK(cudaStreamSynchronize(c->stream), "synchronise");
+    return FM_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batched form
+
+struct fm_batch {
+    std::vector<fm_ctx*> v;
+    int device = 0;
+    int precision = FM_FP32;
+    cudaStream_t origin = nullptr;
+    bool own_origin = false;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<int> gen;  // history generations the captured graph was built with
+    double fraction = 1.0;
+    std::string err;
+};
+
+namespace {
+
+void batch_free(fm_batch* b) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    for (cudaEvent_t e : b->join)
+        if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    for (fm_ctx* c : b->v) fm_destroy(c);
+    if (b->own_origin && b->origin) cudaStreamDestroy(b->origin);
+}
+
+void batch_apply_fraction(fm_batch* b) {
+    for (fm_ctx* c : b->v) {
+        c->grid_data = std::max(1, (int)std::lround(c->base_data * b->fraction));
+        c->grid_ls = std::max(1, (int)std::lround(c->base_ls * b->fraction));
+        c->grid_ic = std::max(1, (int)std::lround(c->base_ic * b->fraction));
+        if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    }
+    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+}
+
+// origin -> every volume stream
+cudaError_t batch_fork(fm_batch* b) {
+    cudaError_t e = cudaEventRecord(b->fork, b->origin);
+    for (fm_ctx* c : b->v)
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, b->fork, 0);
+    return e;
+}
+
+// every volume stream -> origin
+cudaError_t batch_join(fm_batch* b) {
+    cudaError_t e = cudaSuccess;
+    for (size_t k = 0; k < b->v.size() && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(b->join[k], b->v[k]->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, b->join[k], 0);
+    }
+    return e;
+}
+
+template <typename T>
+int batch_solve_t(fm_batch* b, void* const* omega, int init, int niter, double* const* cost_hist) {
+    const size_t n = b->v.size();
+    auto fail_b = [&](int code, const std::string& m) { b->err = m; return code; };
+    if (batch_fork(b) != cudaSuccess) return fail_b(FM_ERR_CUDA, "fork");
+    for (size_t k = 0; k < n; ++k) {
+        const int rc = solve_begin<T>(b->v[k], omega[k], init, niter);
+        if (rc != FM_OK) return fail_b(rc, "volume " + std::to_string(k) + ": " + b->v[k]->err);
+    }
+    int i = 0;
+    if (niter >= 2) {
+        bool stale = !b->gexec || b->gen.size() != n;
+        for (size_t k = 0; k < n && !stale; ++k) stale = b->gen[k] != b->v[k]->hist_gen;
+        if (stale) {
+            if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) e = batch_fork(b);
+            for (size_t k = 0; k < n && e == cudaSuccess; ++k) {
+                e = iteration<T>(b->v[k], 0);
+                if (e == cudaSuccess) e = iteration<T>(b->v[k], 1);
+            }
+            if (e == cudaSuccess) e = batch_join(b);
+            cudaError_t ee = cudaStreamEndCapture(b->origin, &graph);
+            if (e != cudaSuccess || ee != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                return fail_b(FM_ERR_CUDA, std::string("capture batch iteration: ") +
+                                               cudaGetErrorString(e != cudaSuccess ? e : ee));
+            }
+            e = cudaGraphInstantiate(&b->gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return fail_b(FM_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+            b->gen.resize(n);
+            for (size_t k = 0; k < n; ++k) b->gen[k] = b->v[k]->hist_gen;
+        }
+        // the volumes' set-up work runs on their own streams before the graph
+        if (batch_join(b) != cudaSuccess) return fail_b(FM_ERR_CUDA, "join");
+        for (; i + 2 <= niter; i += 2)
+            if (cudaGraphLaunch(b->gexec, b->origin) != cudaSuccess) return fail_b(FM_ERR_CUDA, "launch graph");
+        if (batch_fork(b) != cudaSuccess) return fail_b(FM_ERR_CUDA, "fork");
+    }
+    for (size_t k = 0; k < n; ++k) {
+        fm_ctx* c = b->v[k];
+        for (int ii = i; ii < niter; ++ii)
+            if (iteration<T>(c, ii & 1) != cudaSuccess) return fail_b(FM_ERR_CUDA, "launch iteration");
+        const int rc = solve_end<T>(c, omega[k], niter, cost_hist ? cost_hist[k] : nullptr);
+        if (rc != FM_OK) return fail_b(rc, "volume " + std::to_string(k) + ": " + c->err);
+    }
+    if (batch_join(b) != cudaSuccess) return fail_b(FM_ERR_CUDA, "join");
+    int first = FM_OK;
+    for (size_t k = 0; k < n; ++k) {
+        const int rc = check_dev(b->v[k]);
+        if (rc != FM_OK && first == FM_OK) {
+            first = rc;
+            b->err = "volume " + std::to_string(k) + ": " + b->v[k]->err;
+        }
+    }
+    return first;
+}
+
+int batch_solve(fm_batch* b, void* const* omega, int init, int niter, double* const* cost_hist) {
+    return b->precision == FM_FP64 ? batch_solve_t<double>(b, omega, init, niter, cost_hist)
+                                   : batch_solve_t<float>(b, omega, init, niter, cost_hist);
+}
+
+}  // namespace
+
+extern "C" {
+
+int fm_batch_create(fm_batch** out, int n, const int* dims, const fm_opts* opts, int device, void* cuda_stream) {
+    if (!out) return FM_ERR_ARG;
+    *out = nullptr;
+    if (n < 1 || !dims) return FM_ERR_ARG;
+    fm_batch* b = new (std::nothrow) fm_batch();
+    if (!b) return FM_ERR_OOM;
+    b->device = device;
+    fm_opts o;
+    fm_default_opts(&o);
+    if (opts) o = *opts;
+    b->precision = o.precision;
+    for (int k = 0; k < n; ++k) {
+        fm_ctx* c = nullptr;
+        const int* d = dims + 5 * k;
+        const int rc = fm_create(&c, d[0], d[1], d[2], d[3], d[4], &o, device, nullptr);
+        if (rc != FM_OK) {
+            batch_free(b);
+            delete b;
+            return rc;
+        }
+        b->v.push_back(c);
+    }
+    DevGuard guard(device);
+    bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+    b->join.assign(n, nullptr);
+    for (int k = 0; k < n && ok; ++k) ok = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming) == cudaSuccess;
+    if (ok) {
+        if (cuda_stream) {
+            b->origin = (cudaStream_t)cuda_stream;
+        } else {
+            ok = cudaStreamCreate(&b->origin) == cudaSuccess;
+            b->own_origin = ok;
+        }
+    }
+    if (!ok) {
+        batch_free(b);
+        delete b;
+        return FM_ERR_CUDA;
+    }
+    *out = b;
+    return FM_OK;
+}
+
+int fm_batch_set_data(fm_batch* b, int k, const void* y, const void* smap, const double* te, const uint8_t* mask,
+                      double beta) {
+    if (!b || k < 0 || k >= (int)b->v.size()) return FM_ERR_ARG;
+    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }  // beta / dt are graph arguments
+    return fm_set_data(b->v[k], y, smap, te, mask, beta);
+}
+
+int fm_batch_solve(fm_batch* b, void* const* omega, int init_from_data, int niter, double* const* cost_hist) {
+    if (!b || !omega || niter < 0) return FM_ERR_ARG;
+    for (size_t k = 0; k < b->v.size(); ++k) {
+        if (!omega[k]) return FM_ERR_ARG;
+        if (!b->v[k]->have_data) return FM_ERR_STATE;
+    }
+    DevGuard guard(b->device);
+    return batch_solve(b, omega, init_from_data, niter, cost_hist);
+}
+
+int fm_batch_set_fraction(fm_batch* b, double fraction) {
+    if (!b || !(fraction > 0.0) || fraction > 1.0) return FM_ERR_ARG;
+    DevGuard guard(b->device);
+    b->fraction = fraction;
+    batch_apply_fraction(b);
+    return FM_OK;
+}
+
+int fm_batch_autotune(fm_batch* b, int niter_probe, double* best_fraction, double* best_ms) {
+    if (!b || niter_probe < 2) return FM_ERR_ARG;
+    for (fm_ctx* c : b->v)
+        if (!c->have_data) return FM_ERR_STATE;
+    DevGuard guard(b->device);
+    std::vector<void*> w(b->v.size(), nullptr);
+    bool ok = true;
+    for (size_t k = 0; k < b->v.size() && ok; ++k) ok = dalloc(&w[k], (size_t)b->v[k]->nv * b->v[k]->ts) == cudaSuccess;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ok = ok && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+    const double cand[4] = {1.0, 0.5, 0.25, 0.125};
+    double bestf = b->fraction, bestt = 1e300;
+    int rc = ok ? FM_OK : FM_ERR_OOM;
+    for (int q = 0; q < 4 && rc == FM_OK; ++q) {
+        b->fraction = cand[q];
+        batch_apply_fraction(b);
+        rc = batch_solve(b, w.data(), 1, niter_probe, nullptr);  // warm-up and capture
+        if (rc != FM_OK) break;
+        cudaEventRecord(e0, b->origin);
+        rc = batch_solve(b, w.data(), 1, niter_probe, nullptr);
+        cudaEventRecord(e1, b->origin);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rc == FM_OK && ms < bestt) {
+            bestt = ms;
+            bestf = cand[q];
+        }
+    }
+    for (void* p : w)
+        if (p) cudaFree(p);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    b->fraction = bestf;
+    batch_apply_fraction(b);
+    if (best_fraction) *best_fraction = bestf;
+    if (best_ms) *best_ms = bestt;
+    return rc;
+}
+
+fm_ctx* fm_batch_ctx(fm_batch* b, int k) {
+    if (!b || k < 0 || k >= (int)b->v.size()) return nullptr;
+    return b->v[k];
+}
+
+int fm_batch_destroy(fm_batch* b) {
+    if (!b) return FM_OK;
+    {
+        DevGuard guard(b->device);
+        if (b->origin) cudaStreamSynchronize(b->origin);
+        batch_free(b);
+    }
+    delete b;
     return FM_OK;
 }
 

@@ -28,11 +28,17 @@ enum Scal {
     S_ZZD,         // sum z^2 d
     S_COST,        // Psi(w)
     S_K,           // omega-independent part of Phi (Eq. 2 terms with m = n, and the coil-combination remainder)
+    S_CG_RZPREV,   // adjoint CG: r'z of the previous iteration
+    S_CG_PQ,       // adjoint CG: p' H p
+    S_CG_ALPHA,    // adjoint CG: step r'z / p'Hp
+    S_CG_RR,       // adjoint CG: ||r||^2 after the last update
+    S_CG_BB,       // adjoint CG: ||b||^2
+    S_ADJ_DOT,     // lambda' C'C w (implicit derivative with respect to beta)
     S_NSCAL
 };
 
 // Integer device state.
-enum IState { I_ERR = 0, I_ITER, I_DONE0, I_DONE1, I_BAR_COUNT, I_BAR_GEN, I_NMASK, I_NISTATE };
+enum IState { I_ERR = 0, I_ITER, I_DONE0, I_DONE1, I_BAR_COUNT, I_BAR_GEN, I_NMASK, I_CG_IT, I_CG_DONE, I_NISTATE };
 
 // Setup works on chunks of 1024 consecutive voxels (mask compaction keeps voxel order).
 constexpr int kChunk = 1024;
@@ -41,6 +47,8 @@ struct Pairs {
     int P;                  // number of echo pairs m < n
     int m[kMaxPairs], n[kMaxPairs];
     double dt[kMaxPairs];   // t_m - t_n
+    double gmag[kMaxPairs]; // L |Gamma_mn| (1 in the field-map case)
+    double gph[kMaxPairs];  // angle Gamma_mn (0 in the field-map case)
 };
 
 template <typename T> struct V2;
@@ -184,6 +192,9 @@ struct SetupArgs {
     const void* smap;   // complex [nc][nv] or null
     const uint8_t* mask;// [nv] or null
     double te0, te1;    // first two echo times (Eq. 6)
+    int wf;             // water-fat model: R_mn = L Gamma_mn conj(Z_m) Z_n with lgam below
+    double lgam[2 * FM_MAX_ECHO * FM_MAX_ECHO];  // L Gamma_mn, complex, row m, column n
+    void* rho;          // T [nv] compact order: sum |r_cdmn| (Eq. w0_wf weights), or null
     void* pairs;        // T2 [P][nv]: (|R_mn|, angle R_mn)
     void* coils;        // T2 [L][nc][nv]: (|W_cm|, angle W_cm), or null
     uint8_t* nb;        // [nv]
@@ -201,6 +212,7 @@ struct DataArgs {
     Pairs pr;
     double beta;
     int literal;           // literal curvature over coils (nc > 1 and FM_CURV_LITERAL)
+    int wf;                // water-fat Gamma: the literal curvature takes the runtime-coil path
     const void* pairs;     // compact order: [P][cap]
     const void* coils;     // compact order: [L][nc][cap]
     const uint8_t* nb;
@@ -255,6 +267,44 @@ struct IcArgs {
     long long spin_limit;
 };
 
+// Implicit differentiation of the converged field map: true curvature, the adjoint CG on
+// H_true = diag(h) + beta C'C, and the derivatives with respect to beta and the images.
+struct AdjArgs {
+    Geo geo;
+    int nc, L;
+    Pairs pr;
+    double beta;
+    double te[FM_MAX_ECHO];
+    const void* pairs;     // compact order: [P][nv] (|R_mn|, angle R_mn)
+    const uint8_t* nb;
+    const int* vlist;
+    const void* w;         // T [nv] field map at which everything is evaluated
+    const void* rhs;       // T [nv] right-hand side b
+    void* h;               // T [nv] true curvature
+    void* x;               // T [nv] CG iterate (lambda)
+    void* r;               // T [nv] residual
+    const void* z;         // T [nv] preconditioned residual
+    const void* p_old;     // T [nv]
+    void* p_new;           // T [nv]
+    void* q;               // T [nv] H_true p
+    double tol2;           // stop when ||r||^2 <= tol2 ||b||^2
+    int maxiter;
+    int identity_pc;       // 1: no preconditioner (z = r; the update pass supplies r'r as r'z)
+    const void* rho;       // T compact [nv]: PWLS weights (Eq. w0_wf)
+    const void* x0;        // T [nv]: PWLS start (the sweep's map)
+    double fat_re[FM_MAX_ECHO], fat_im[FM_MAX_ECHO];  // second basis column of Eq. gamma
+    double ginv[8];        // (gamma^H gamma)^{-1}, complex 2 x 2 row-major
+    void* water;           // complex [nv]
+    void* fat;             // complex [nv]
+    const void* y;         // complex [L][nc][nv] images
+    const void* smap;      // complex [nc][nv] or null
+    const void* lam;       // T [nv]
+    void* dldy;            // complex [L][nc][nv]
+    double* scal;
+    double* partials;
+    int* istate;
+};
+
 template <typename T> cudaError_t launch_setup(const SetupArgs& a, cudaStream_t s);
 template <typename T> cudaError_t launch_masked_copy(const void* in, void* out, const uint8_t* nb, long long nv,
                                                      int grid, cudaStream_t s);
@@ -265,6 +315,16 @@ template <typename T> cudaError_t launch_pdiag(const DataArgs& a, int mode, int 
 template <typename T> int ls_max_blocks_per_sm(const DataArgs& a);
 template <typename T> cudaError_t launch_ic_fwd(const IcArgs& a, int grid, cudaStream_t s);
 template <typename T> cudaError_t launch_ic_bwd(const IcArgs& a, int grid, cudaStream_t s);
+template <typename T> cudaError_t launch_true_curv(const AdjArgs& a, int grid, cudaStream_t s);
+template <typename T> cudaError_t launch_cg_init(const AdjArgs& a, int grid, cudaStream_t s);
+template <typename T> cudaError_t launch_cg_dir(const AdjArgs& a, int grid, cudaStream_t s);
+template <typename T> cudaError_t launch_cg_upd(const AdjArgs& a, int grid, cudaStream_t s);
+template <typename T> cudaError_t launch_lap_dot(const AdjArgs& a, int grid, cudaStream_t s);
+template <typename T> cudaError_t launch_dldy(const AdjArgs& a, int grid, cudaStream_t s);
+template <typename T> cudaError_t launch_pwls_init(const AdjArgs& a, int grid, cudaStream_t s);
+template <typename T> cudaError_t launch_wf_sweep(const AdjArgs& a, int nsweep, double wlo, double whi, int grid,
+                                                  cudaStream_t s);
+template <typename T> cudaError_t launch_wf_amp(const AdjArgs& a, int grid, cudaStream_t s);
 template <typename T> int ic_tz();
 template <typename T> size_t ic_face_bytes_per_tile();
 template <typename T> int ic_max_blocks_per_sm();

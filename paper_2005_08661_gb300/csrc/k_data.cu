@@ -94,18 +94,21 @@ __device__ __forceinline__ void eval_voxel(const DataArgs& a, long long j /* com
                 }
                 d_acc += dt * dt * inner;
             } else {
+                // runtime coil count; also the water-fat model, whose angle r_cdmn carries the
+                // phase of Gamma_mn and |r_cdmn| the factor L |Gamma_mn| (0 and 1 otherwise)
                 const int m = a.pr.m[p], n = a.pr.n[p], nc = a.nc;
+                const T gph = (T)a.pr.gph[p];
                 T inner = 0;
                 for (int cc = 0; cc < nc; ++cc) {
                     const T2 q = coils[((size_t)m * nc + cc) * nv + j];
                     T acc = 0;
                     for (int dd = 0; dd < nc; ++dd) {
                         const T2 r = coils[((size_t)n * nc + dd) * nv + j];
-                        acc += r.x * sinc_wrapped(wrap_angle(r.y + w * dt - q.y));
+                        acc += r.x * sinc_wrapped(wrap_angle(r.y + w * dt + gph - q.y));
                     }
                     inner += q.x * acc;
                 }
-                d_acc += dt * dt * inner;
+                d_acc += dt * dt * (T)a.pr.gmag[p] * inner;
             }
         }
     }
@@ -395,6 +398,7 @@ static cudaError_t grad_nc(const DataArgs& a, int grid, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_grad(const DataArgs& a, int grid, cudaStream_t s) {
     if (!a.literal) return grad_nc<T, 1>(a, grid, s);
+    if (a.wf) return grad_nc<T, 0>(a, grid, s);
     switch (a.nc) {
         case 2: return grad_nc<T, 2>(a, grid, s);
         case 4: return grad_nc<T, 4>(a, grid, s);
@@ -419,6 +423,7 @@ static cudaError_t ls_nc(const DataArgs& a, int grid, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_ls(const DataArgs& a, int grid, cudaStream_t s) {
     if (!a.literal) return ls_nc<T, 1>(a, grid, s);
+    if (a.wf) return ls_nc<T, 0>(a, grid, s);
     switch (a.nc) {
         case 2: return ls_nc<T, 2>(a, grid, s);
         case 4: return ls_nc<T, 4>(a, grid, s);
@@ -437,6 +442,7 @@ static int ls_occ() {
 template <typename T>
 int ls_max_blocks_per_sm(const DataArgs& a) {
     if (!a.literal) return ls_occ<T, 1>();
+    if (a.wf) return ls_occ<T, 0>();
     switch (a.nc) {
         case 2: return ls_occ<T, 2>();
         case 4: return ls_occ<T, 4>();

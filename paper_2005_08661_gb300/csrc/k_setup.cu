@@ -10,6 +10,11 @@
 //   Phi_j(w) = K_j + 4 sum_{m<n} |R_mn| sin^2((angle R_mn + w (t_m - t_n)) / 2),
 //   K_j = (sum_m A_m)^2 - (sum_m |Z_m|)^2  (the m = n terms plus, for each pair, the
 //   coil-combination remainder sum_cd |r| - |R|), which does not depend on w.
+// Water-fat model (Eq. gamma): r_cdmn = L Gamma_mn conj(W_cm) W_dn with the complex projector
+// Gamma, so R_mn = L Gamma_mn conj(Z_m) Z_n, sum_cd |r_cdmn| = L |Gamma_mn| A_m A_n and
+//   K_j = sum_{m,n} L |Gamma_mn| (A_m A_n - |Z_m| |Z_n|)
+// (the m = n terms of the varying part vanish: Gamma_mm is real and nonnegative).  The PWLS
+// weights of the water-fat initialisation are rho_j = sum_{m,n} L |Gamma_mn| A_m A_n.
 // Stored per mask voxel, in the compact (ascending voxel) order the data-term kernels
 // iterate: (|R_mn|, angle R_mn) for each pair m < n, and (|W_cm|, angle W_cm) for the
 // literal curvature sum of Eq. 10, which does not collapse over coils.
@@ -170,20 +175,41 @@ __global__ void __launch_bounds__(kSetupThreads) k_setup(SetupArgs a) {
         }
         for (int p = 0; p < a.pr.P; ++p) {
             const int mm = a.pr.m[p], n = a.pr.n[p];
-            // R = conj(Z_m) Z_n
-            const double rr = Zr[mm] * Zr[n] + Zi[mm] * Zi[n];
-            const double ri = Zr[mm] * Zi[n] - Zi[mm] * Zr[n];
+            // R = conj(Z_m) Z_n (times L Gamma_mn in the water-fat model)
+            double rr = Zr[mm] * Zr[n] + Zi[mm] * Zi[n];
+            double ri = Zr[mm] * Zi[n] - Zi[mm] * Zr[n];
+            if (a.wf) {
+                const double gr = a.lgam[2 * (mm * L + n)], gi = a.lgam[2 * (mm * L + n) + 1];
+                const double tr = gr * rr - gi * ri;
+                ri = gr * ri + gi * rr;
+                rr = tr;
+            }
             T2 o;
             o.x = (T)sqrt(rr * rr + ri * ri);
             o.y = (T)((rr == 0.0 && ri == 0.0) ? 0.0 : atan2(ri, rr));
             pairs[(size_t)p * nv + k] = o;
         }
-        double sa = 0.0, sz = 0.0;
-        for (int mm = 0; mm < L; ++mm) {
-            sa += Am[mm];
-            sz += sqrt(Zr[mm] * Zr[mm] + Zi[mm] * Zi[mm]);
+        if (a.wf) {
+            double kj = 0.0, rj = 0.0;
+            for (int mm = 0; mm < L; ++mm)
+                for (int n = 0; n < L; ++n) {
+                    const double gr = a.lgam[2 * (mm * L + n)], gi = a.lgam[2 * (mm * L + n) + 1];
+                    const double g = sqrt(gr * gr + gi * gi);
+                    const double zm = sqrt(Zr[mm] * Zr[mm] + Zi[mm] * Zi[mm]), zn = sqrt(Zr[n] * Zr[n] + Zi[n] * Zi[n]);
+                    kj += g * (Am[mm] * Am[n] - zm * zn);
+                    rj += g * Am[mm] * Am[n];
+                }
+            if (S > 0.0) kacc += kj;
+            if (a.rho) ((T*)a.rho)[k] = (T)rj;
+        } else {
+            double sa = 0.0, sz = 0.0;
+            for (int mm = 0; mm < L; ++mm) {
+                sa += Am[mm];
+                sz += sqrt(Zr[mm] * Zr[mm] + Zi[mm] * Zi[mm]);
+            }
+            if (S > 0.0) kacc += (sa - sz) * (sa + sz);
+            if (a.rho) ((T*)a.rho)[k] = (T)(sa * sa);
         }
-        if (S > 0.0) kacc += (sa - sz) * (sa + sz);
         // Eq. 6: angle(conj(z_1) z_2) / (t_2 - t_1); z_m and Z_m differ by a positive scale
         const double er = Zr[0] * Zr[1] + Zi[0] * Zi[1];
         const double ei = Zr[0] * Zi[1] - Zi[0] * Zr[1];

@@ -42,7 +42,10 @@ _LOCK = threading.Lock()
 
 EXPORTS = ["fm_default_opts", "fm_create", "fm_set_data", "fm_init_omega", "fm_cost_grad", "fm_ic_factor",
            "fm_ic_apply", "fm_solve", "fm_get_history", "fm_set_profiling", "fm_kernel_times", "fm_destroy",
-           "fm_strerror", "fm_last_error", "fm_cost_grad_noalloc"]
+           "fm_strerror", "fm_last_error", "fm_cost_grad_noalloc", "fm_batch_create", "fm_batch_set_data",
+           "fm_batch_solve", "fm_batch_autotune", "fm_batch_set_fraction", "fm_batch_ctx", "fm_batch_destroy",
+           "fm_true_curv", "fm_adjoint_solve", "fm_implicit_grad", "fm_set_fat_model", "fm_wf_sweep",
+           "fm_pwls_init", "fm_wf_amplitudes"]
 KERNELS = ["grad", "ic_fwd", "ic_bwd", "dir", "ls"]
 
 
@@ -81,6 +84,27 @@ def load_library(path=None):
         lib.fm_cost_grad_noalloc.argtypes = [i, i, i, i, i, C.POINTER(FmOpts), vp, vp, C.POINTER(d), vp, d, vp,
                                              C.POINTER(d), vp, vp, i, vp]
         lib.fm_cost_grad_noalloc.restype = C.c_int
+        lib.fm_true_curv.argtypes = [vp, vp, vp]
+        lib.fm_adjoint_solve.argtypes = [vp, vp, vp, vp, d, i, C.POINTER(i), C.POINTER(d)]
+        lib.fm_implicit_grad.argtypes = [vp, vp, vp, vp, vp, vp, C.POINTER(d)]
+        lib.fm_set_fat_model.argtypes = [vp, i, C.POINTER(d), C.POINTER(d)]
+        lib.fm_wf_sweep.argtypes = [vp, i, d, d, vp]
+        lib.fm_pwls_init.argtypes = [vp, vp, i, vp]
+        lib.fm_wf_amplitudes.argtypes = [vp, vp, vp, vp, vp, vp]
+        for fn in ("fm_true_curv", "fm_adjoint_solve", "fm_implicit_grad", "fm_set_fat_model", "fm_wf_sweep",
+                   "fm_pwls_init", "fm_wf_amplitudes"):
+            getattr(lib, fn).restype = C.c_int
+        lib.fm_batch_create.argtypes = [C.POINTER(vp), i, C.POINTER(i), C.POINTER(FmOpts), i, vp]
+        lib.fm_batch_set_data.argtypes = [vp, i, vp, vp, C.POINTER(d), vp, d]
+        lib.fm_batch_solve.argtypes = [vp, C.POINTER(vp), i, i, C.POINTER(C.POINTER(d))]
+        lib.fm_batch_autotune.argtypes = [vp, i, C.POINTER(d), C.POINTER(d)]
+        lib.fm_batch_set_fraction.argtypes = [vp, d]
+        lib.fm_batch_ctx.argtypes = [vp, i]
+        lib.fm_batch_ctx.restype = vp
+        lib.fm_batch_destroy.argtypes = [vp]
+        for fn in ("fm_batch_create", "fm_batch_set_data", "fm_batch_solve", "fm_batch_autotune",
+                   "fm_batch_set_fraction", "fm_batch_destroy"):
+            getattr(lib, fn).restype = C.c_int
         lib.fm_strerror.argtypes = [i]
         lib.fm_strerror.restype = C.c_char_p
         lib.fm_last_error.argtypes = [vp]
@@ -128,6 +152,8 @@ class FieldMap:
         if st != FM_OK:
             raise FmError(st, f"fm_create: {self.lib.fm_strerror(st).decode()}")
         self._h = h
+        self.fat_model = None
+        self.data = None
 
     # ---------------------------------------------------------------- helpers
     def _check(self, st, what):
@@ -163,6 +189,7 @@ class FieldMap:
         te_arr = (C.c_double * self.necho)(*[float(v) for v in te])
         self._check(self.lib.fm_set_data(self._h, _dptr(y), _dptr(smap), te_arr, _dptr(mask), float(beta)),
                     "fm_set_data")
+        self.data = (y, smap, tuple(float(v) for v in te), mask, float(beta))
 
     def init_omega(self):
         out = self.empty()
@@ -189,6 +216,86 @@ class FieldMap:
         p = self.empty() if out is None else self._vec(out, "out")
         self._check(self.lib.fm_ic_apply(self._h, _dptr(g), _dptr(p)), "fm_ic_apply")
         return p
+
+    # ---------------------------------------------------------------- water-fat model
+    def set_fat_model(self, amps, freqs):
+        """Water-fat model for the next set_data: relative peak amplitudes and frequency
+        offsets in cycles per unit of the echo times (kHz for ms).  Empty -> field map."""
+        amps = [float(v) for v in amps]
+        freqs = [float(v) for v in freqs]
+        if len(amps) != len(freqs):
+            raise ValueError("amps and freqs must have the same length")
+        n = len(amps)
+        a = (C.c_double * max(n, 1))(*amps)
+        f = (C.c_double * max(n, 1))(*freqs)
+        self._check(self.lib.fm_set_fat_model(self._h, n, a, f), "fm_set_fat_model")
+        self.fat_model = (tuple(amps), tuple(freqs)) if n else None
+
+    def wf_sweep(self, nsweep=100, w_lo=None, w_hi=None):
+        """Voxel-wise sweep initialisation; the default range is +-pi |f| of the largest fat peak
+        (+-|Delta_f / 2| in rad per unit of te)."""
+        if w_lo is None or w_hi is None:
+            amps, freqs = self.fat_model
+            half = float(np.pi * abs(freqs[int(np.argmax(amps))]))
+            w_lo, w_hi = -half, half
+        out = self.empty()
+        self._check(self.lib.fm_wf_sweep(self._h, int(nsweep), float(w_lo), float(w_hi), _dptr(out)), "fm_wf_sweep")
+        return out
+
+    def pwls_init(self, omega_tilde, niter=10):
+        """PWLS initialisation (niter CG iterations) from the sweep's map."""
+        self._vec(omega_tilde, "omega_tilde")
+        out = self.empty()
+        self._check(self.lib.fm_pwls_init(self._h, _dptr(omega_tilde), int(niter), _dptr(out)), "fm_pwls_init")
+        return out
+
+    def wf_init(self, nsweep=100, niter=10):
+        """Sweep then PWLS: the water-fat initial map."""
+        return self.pwls_init(self.wf_sweep(nsweep), niter)
+
+    def wf_amplitudes(self, omega, y=None, smap=None):
+        """(water, fat) complex maps at omega by the closed form of the water-fat model."""
+        self._vec(omega, "omega")
+        if y is None:
+            y, smap = self.data[0], self.data[1]
+        w = self._torch.empty(self.shape, dtype=self.cdtype, device=self.device)
+        f = self._torch.empty(self.shape, dtype=self.cdtype, device=self.device)
+        self._check(self.lib.fm_wf_amplitudes(self._h, _dptr(y), _dptr(smap), _dptr(omega), _dptr(w), _dptr(f)),
+                    "fm_wf_amplitudes")
+        return w, f
+
+    def true_curv(self, omega):
+        """Exact second derivative of the data term at omega (0 outside the mask)."""
+        self._vec(omega, "omega")
+        h = self.empty()
+        self._check(self.lib.fm_true_curv(self._h, _dptr(omega), _dptr(h)), "fm_true_curv")
+        return h
+
+    def adjoint_solve(self, omega_hat, rhs, tol=None, maxiter=1000):
+        """lambda = H_true^{-1} rhs by IC(0)-preconditioned CG.  Returns (lambda, iterations,
+        relative residual).  tol defaults to 1e-6 (fp32) or 1e-12 (fp64)."""
+        self._vec(omega_hat, "omega_hat")
+        self._vec(rhs, "rhs")
+        if tol is None:
+            tol = 1e-6 if self.precision == "fp32" else 1e-12
+        lam = self.empty()
+        it, rr = C.c_int(0), C.c_double(0.0)
+        self._check(self.lib.fm_adjoint_solve(self._h, _dptr(omega_hat), _dptr(rhs), _dptr(lam), float(tol),
+                                              int(maxiter), C.byref(it), C.byref(rr)), "fm_adjoint_solve")
+        return lam, it.value, rr.value
+
+    def implicit_grad(self, omega_hat, lam, y=None, smap=None, want_dy=True, want_dbeta=True):
+        """(dl/dy, dl/dbeta) of a loss whose adjoint is lam; y and smap default to the
+        arrays of the last set_data."""
+        self._vec(omega_hat, "omega_hat")
+        self._vec(lam, "lam")
+        if y is None:
+            y, smap = self.data[0], self.data[1]
+        dy = self._torch.empty(tuple(y.shape), dtype=self.cdtype, device=self.device) if want_dy else None
+        db = C.c_double(0.0)
+        self._check(self.lib.fm_implicit_grad(self._h, _dptr(y), _dptr(smap), _dptr(omega_hat), _dptr(lam),
+                                              _dptr(dy), C.byref(db) if want_dbeta else None), "fm_implicit_grad")
+        return dy, (db.value if want_dbeta else None)
 
     def solve(self, omega=None, niter=50, want_history=True):
         """Run niter NCG-MLS iterations; omega=None starts from Eq. 6.  Returns (omega, costs)."""
@@ -235,3 +342,89 @@ class FieldMap:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class FieldMapBatch:
+    """Many independent volumes solved together (fm_batch_*): one CUDA graph launch
+    advances every volume's outer iteration."""
+
+    def __init__(self, shapes, precision="fp32", nls=5, precond="ic0", curvature="literal", spin_limit=1 << 21,
+                 device=None, stream=None):
+        """shapes: list of (nx, ny, nz, ncoil, necho)."""
+        import torch
+        self._torch = torch
+        self.lib = load_library()
+        self.shapes = [tuple(int(v) for v in sh) for sh in shapes]
+        self.precision = precision
+        self.rdtype = torch.float32 if precision == "fp32" else torch.float64
+        self.cdtype = torch.complex64 if precision == "fp32" else torch.complex128
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.device = dev
+        if stream is None:
+            stream = torch.cuda.current_stream(dev)
+        self.stream = stream
+        o = FmOpts()
+        self.lib.fm_default_opts(C.byref(o))
+        o.precision = _PREC[precision]
+        o.nls = int(nls)
+        o.precond = _PC[precond]
+        o.curvature = _CURV[curvature]
+        o.spin_limit = int(spin_limit)
+        dims = (C.c_int * (5 * len(shapes)))(*[v for sh in self.shapes for v in sh])
+        h = C.c_void_p()
+        sp = stream.cuda_stream if stream is not None else 0
+        st = self.lib.fm_batch_create(C.byref(h), len(shapes), dims, C.byref(o), dev.index,
+                                      C.c_void_p(sp) if sp else None)
+        if st != FM_OK:
+            raise FmError(st, f"fm_batch_create: {self.lib.fm_strerror(st).decode()}")
+        self._h = h
+
+    def _check(self, st, what):
+        if st != FM_OK:
+            raise FmError(st, f"{what}: {self.lib.fm_strerror(st).decode()}")
+
+    def set_data(self, k, y, smap, te, mask=None, beta=2.0 ** -3):
+        nx, ny, nz, nc, L = self.shapes[k]
+        if not (y.is_cuda and y.dtype == self.cdtype and y.is_contiguous() and tuple(y.shape) == (L, nc, nz, ny, nx)):
+            raise TypeError(f"y[{k}] must be a contiguous {self.cdtype} CUDA tensor of shape {(L, nc, nz, ny, nx)}")
+        te_arr = (C.c_double * L)(*[float(v) for v in te])
+        self._check(self.lib.fm_batch_set_data(self._h, k, _dptr(y), _dptr(smap), te_arr, _dptr(mask), float(beta)),
+                    "fm_batch_set_data")
+
+    def empty(self, k):
+        nx, ny, nz, _, _ = self.shapes[k]
+        return self._torch.empty((nz, ny, nx), dtype=self.rdtype, device=self.device)
+
+    def solve(self, omegas=None, niter=50, want_history=True):
+        """Returns (list of field maps, list of cost histories or None)."""
+        n = len(self.shapes)
+        init = omegas is None
+        ws = [self.empty(k) for k in range(n)] if init else [w.clone() for w in omegas]
+        ptrs = (C.c_void_p * n)(*[w.data_ptr() for w in ws])
+        hists = [(C.c_double * (niter + 1))() for _ in range(n)] if want_history else None
+        hp = (C.POINTER(C.c_double) * n)(*[C.cast(hh, C.POINTER(C.c_double)) for hh in hists]) if hists else None
+        self._check(self.lib.fm_batch_solve(self._h, ptrs, 1 if init else 0, int(niter), hp), "fm_batch_solve")
+        return ws, ([np.array(hh[:]) for hh in hists] if hists else None)
+
+    def solve_into(self, ptrs, init, niter):
+        """Lowest-overhead form: ptrs is a ctypes array of device pointers updated in place."""
+        self._check(self.lib.fm_batch_solve(self._h, ptrs, 1 if init else 0, int(niter), None), "fm_batch_solve")
+
+    def autotune(self, niter_probe=4):
+        f, ms = C.c_double(), C.c_double()
+        self._check(self.lib.fm_batch_autotune(self._h, int(niter_probe), C.byref(f), C.byref(ms)), "fm_batch_autotune")
+        return f.value, ms.value
+
+    def set_fraction(self, f):
+        self._check(self.lib.fm_batch_set_fraction(self._h, float(f)), "fm_batch_set_fraction")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.fm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -7,7 +7,9 @@ none of the estimator's arithmetic (no cost, gradient, curvature, factor or
 solver), so both the FP64 oracle and the CUDA path may take their inputs from it.
 """
 from .volumes import (Volume, make_volume, ellipsoid_mask, small_config, full_config,
-                      diff_config, batch_configs, TE_MS)
+                      diff_config, batch_configs, TE_MS, make_wf_volume, wf_config, fat_spectrum,
+                      WF_TE_MS)
 
 __all__ = ["Volume", "make_volume", "ellipsoid_mask", "small_config", "full_config",
-           "diff_config", "batch_configs", "TE_MS"]
+           "diff_config", "batch_configs", "TE_MS", "make_wf_volume", "wf_config", "fat_spectrum",
+           "WF_TE_MS"]

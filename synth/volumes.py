@@ -17,6 +17,11 @@ Recipe (the paper's datasets are not available, so these stand in for them):
 * support mask (Sec. IV): voxel centres inside the ellipsoid (where the magnitude is
   at least 0.1 of its maximum) dilated by a Euclidean ball of radius 2 voxels.
 
+Water-fat volumes (make_wf_volume; Sec. II water-fat case, x_l = m_w + m_f sum_p a_p
+e^{i 2 pi f_p t_l}): water and fat amplitude maps are smooth nonnegative sums of Gaussians
+over the phantom (water 0.05 outside it, fat 0 outside), the fat spectrum is a seeded
+6-peak vector (fat_spectrum), echo times 1.2 + k ms, k = 0..5.
+
 Units: echo times in milliseconds, so the field map w is in rad/ms and
 f[Hz] = 1000 w / (2 pi).  Arrays are C-ordered [z][y][x] (x fastest); the echo
 images are [L][N_c][z][y][x].
@@ -190,6 +195,97 @@ def make_volume(nx, ny, nz, ncoil=1, te=TE_MS, snr_db=20.0, seed=0, fmax_hz=150.
                   name=name or f"{nx}x{ny}x{nz}_c{ncoil}",
                   meta=dict(seed=seed, snr_db=snr_db, fmax_hz=fmax_hz, step_hz=step_hz,
                             nblobs=nblobs, sigma_n=sigma_n))
+
+
+GYRO_MHZ_PER_T = 42.577478  # proton gyromagnetic ratio / (2 pi)
+
+
+def fat_spectrum(seed=3003, npeak=6, field_t=3.0):
+    """Seeded multipeak fat model for field strength field_t: peak offsets in ppm relative
+    to water spanning -3.8 .. +0.6 (both ends fixed, the others uniform in between) and
+    relative amplitudes drawn from a Dirichlet distribution whose largest weight sits on the
+    peak nearest -3.4 ppm, so they sum to 1.  Returns (amps, freqs) with freqs in cycles per
+    ms (kHz) and the ppm offsets for the record."""
+    rng = np.random.default_rng(seed)
+    inner = np.sort(rng.uniform(-3.8, 0.6, size=npeak - 2))
+    ppm = np.concatenate([[-3.8], inner, [0.6]])
+    conc = np.ones(npeak)
+    conc[int(np.argmin(np.abs(ppm + 3.4)))] = 8.0
+    amps = rng.dirichlet(conc)
+    freqs_khz = ppm * GYRO_MHZ_PER_T * field_t / 1000.0  # ppm x MHz = Hz
+    return amps, freqs_khz, ppm
+
+
+def _smooth_nonneg(rng, nx, ny, nz, nblobs):
+    """Sum of positive 3-D Gaussians centred in the ellipsoid, scaled to a maximum of 1."""
+    ax, ay, az = 0.4 * nx, 0.35 * ny, 0.4 * nz
+    xs, ys, zs = _axis(nx), _axis(ny), _axis(nz)
+    f = np.zeros((nz, ny, nx), dtype=np.float64)
+    for _ in range(nblobs):
+        while True:
+            u = rng.uniform(-1.0, 1.0, size=3)
+            if float(u @ u) <= 1.0:
+                break
+        c = (u[0] * ax, u[1] * ay, u[2] * az)
+        sig = rng.uniform(0.15, 0.4, size=3) * np.array([nx, ny, nz], dtype=np.float64)
+        amp = rng.uniform(0.3, 1.0)
+        gx = np.exp(-0.5 * ((xs - c[0]) / sig[0]) ** 2)
+        gy = np.exp(-0.5 * ((ys - c[1]) / sig[1]) ** 2)
+        gz = np.exp(-0.5 * ((zs - c[2]) / sig[2]) ** 2)
+        f += amp * gz[:, None, None] * gy[None, :, None] * gx[None, None, :]
+    return f / max(float(f.max()), 1e-30)
+
+
+WF_TE_MS = tuple(1.2 + k * 1.0 for k in range(6))
+
+
+def make_wf_volume(nx, ny, nz, ncoil=1, te=WF_TE_MS, snr_db=20.0, seed=0, fmax_hz=200.0, nblobs=4,
+                   beta=2.0 ** -7, fat=None, dtype=np.complex64, name=None, dilate=2, noise=True):
+    """Water-fat acquisition by Eq. 1 with x_l = m_w + m_f sum_p a_p e^{i 2 pi f_p t_l}.
+    meta holds the true water and fat maps and the fat model (amps, freqs in kHz, ppm)."""
+    rng = np.random.default_rng(seed)
+    te = np.asarray(te, dtype=np.float64)
+    L = te.size
+    inside = ellipsoid_inside(nx, ny, nz)
+    water = np.where(inside, 0.2 + 0.8 * _smooth_nonneg(rng, nx, ny, nz, nblobs), 0.05)
+    fatm = np.where(inside, _smooth_nonneg(rng, nx, ny, nz, nblobs), 0.0)
+    amps, freqs, ppm = fat if fat is not None else fat_spectrum()
+    f_hz = _field_map_hz(rng, nx, ny, nz, nblobs, fmax_hz, 0.0)
+    omega = hz_to_rad_per_ms(f_hz)
+    smap = _coil_maps(rng, nx, ny, nz, ncoil) if ncoil > 1 else None
+    y = np.empty((L, ncoil, nz, ny, nx), dtype=dtype)
+    sq = 0.0
+    cnt = 0
+    for l in range(L):
+        phi_l = complex(np.sum(amps * np.exp(2j * math.pi * freqs * te[l])))
+        x = water + fatm * phi_l
+        ph = np.exp(1j * omega * te[l]) * x
+        for c in range(ncoil):
+            yc = ph * smap[c] if smap is not None else ph
+            y[l, c] = yc
+            sq += float(np.sum(np.abs(yc[inside]) ** 2))
+            cnt += int(inside.sum())
+    rms = math.sqrt(sq / max(cnt, 1))
+    sigma_n = rms / (math.sqrt(2.0) * 10.0 ** (snr_db / 20.0)) if noise else 0.0
+    rdt = np.float32 if dtype == np.complex64 else np.float64
+    if noise:
+        for l in range(L):
+            for c in range(ncoil):
+                nz_ = rng.standard_normal((2, nz, ny, nx), dtype=rdt)
+                y[l, c] += (sigma_n * nz_[0] + 1j * sigma_n * nz_[1]).astype(dtype)
+    mask = ellipsoid_mask(nx, ny, nz, dilate=dilate)
+    smap_out = smap.astype(dtype) if smap is not None else None
+    return Volume(y=y, smap=smap_out, mask=mask, te=te, omega_true=omega, beta=float(beta),
+                  name=name or f"wf_{nx}x{ny}x{nz}_c{ncoil}",
+                  meta=dict(seed=seed, snr_db=snr_db, fmax_hz=fmax_hz, nblobs=nblobs, sigma_n=sigma_n,
+                            water=water, fat=fatm, fat_amps=np.asarray(amps), fat_freqs_khz=np.asarray(freqs),
+                            fat_ppm=np.asarray(ppm)))
+
+
+def wf_config(seed=1003, **kw):
+    """192x192x64, 1 coil, 6 echoes 1.2..6.2 ms, +-200 Hz smooth field, SNR 20 dB, water-fat."""
+    return make_wf_volume(192, 192, 64, ncoil=1, snr_db=20.0, seed=seed, fmax_hz=200.0, nblobs=4,
+                          name="wf_192x192x64_c1", **kw)
 
 
 def small_config(seed=1001, **kw):
