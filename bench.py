@@ -56,6 +56,14 @@ WORKLOADS = {
     "batch": dict(desc="32 independent volumes from 64x64x16 to 192x192x96, 1 or 8 coils, 3 echoes "
                        "(0/2/10 ms), SNR 10-25 dB, beta=2^-3, 50 NCG iterations each, N_ls=5, IC(0), one "
                        "CUDA graph launch per two iterations of all volumes", niter=50),
+    "wf": dict(desc="water-fat: 192x192x64 voxels, 1 coil, 6 echoes (1.2..6.2 ms), seeded 6-peak fat spectrum "
+                    "(-3.8..+0.6 ppm at 3 T), +-200 Hz smooth field, SNR 20 dB, beta=2^-7; per step: setup, "
+                    "100-value voxel-wise sweep, 10 PWLS CG iterations, 100 NCG iterations (N_ls=5, IC(0)), "
+                    "water/fat amplitudes", niter=100),
+    "precond": dict(desc="preconditioner comparison: 74x74x10 voxels, 32 coils, 3 echoes (0/1/2.3 ms), SNR 20 dB, "
+                         "beta=2^-3, FP32 NCG-MLS (N_ls=5) with IC(0) natural order, IC(0) red-black, diagonal, "
+                         "none: iterations and time until the RMSD to the converged map falls below 0.5 Hz",
+                    niter=0),
     "diff": dict(desc="128x128x64 voxels, 8 coils, 3 echoes (0/2/10 ms), SNR 20 dB, beta=2^-3: "
                       "torch.autograd forward (100 NCG iterations) + backward (IC(0)-preconditioned adjoint "
                       "CG to 1e-6, dl/dbeta and dl/dy) of l = ||w^ - w_true||^2", niter=100),
@@ -64,7 +72,9 @@ CPU_SAMPLE = (32, 32, 16)  # oracle sample: centred sub-volume of the same acqui
 
 
 def make_workload(name, seed_offset=0):
-    from synth import diff_config, full_config, small_config
+    from synth import diff_config, full_config, small_config, wf_config
+    if name == "wf":
+        return wf_config(seed=1003 + seed_offset)
     if name == "full":
         return full_config(seed=1002 + seed_offset)
     if name == "medium":
@@ -81,7 +91,8 @@ def sub_volume(vol, size):
     return Volume(y=np.ascontiguousarray(vol.y[(slice(None), slice(None)) + sl]),
                   smap=None if vol.smap is None else np.ascontiguousarray(vol.smap[(slice(None),) + sl]),
                   mask=np.ascontiguousarray(vol.mask[sl]), te=vol.te, omega_true=vol.omega_true[sl],
-                  beta=vol.beta, name=f"{vol.name}_sub{sx}x{sy}x{sz}")
+                  beta=vol.beta, name=f"{vol.name}_sub{sx}x{sy}x{sz}",
+                  meta={k: v for k, v in vol.meta.items() if k.startswith("fat_")})
 
 
 # ------------------------------------------------------------------ flop / byte model
@@ -199,8 +210,19 @@ def barrier(world):
 
 def oracle_sample(vol, iters):
     """Time the FP64 oracle, single-threaded, on a centred sub-volume; returns (seconds, units)."""
-    from oracle import Oracle
+    from oracle import Oracle, wf_gamma
     sub = sub_volume(vol, CPU_SAMPLE)
+    if "fat_amps" in sub.meta:  # water-fat: the sweep + PWLS start, then the timed NCG iterations
+        amps, freqs = sub.meta["fat_amps"], sub.meta["fat_freqs_khz"]
+        o = Oracle.from_volume(sub)
+        o.set_gamma(wf_gamma(sub.te, amps, freqs)[1])
+        half = float(np.pi * abs(freqs[int(np.argmax(amps))]))
+        w0 = o.pwls(o.wf_sweep(100, -half, half), 10)
+        t0 = time.perf_counter()
+        o.solve(w0=w0, niter=iters, nls=5)
+        dt = time.perf_counter() - t0
+        o.close()
+        return dt, sub.nvox * iters
     t0 = time.perf_counter()
     o = Oracle.from_volume(sub)
     o.solve(niter=iters, nls=5)
@@ -281,10 +303,25 @@ def run_ours(args, world, rank, local):
     fm.set_profiling(True)
     w = torch.empty(vol.mask.shape, dtype=rd, device=dev)
     w_h = torch.empty(vol.mask.shape, dtype=rd).pin_memory()
+    wf = "fat_amps" in vol.meta
+    if wf:  # water-fat: sweep + PWLS start, NCG from there, then the water and fat maps
+        fm.set_fat_model(vol.meta["fat_amps"], vol.meta["fat_freqs_khz"])
+        w_t = torch.empty_like(w)
+        amp_w = torch.empty(vol.mask.shape, dtype=cd, device=dev)
+        amp_f = torch.empty_like(amp_w)
+
+    def solve_path():
+        fm.set_data(y_d, s_d, vol.te, m_d, vol.beta)
+        if wf:
+            fm.wf_sweep(100, out=w_t)
+            fm.pwls_init(w_t, 10, out=w)
+            fm.solve_into(w, False, niter)
+            fm.wf_amplitudes(w, out=(amp_w, amp_f))
+        else:
+            fm.solve_into(w, True, niter)
 
     def step():
-        fm.set_data(y_d, s_d, vol.te, m_d, vol.beta)
-        fm.solve_into(w, True, niter)
+        solve_path()
 
     for _ in range(args.warmup):
         step()
@@ -317,8 +354,7 @@ def run_ours(args, world, rank, local):
                 if s_d is not None:
                     s_d.copy_(s_h, non_blocking=True)
                 m_d.copy_(m_h, non_blocking=True)
-            fm.set_data(y_d, s_d, vol.te, m_d, vol.beta)
-            fm.solve_into(w, True, niter)
+            solve_path()
             with torch.cuda.stream(stream):
                 w_h.copy_(w, non_blocking=True)
         step_e2e()
@@ -383,7 +419,9 @@ def run_ours(args, world, rank, local):
                          f"{CPU_SAMPLE[0]}x{CPU_SAMPLE[1]}x{CPU_SAMPLE[2]} sub-volume of the workload "
                          f"({vol.ncoil} coils), {dt:.1f} s, host {cpu_desc()}, nproc {os.cpu_count()}"}
 
-    launches = args.steps * (1 + (5 if vol.ncoil >= 1 else 0) * niter + 1)
+    # per step: mask count, chunk scan, setup; 5 kernels per outer iteration; the final update
+    # (water-fat adds the sweep, the PWLS start and 2 kernels per PWLS iteration, the amplitudes)
+    launches = args.steps * (3 + 5 * niter + 1 + ((1 + 1 + 2 * 10 + 1) if wf else 0))
     line = {"metric": "voxel-NCG-iters/s", "value": value, "unit": "voxel-iter/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
@@ -562,6 +600,90 @@ def run_diff(args, world, rank, local):
     return 0
 
 
+def run_precond(args, world, rank, local):
+    """Time for each preconditioner to bring the RMSD to the converged map below 0.5 Hz
+    (the paper's phantom comparison), with the converged map from a long FP64 IC(0) solve."""
+    import torch
+    from paper_2005_08661_gb300 import FieldMap, build as fm_build
+    from synth import phantom_config
+    fm_build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    vol = phantom_config(seed=1006 + rank)
+    stream = torch.cuda.Stream(dev)
+    m = torch.from_numpy(vol.mask).to(dev)
+    nmask = int(vol.mask.sum())
+
+    def open_fm(prec, pc):
+        cd = torch.complex64 if prec == "fp32" else torch.complex128
+        fm = FieldMap(vol.nx, vol.ny, vol.nz, ncoil=vol.ncoil, necho=vol.necho, precision=prec, precond=pc,
+                      device=local, stream=stream)
+        fm.set_data(torch.from_numpy(vol.y).to(dev).to(cd), torch.from_numpy(vol.smap).to(dev).to(cd), vol.te, m,
+                    vol.beta)
+        return fm
+
+    ref = open_fm("fp64", "ic0")
+    w_inf, _ = ref.solve(niter=400, want_history=False)
+    ref.close()
+    w_inf = w_inf.double()
+    hz = 1000.0 / (2 * math.pi)
+
+    def rmsd_hz(w):
+        return float(((w.double() - w_inf) ** 2 * m).sum().div(nmask).sqrt()) * hz
+
+    rows = {}
+    for pc in ("ic0", "rb", "diag", "none"):
+        fm = open_fm("fp32", pc)
+        cache = {}
+
+        def rmsd_at(k):
+            if k not in cache:
+                w, _ = fm.solve(niter=k, want_history=False)
+                cache[k] = rmsd_hz(w)
+            return cache[k]
+        kmax = 4096
+        hi = 1
+        while hi < kmax and rmsd_at(hi) >= 0.5:
+            hi *= 2
+        if rmsd_at(hi) >= 0.5:
+            rows[pc] = {"iterations": None, "ms": None, "rmsd_hz_at_limit": rmsd_at(hi)}
+            fm.close()
+            continue
+        lo = hi // 2
+        while hi - lo > 1:  # first k with RMSD < 0.5 Hz (RMSD falls monotonically here)
+            mid = (lo + hi) // 2
+            if rmsd_at(mid) < 0.5:
+                hi = mid
+            else:
+                lo = mid
+        k = hi
+        w = torch.empty(vol.mask.shape, dtype=torch.float32, device=dev)
+        for _ in range(max(3, args.warmup)):
+            fm.solve_into(w, True, k)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = max(1, args.steps)
+        e0.record(stream)
+        for _ in range(reps):
+            fm.solve_into(w, True, k)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        rows[pc] = {"iterations": k, "ms": e0.elapsed_time(e1) / reps, "rmsd_hz": rmsd_at(k)}
+        fm.close()
+    base = rows["ic0"]["ms"]
+    for r in rows.values():
+        r["vs_ic0"] = (r["ms"] / base) if (r.get("ms") and base) else None
+    line = {"metric": "time to RMSD < 0.5 Hz", "value": base, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS["precond"]["desc"], "voxels": vol.nvox, "mask_voxels": nmask,
+                       "reference": "converged map: 400 FP64 IC(0) iterations", "parallelism": f"replicas{world}"},
+            "preconditioners": rows}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def time_to_oracle_cost(prec, stream):
     """FP32/FP64 solve of the 64x64x16 workload: seconds until the cost first falls to the
     FP64 oracle's 50-iteration cost x (1 + 1e-6)."""
@@ -632,6 +754,8 @@ def main():
             return run_batch(args, world, rank, local)
         if args.workload == "diff":
             return run_diff(args, world, rank, local)
+        if args.workload == "precond":
+            return run_precond(args, world, rank, local)
         return run_ours(args, world, rank, local)
     finally:
         if world > 1:

@@ -65,6 +65,8 @@ extern "C" {
 #define FM_PC_IC0 0  /* IC(0) of H in natural order (Sec. III-B, Eq. 12): the paper's L_0 */
 #define FM_PC_DIAG 1 /* diag(H): the paper's NCG-MLS-D comparison (Sec. IV) */
 #define FM_PC_NONE 2 /* identity: the paper's NCG-MLS comparison (Sec. IV) */
+#define FM_PC_RB 3   /* IC(0) in red-black order (x + y + z even first): a labelled multicolour
+                        variant, two parallel stencil passes instead of the wavefronts */
 
 #define FM_CURV_LITERAL 0  /* d_j summed over every (c, d, m, n) term (Eq. 10) */
 #define FM_CURV_COMBINED 1 /* d_j from the coil-combined pair weights (labelled variant) */
@@ -138,8 +140,9 @@ FM_API int fm_cost_grad(fm_ctx *ctx, const void *omega, double *cost, void *grad
 
 /*
  * Form H = diag(d(omega)) + beta C'C (Eq. 9) and its IC(0) factor (Eq. 12), natural
- * x-fastest order, zero fill-in: L = (Pi + E) Pi^{-1/2} with E the strict lower
- * triangle of H and pivots pi_j = H_jj - sum_k E_jk^2 / pi_k.  The factor is kept
+ * x-fastest order (red-black order when fm_opts.precond is FM_PC_RB), zero fill-in:
+ * L = (Pi + E) Pi^{-1/2} with E the strict lower triangle of H in that order and pivots
+ * pi_j = H_jj - sum_k E_jk^2 / pi_k.  The factor is kept
  * in the context for fm_ic_apply.  inv_pivot (device [nz][ny][nx] of the voxel type,
  * nullable) receives 1/pi_j (0 outside the mask).  Pivots are computed in double.
  * Errors: FM_ERR_STATE, FM_ERR_NOT_PD (some pivot <= 0; reported at the next

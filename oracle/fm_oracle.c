@@ -416,6 +416,16 @@ int orc_set_gamma(orc_t *h, const double *gam) {
     return ORC_OK;
 }
 
+/* Phi_j(w_j) (Eq. 2) of every voxel (0 outside the mask). */
+void orc_phi_vox(const orc_t *h, const double *w, double *out) {
+    for (long j = 0; j < h->nv; ++j) {
+        long k = h->slot[j];
+        double phi = 0.0;
+        if (k >= 0) voxel_terms(h->T, h->rabs + k * h->T, h->rang + k * h->T, h->dt, w[j], &phi, NULL, NULL);
+        out[j] = phi;
+    }
+}
+
 /* Spatial weights of the PWLS initialisation (Eq. w0_wf): rho_j = sum_{c,d,m,n} |r_cdmnj|. */
 void orc_rho(const orc_t *h, double *out) {
     for (long j = 0; j < h->nv; ++j) {
@@ -518,20 +528,29 @@ void orc_init(const orc_t *h, double *w) {
  * IC(0) of H = diag(d) + beta C'C (Eq. 9, Eq. 12) on the mask voxels, generic sparse
  * code: H's lower triangle in compressed-column form (diagonal first in each column,
  * rows ascending), factorised in place by the textbook right-looking loop that only
- * updates entries inside the pattern.  Unknowns are numbered in natural voxel order.
+ * updates entries inside the pattern.  order 0: unknowns in natural voxel order (the
+ * paper's); order 1: red-black, every voxel with x + y + z even (natural order among
+ * them) before every voxel with x + y + z odd (the labelled multicolour variant, an
+ * IC(0) of P H P' for that permutation P).
  * colptr: [n+1], rowidx/val: capacity 4 nv, umap: [nv] voxel of each unknown.
  * ------------------------------------------------------------------------------- */
-int orc_ic0(int nx, int ny, int nz, const unsigned char *mask, const double *d, double beta,
-            long *colptr, long *rowidx, double *val, long *umap, long *n_out, long *nnz_out) {
+int orc_ic0_ordered(int nx, int ny, int nz, const unsigned char *mask, const double *d, double beta, int order,
+                    long *colptr, long *rowidx, double *val, long *umap, long *n_out, long *nnz_out) {
     long nv = (long)nx * ny * nz, nxy = (long)nx * ny;
     long *uidx = (long *)malloc(sizeof(long) * nv);
     if (!uidx) return ORC_ERR_OOM;
     long n = 0;
-    for (long j = 0; j < nv; ++j) {
-        uidx[j] = (mask == NULL || mask[j]) ? n : -1;
-        if (uidx[j] >= 0) umap[n++] = j;
-    }
-    /* assemble lower(H) column by column */
+    for (int pass = 0; pass < (order == 1 ? 2 : 1); ++pass)
+        for (long j = 0; j < nv; ++j) {
+            if (order == 1 && (int)((j % nx + (j / nx) % ny + j / nxy) % 2) != pass) continue;
+            if (mask == NULL || mask[j]) {
+                uidx[j] = n;
+                umap[n++] = j;
+            } else {
+                uidx[j] = -1;
+            }
+        }
+    /* assemble lower(H) column by column: the diagonal, then every neighbour numbered later */
     long nnz = 0;
     for (long u = 0; u < n; ++u) {
         long j = umap[u];
@@ -542,9 +561,15 @@ int orc_ic0(int nx, int ny, int nz, const unsigned char *mask, const double *d, 
         for (int q = 0; q < 6; ++q) if (nb[q] >= 0 && uidx[nb[q]] >= 0) ++cnt;
         colptr[u] = nnz;
         rowidx[nnz] = u; val[nnz] = d[j] + beta * cnt; ++nnz;
-        long up[3] = {nb[1], nb[3], nb[5]}; /* ascending voxel (and unknown) index */
-        for (int q = 0; q < 3; ++q)
-            if (up[q] >= 0 && uidx[up[q]] >= 0) { rowidx[nnz] = uidx[up[q]]; val[nnz] = -beta; ++nnz; }
+        long later[6];
+        int nl = 0;
+        for (int q = 0; q < 6; ++q)
+            if (nb[q] >= 0 && uidx[nb[q]] > u) later[nl++] = uidx[nb[q]];
+        for (int a = 1; a < nl; ++a) /* ascending row order */
+            for (int b = a; b > 0 && later[b - 1] > later[b]; --b) {
+                long t = later[b]; later[b] = later[b - 1]; later[b - 1] = t;
+            }
+        for (int q = 0; q < nl; ++q) { rowidx[nnz] = later[q]; val[nnz] = -beta; ++nnz; }
     }
     colptr[n] = nnz;
     free(uidx);
@@ -569,6 +594,11 @@ int orc_ic0(int nx, int ny, int nz, const unsigned char *mask, const double *d, 
     return ORC_OK;
 }
 
+int orc_ic0(int nx, int ny, int nz, const unsigned char *mask, const double *d, double beta,
+            long *colptr, long *rowidx, double *val, long *umap, long *n_out, long *nnz_out) {
+    return orc_ic0_ordered(nx, ny, nz, mask, d, beta, 0, colptr, rowidx, val, umap, n_out, nnz_out);
+}
+
 /* x = (L L')^{-1} b with the compressed-column factor of orc_ic0 */
 void orc_ic0_solve(long n, const long *colptr, const long *rowidx, const double *val, const double *b,
                    double *x) {
@@ -586,8 +616,9 @@ void orc_ic0_solve(long n, const long *colptr, const long *rowidx, const double 
     free(v);
 }
 
-/* p = (L L')^{-1} g for the factor of H(w) = diag(d(w)) + beta C'C; voxel-indexed arrays */
-int orc_precondition(const orc_t *h, const double *d, const double *g, double *p) {
+/* p = (L L')^{-1} g for the IC(0) factor of H(w) = diag(d(w)) + beta C'C in the given
+ * unknown order (0 natural, 1 red-black); voxel-indexed arrays */
+int orc_precondition_ordered(const orc_t *h, const double *d, const double *g, double *p, int order) {
     long nv = h->nv;
     long *colptr = (long *)malloc(sizeof(long) * (nv + 1));
     long *rowidx = (long *)malloc(sizeof(long) * 4 * nv);
@@ -597,7 +628,7 @@ int orc_precondition(const orc_t *h, const double *d, const double *g, double *p
     int st = ORC_ERR_OOM;
     if (colptr && rowidx && val && umap && gb && pb) {
         long n, nnz;
-        st = orc_ic0(h->nx, h->ny, h->nz, h->mask, d, h->beta, colptr, rowidx, val, umap, &n, &nnz);
+        st = orc_ic0_ordered(h->nx, h->ny, h->nz, h->mask, d, h->beta, order, colptr, rowidx, val, umap, &n, &nnz);
         if (st == ORC_OK) {
             for (long u = 0; u < n; ++u) gb[u] = g[umap[u]];
             orc_ic0_solve(n, colptr, rowidx, val, gb, pb);
@@ -609,12 +640,16 @@ int orc_precondition(const orc_t *h, const double *d, const double *g, double *p
     return st;
 }
 
+int orc_precondition(const orc_t *h, const double *d, const double *g, double *p) {
+    return orc_precondition_ordered(h, d, g, p, 0);
+}
+
 /* ---------------------------------------------------------------------------------
  * Preconditioned NCG with the monotonic line search (Algorithm box, Eq. 13-16).
  * w: [nv] in/out (read as the start point unless init != 0, which applies Eq. 6).
  * cost_hist [niter+1], alpha_hist [niter], mu_hist [niter], inner_cost [niter*nls]
  * (Psi after each inner step) may be NULL.  precond: 0 = IC(0), 1 = diagonal of H,
- * 2 = none.
+ * 2 = none, 3 = red-black IC(0).
  * ------------------------------------------------------------------------------- */
 int orc_solve(const orc_t *h, double *w, int init, int niter, int nls, int precond, double *cost_hist,
               double *alpha_hist, double *mu_hist, double *inner_cost) {
@@ -632,8 +667,8 @@ int orc_solve(const orc_t *h, double *w, int init, int niter, int nls, int preco
     for (int i = 0; i < niter; ++i) {
         orc_grad(h, w, g);
         orc_curv(h, w, d);
-        if (precond == 0) {
-            st = orc_precondition(h, d, g, p);
+        if (precond == 0 || precond == 3) {
+            st = orc_precondition_ordered(h, d, g, p, precond == 3 ? 1 : 0);
             if (st != ORC_OK) goto done;
         } else {
             for (long j = 0; j < nv; ++j) {

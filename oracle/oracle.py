@@ -64,6 +64,8 @@ def _lib():
         lib.orc_dgrad_dy_adj.restype = None
         lib.orc_set_gamma.argtypes = [vp, _dp]
         lib.orc_set_gamma.restype = C.c_int
+        lib.orc_phi_vox.argtypes = [vp, _dp, _dp]
+        lib.orc_phi_vox.restype = None
         lib.orc_rho.argtypes = [vp, _dp]
         lib.orc_rho.restype = None
         lib.orc_wf_sweep.argtypes = [vp, C.c_int, C.c_double, C.c_double, _dp]
@@ -82,6 +84,11 @@ def _lib():
                                 _lp, C.POINTER(C.c_long), C.POINTER(C.c_long)]
         lib.orc_ic0.restype = C.c_int
         lib.orc_ic0_solve.argtypes = [C.c_long, _lp, _lp, _dp, _dp, _dp]
+        lib.orc_ic0_ordered.argtypes = [C.c_int, C.c_int, C.c_int, vp, _dp, C.c_double, C.c_int, _lp, _lp, _dp,
+                                        _lp, C.POINTER(C.c_long), C.POINTER(C.c_long)]
+        lib.orc_ic0_ordered.restype = C.c_int
+        lib.orc_precondition_ordered.argtypes = [vp, _dp, _dp, _dp, C.c_int]
+        lib.orc_precondition_ordered.restype = C.c_int
         lib.orc_voxel.argtypes = [C.c_int, C.c_int, _dp, _dp, vp, C.c_double, _dp]
         lib.orc_voxel.restype = C.c_int
         lib.orc_voxel_r.argtypes = [C.c_int, C.c_int, _dp, vp, _dp, _dp]
@@ -140,6 +147,10 @@ class Oracle:
         if st != ORC_OK:
             raise RuntimeError(f"orc_set_gamma failed: {st}")
         self.gamma = G
+
+    def phi_vox(self, w):
+        """Phi_j(w_j) of Eq. 2 per voxel."""
+        return self._vec("orc_phi_vox", w)
 
     def rho(self):
         """PWLS weights rho_j = sum |r_cdmnj| (Eq. w0_wf)."""
@@ -288,9 +299,10 @@ class Oracle:
         self._lib.orc_init(self._h, out)
         return out.reshape(self.shape)
 
-    def precondition(self, d, g):
+    def precondition(self, d, g, order=0):
+        """(L L')^{-1} g with the IC(0) factor of diag(d) + beta C'C; order 0 natural, 1 red-black."""
         p = np.zeros(int(np.prod(self.shape)), np.float64)
-        st = self._lib.orc_precondition(self._h, self._w(d), self._w(g), p)
+        st = self._lib.orc_precondition_ordered(self._h, self._w(d), self._w(g), p, int(order))
         if st != ORC_OK:
             raise RuntimeError(f"orc_precondition failed: {st}")
         return p.reshape(self.shape)
@@ -323,8 +335,9 @@ def wf_gamma(te, amps, freqs):
     return g, G
 
 
-def ic0_factor(shape, mask, d, beta):
-    """Generic IC(0) of H = diag(d) + beta C'C on the mask voxels (natural order).
+def ic0_factor(shape, mask, d, beta, order=0):
+    """Generic IC(0) of H = diag(d) + beta C'C on the mask voxels (order 0: natural; 1:
+    red-black, even x + y + z first).
 
     Returns (colptr, rowidx, val, umap): the factor L in compressed-column form over the
     n unknowns (diagonal first in each column) and the voxel index of each unknown.
@@ -339,8 +352,8 @@ def ic0_factor(shape, mask, d, beta):
     val = np.zeros(4 * nv, np.float64)
     umap = np.zeros(nv, np.int64)
     n, nnz = C.c_long(), C.c_long()
-    st = lib.orc_ic0(nx, ny, nz, _ptr(m), d, float(beta), colptr, rowidx, val, umap, C.byref(n),
-                     C.byref(nnz))
+    st = lib.orc_ic0_ordered(nx, ny, nz, _ptr(m), d, float(beta), int(order), colptr, rowidx, val, umap,
+                             C.byref(n), C.byref(nnz))
     if st != ORC_OK:
         raise RuntimeError(f"orc_ic0 failed: {st}")
     n, nnz = n.value, nnz.value

@@ -251,6 +251,20 @@ cudaError_t iteration(fm_ctx* c, int cur) {
     if (e != cudaSuccess) return e;
     if (c->o.precond == FM_PC_IC0) {
         e = run_ic<T>(c, c->d, c->g[cur], c->p, c->g[cur], c->g[nxt], cur);
+    } else if (c->o.precond == FM_PC_RB) {
+        DataArgs a = base_args(c);
+        a.g = c->g[cur];
+        a.g_prev = c->g[nxt];
+        a.d = c->d;
+        a.z_new = c->p;
+        {
+            Mark m(c, cur, FM_K_IC_FWD);
+            e = launch_rb_black<T>(a, c->grid_data, c->stream);
+        }
+        if (e == cudaSuccess) {
+            Mark m(c, cur, FM_K_IC_BWD);
+            e = launch_rb_red<T>(a, c->grid_data, c->stream);
+        }
     } else {
         Mark m(c, cur, FM_K_IC_BWD);
         DataArgs a = base_args(c);
@@ -536,7 +550,7 @@ bool set_ls_grid(fm_ctx* c) {
 
 bool valid_opts(const fm_opts& o) {
     return (o.precision == FM_FP32 || o.precision == FM_FP64) && o.nls >= 1 && o.nls <= 1000 &&
-           (o.precond == FM_PC_IC0 || o.precond == FM_PC_DIAG || o.precond == FM_PC_NONE) &&
+           (o.precond == FM_PC_IC0 || o.precond == FM_PC_DIAG || o.precond == FM_PC_NONE || o.precond == FM_PC_RB) &&
            (o.curvature == FM_CURV_LITERAL || o.curvature == FM_CURV_COMBINED) && o.spin_limit >= 1;
 }
 
@@ -639,13 +653,20 @@ int fm_create(fm_ctx** out, int nx, int ny, int nz, int ncoil, int necho, const 
     A(&c->icint, (4 + 2 * (size_t)c->ntiles) * sizeof(int));
     A(&c->order, (size_t)c->ntiles * sizeof(int));
     if (!ok) { cudaGetLastError(); return bail(FM_ERR_OOM); }
-    // tiles in order of their tile hyperplane X + Y + Z (ties: z, y, x), a topological order
+    // tiles in order of a weighted tile hyperplane wxy (X + Y) + wz Z (ties: z, y, x): every
+    // weight is positive, so a tile's -x, -y, -z neighbours always come first
+#ifndef FM_IC_WXY
+#define FM_IC_WXY 1
+#endif
+#ifndef FM_IC_WZ
+#define FM_IC_WZ 1
+#endif
     std::vector<int> ord(c->ntiles);
     for (int t = 0; t < c->ntiles; ++t) ord[t] = t;
     const int ntx = c->ntx, nty = c->nty;
     std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
-        const int ha = a % ntx + (a / ntx) % nty + a / (ntx * nty);
-        const int hb = b % ntx + (b / ntx) % nty + b / (ntx * nty);
+        const int ha = FM_IC_WXY * (a % ntx + (a / ntx) % nty) + FM_IC_WZ * (a / (ntx * nty));
+        const int hb = FM_IC_WXY * (b % ntx + (b / ntx) % nty) + FM_IC_WZ * (b / (ntx * nty));
         return ha != hb ? ha < hb : a < b;
     });
     if (cudaMemcpy(c->order, ord.data(), ord.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -799,8 +820,18 @@ int fm_ic_factor(fm_ctx* c, const void* omega, void* inv_pivot) {
     cudaError_t e = f64 ? run_grad<double>(c, omega, nullptr, c->w[0], c->g[0], c->d, nullptr)
                         : run_grad<float>(c, omega, nullptr, c->w[0], c->g[0], c->d, nullptr);
     if (e != cudaSuccess) return cuda_fail(c, e, "gradient kernel");
-    e = f64 ? run_ic<double>(c, c->d, c->g[0], c->p, nullptr, nullptr)
-            : run_ic<float>(c, c->d, c->g[0], c->p, nullptr, nullptr);
+    if (c->o.precond == FM_PC_RB) {  // red-black pivots of both colours
+        DataArgs a = base_args(c);
+        a.d = c->d;
+        a.g = c->g[0];
+        a.z_new = c->p;
+        a.ip_out = c->ip;
+        FM_CK(cudaMemsetAsync(c->ip, 0, (size_t)c->nv * c->ts, c->stream), "clear pivots");
+        e = f64 ? launch_rb_black<double>(a, c->grid_data, c->stream) : launch_rb_black<float>(a, c->grid_data, c->stream);
+    } else {
+        e = f64 ? run_ic<double>(c, c->d, c->g[0], c->p, nullptr, nullptr)
+                : run_ic<float>(c, c->d, c->g[0], c->p, nullptr, nullptr);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "IC(0) kernels");
     if (inv_pivot)
         FM_CK(cudaMemcpyAsync(inv_pivot, c->ip, (size_t)c->nv * c->ts, cudaMemcpyDeviceToDevice, c->stream), "copy");
@@ -813,8 +844,21 @@ int fm_ic_apply(fm_ctx* c, const void* g, void* p) {
     if (!g || !p || g == p) return fail(c, FM_ERR_ARG, "g and p must be distinct device arrays");
     if (!c->have_factor) return fail(c, FM_ERR_STATE, "fm_ic_factor first");
     DevGuard guard(c->device);
-    cudaError_t e = c->o.precision == FM_FP64 ? run_ic<double>(c, nullptr, g, p, nullptr, nullptr)
-                                              : run_ic<float>(c, nullptr, g, p, nullptr, nullptr);
+    cudaError_t e;
+    if (c->o.precond == FM_PC_RB) {
+        DataArgs a = base_args(c);
+        a.g = const_cast<void*>(g);  // read only here
+        a.z_new = p;
+        a.ip_in = c->ip;
+        const bool f64 = c->o.precision == FM_FP64;
+        FM_CK(cudaMemsetAsync(p, 0, (size_t)c->nv * c->ts, c->stream), "clear");
+        e = f64 ? launch_rb_black<double>(a, c->grid_data, c->stream) : launch_rb_black<float>(a, c->grid_data, c->stream);
+        if (e == cudaSuccess)
+            e = f64 ? launch_rb_red<double>(a, c->grid_data, c->stream) : launch_rb_red<float>(a, c->grid_data, c->stream);
+    } else {
+        e = c->o.precision == FM_FP64 ? run_ic<double>(c, nullptr, g, p, nullptr, nullptr)
+                                      : run_ic<float>(c, nullptr, g, p, nullptr, nullptr);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "IC(0) kernels");
     return FM_OK;
 }

@@ -12,8 +12,9 @@ namespace fm {
 constexpr int kMaxPairs = FM_MAX_ECHO * (FM_MAX_ECHO - 1) / 2;
 
 // Neighbour-bit byte stored per voxel: bit 0 = voxel is an unknown (inside the mask);
-// bits 1..6 = its (-x, +x, -y, +y, -z, +z) neighbour exists and is an unknown too.
-enum : uint8_t { NB_IN = 1, NB_XM = 2, NB_XP = 4, NB_YM = 8, NB_YP = 16, NB_ZM = 32, NB_ZP = 64 };
+// bits 1..6 = its (-x, +x, -y, +y, -z, +z) neighbour exists and is an unknown too;
+// bit 7 = x + y + z is odd (the black colour of the red-black ordering; mask voxels only).
+enum : uint8_t { NB_IN = 1, NB_XM = 2, NB_XP = 4, NB_YM = 8, NB_YP = 16, NB_ZM = 32, NB_ZP = 64, NB_ODD = 128 };
 
 // Device scalar slots (double) kept per context.
 enum Scal {
@@ -228,6 +229,8 @@ struct DataArgs {
     const void* z_old;     // T [nv]
     void* z_new;           // T [nv]
     const void* g_prev;    // T [nv]
+    const void* ip_in;     // T [nv] stored inverse pivots (red-black apply) or null
+    void* ip_out;          // T [nv] inverse pivots out (red-black factor) or null
     double* scal;
     double* partials;      // [4][grid] (+ [2][2][grid] for the line search)
     double* cost_hist;     // device [niter+1] or null
@@ -313,6 +316,8 @@ template <typename T> cudaError_t launch_dir(const DataArgs& a, int grid, cudaSt
 template <typename T> cudaError_t launch_ls(const DataArgs& a, int grid, cudaStream_t s);
 template <typename T> cudaError_t launch_pdiag(const DataArgs& a, int mode, int grid, cudaStream_t s);
 template <typename T> int ls_max_blocks_per_sm(const DataArgs& a);
+template <typename T> cudaError_t launch_rb_black(const DataArgs& a, int grid, cudaStream_t s);
+template <typename T> cudaError_t launch_rb_red(const DataArgs& a, int grid, cudaStream_t s);
 template <typename T> cudaError_t launch_ic_fwd(const IcArgs& a, int grid, cudaStream_t s);
 template <typename T> cudaError_t launch_ic_bwd(const IcArgs& a, int grid, cudaStream_t s);
 template <typename T> cudaError_t launch_true_curv(const AdjArgs& a, int grid, cudaStream_t s);

@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(kSetupThreads) k_setup(SetupArgs a) {
             if (yy + 1 < ny && in_mask(a.mask, j + nx)) bits |= NB_YP;
             if (z > 0 && in_mask(a.mask, j - nxy)) bits |= NB_ZM;
             if (z + 1 < nz && in_mask(a.mask, j + nxy)) bits |= NB_ZP;
+            if ((x + yy + z) & 1) bits |= NB_ODD;
         }
         a.nb[j] = bits;
         if (!in) {

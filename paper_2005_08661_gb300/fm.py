@@ -18,11 +18,11 @@ FM_OK, FM_ERR_ARG, FM_ERR_STATE, FM_ERR_CUDA = 0, -1, -2, -3
 FM_ERR_NOT_PD, FM_ERR_TIMEOUT, FM_ERR_NONFINITE, FM_ERR_OOM = -4, -5, -6, -7
 FM_ERR_SIZE = -8
 FM_FP64, FM_FP32 = 0, 1
-FM_PC_IC0, FM_PC_DIAG, FM_PC_NONE = 0, 1, 2
+FM_PC_IC0, FM_PC_DIAG, FM_PC_NONE, FM_PC_RB = 0, 1, 2, 3
 FM_CURV_LITERAL, FM_CURV_COMBINED = 0, 1
 
 _PREC = {"fp32": FM_FP32, "fp64": FM_FP64}
-_PC = {"ic0": FM_PC_IC0, "diag": FM_PC_DIAG, "none": FM_PC_NONE}
+_PC = {"ic0": FM_PC_IC0, "diag": FM_PC_DIAG, "none": FM_PC_NONE, "rb": FM_PC_RB}
 _CURV = {"literal": FM_CURV_LITERAL, "combined": FM_CURV_COMBINED}
 
 
@@ -231,21 +231,21 @@ class FieldMap:
         self._check(self.lib.fm_set_fat_model(self._h, n, a, f), "fm_set_fat_model")
         self.fat_model = (tuple(amps), tuple(freqs)) if n else None
 
-    def wf_sweep(self, nsweep=100, w_lo=None, w_hi=None):
+    def wf_sweep(self, nsweep=100, w_lo=None, w_hi=None, out=None):
         """Voxel-wise sweep initialisation; the default range is +-pi |f| of the largest fat peak
         (+-|Delta_f / 2| in rad per unit of te)."""
         if w_lo is None or w_hi is None:
             amps, freqs = self.fat_model
             half = float(np.pi * abs(freqs[int(np.argmax(amps))]))
             w_lo, w_hi = -half, half
-        out = self.empty()
+        out = self.empty() if out is None else self._vec(out, "out")
         self._check(self.lib.fm_wf_sweep(self._h, int(nsweep), float(w_lo), float(w_hi), _dptr(out)), "fm_wf_sweep")
         return out
 
-    def pwls_init(self, omega_tilde, niter=10):
+    def pwls_init(self, omega_tilde, niter=10, out=None):
         """PWLS initialisation (niter CG iterations) from the sweep's map."""
         self._vec(omega_tilde, "omega_tilde")
-        out = self.empty()
+        out = self.empty() if out is None else self._vec(out, "out")
         self._check(self.lib.fm_pwls_init(self._h, _dptr(omega_tilde), int(niter), _dptr(out)), "fm_pwls_init")
         return out
 
@@ -253,13 +253,19 @@ class FieldMap:
         """Sweep then PWLS: the water-fat initial map."""
         return self.pwls_init(self.wf_sweep(nsweep), niter)
 
-    def wf_amplitudes(self, omega, y=None, smap=None):
+    def wf_amplitudes(self, omega, y=None, smap=None, out=None):
         """(water, fat) complex maps at omega by the closed form of the water-fat model."""
         self._vec(omega, "omega")
         if y is None:
             y, smap = self.data[0], self.data[1]
-        w = self._torch.empty(self.shape, dtype=self.cdtype, device=self.device)
-        f = self._torch.empty(self.shape, dtype=self.cdtype, device=self.device)
+        if out is None:
+            w = self._torch.empty(self.shape, dtype=self.cdtype, device=self.device)
+            f = self._torch.empty(self.shape, dtype=self.cdtype, device=self.device)
+        else:
+            w, f = out
+            for t in out:
+                if not (t.is_cuda and t.dtype == self.cdtype and t.is_contiguous() and tuple(t.shape) == self.shape):
+                    raise TypeError(f"out tensors must be contiguous {self.cdtype} CUDA tensors of shape {self.shape}")
         self._check(self.lib.fm_wf_amplitudes(self._h, _dptr(y), _dptr(smap), _dptr(omega), _dptr(w), _dptr(f)),
                     "fm_wf_amplitudes")
         return w, f

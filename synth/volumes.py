@@ -306,6 +306,13 @@ def diff_config(seed=1005, **kw):
                        nblobs=6, step_hz=40.0, name="diff_128x128x64_c8", **kw)
 
 
+def phantom_config(seed=1006, **kw):
+    """74x74x10, 32 coils, echoes 0/1/2.3 ms, beta 2^-3: the shape of the paper's phantom
+    comparison (Sec. IV), with the synthetic phantom and a smooth +-150 Hz field."""
+    return make_volume(74, 74, 10, ncoil=32, te=(0.0, 1.0, 2.3), snr_db=20.0, seed=seed, fmax_hz=150.0,
+                       nblobs=4, name="phantom_74x74x10_c32", **kw)
+
+
 def batch_configs(n=32, seed=1004):
     """Sizes/coils/SNRs of n independent volumes from 64x64x16 up to 192x192x96."""
     rng = np.random.default_rng(seed)
