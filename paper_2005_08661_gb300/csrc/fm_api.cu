@@ -209,6 +209,7 @@ cudaError_t run_ic(fm_ctx* c, const void* d, const void* g, void* p, const void*
     b.flags = c->icint + 4 + c->ntiles;
     b.ticket = c->icint + 1;
     b.done = c->icint + 2;
+    b.order = c->order + c->ntiles;
     b.vin = c->v;
     b.ipb = c->ip;
     b.p = p;
@@ -651,24 +652,31 @@ int fm_create(fm_ctx** out, int nx, int ny, int nz, int ncoil, int necho, const 
     A(&c->tile_part, 2 * (size_t)c->ntiles * sizeof(double));
     A(&c->istate, I_NISTATE * sizeof(int));
     A(&c->icint, (4 + 2 * (size_t)c->ntiles) * sizeof(int));
-    A(&c->order, (size_t)c->ntiles * sizeof(int));
+    A(&c->order, 2 * (size_t)c->ntiles * sizeof(int));  // forward order, then the back substitution's
     if (!ok) { cudaGetLastError(); return bail(FM_ERR_OOM); }
-    // tiles in order of a weighted tile hyperplane wxy (X + Y) + wz Z (ties: z, y, x): every
-    // weight is positive, so a tile's -x, -y, -z neighbours always come first
+    // Tiles in order of a weighted tile hyperplane wxy (X + Y) + wz Z (ties: z, y, x).  Every
+    // weight is positive, so a tile's -x, -y, -z neighbours always come first.  The forward
+    // sweep streams faces and a tile starts about 2x more steps behind its x / y
+    // predecessors than behind its z predecessor, hence 2 : 1; the tile-by-tile back
+    // substitution (which walks its order backwards) uses the plain hyperplane X + Y + Z.
 #ifndef FM_IC_WXY
-#define FM_IC_WXY 1
+#define FM_IC_WXY 2
 #endif
 #ifndef FM_IC_WZ
 #define FM_IC_WZ 1
 #endif
-    std::vector<int> ord(c->ntiles);
-    for (int t = 0; t < c->ntiles; ++t) ord[t] = t;
+    std::vector<int> ord(2 * (size_t)c->ntiles);
     const int ntx = c->ntx, nty = c->nty;
-    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
-        const int ha = FM_IC_WXY * (a % ntx + (a / ntx) % nty) + FM_IC_WZ * (a / (ntx * nty));
-        const int hb = FM_IC_WXY * (b % ntx + (b / ntx) % nty) + FM_IC_WZ * (b / (ntx * nty));
-        return ha != hb ? ha < hb : a < b;
-    });
+    for (int pass = 0; pass < 2; ++pass) {
+        const int wxy = pass == 0 ? FM_IC_WXY : 1, wz = pass == 0 ? FM_IC_WZ : 1;
+        auto first = ord.begin() + (size_t)pass * c->ntiles;
+        for (int t = 0; t < c->ntiles; ++t) first[t] = t;
+        std::stable_sort(first, first + c->ntiles, [&](int a, int b) {
+            const int ha = wxy * (a % ntx + (a / ntx) % nty) + wz * (a / (ntx * nty));
+            const int hb = wxy * (b % ntx + (b / ntx) % nty) + wz * (b / (ntx * nty));
+            return ha != hb ? ha < hb : a < b;
+        });
+    }
     if (cudaMemcpy(c->order, ord.data(), ord.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(c->scal, 0, S_NSCAL * sizeof(double)) != cudaSuccess ||
         cudaMemset(c->istate, 0, I_NISTATE * sizeof(int)) != cudaSuccess ||
