@@ -39,8 +39,6 @@ if ROOT not in sys.path:
 # kernel), from one capture of the full workload (profiles/traffic_full_256x256x128_c8.md);
 # an entry is removed when its kernel changes.
 NCU_TRAFFIC_BYTES = {
-    ("full", "ls"): 1944825856 + 177280,
-    ("full", "grad"): 504680704 + 21979008,
     ("full", "ic_bwd"): 134266496 + 17990656,
     ("full", "dir"): 64359680 + 1216640,
 }
@@ -102,14 +100,14 @@ def data_eval_flops(nc, L, literal):
 
     Per echo pair: phase (2), half-angle sine/cosine (20), gradient/cost terms (6).  Literal
     curvature per (pair, c, d): phase difference (1), wrap to [-pi, pi] (5), u^2 (1),
-    degree-6 polynomial in u^2 for sin(u)/u (12), amplitude multiply-accumulate (2) = 21;
+    degree-5 polynomial in u^2 for sin(u)/u (10), amplitude multiply-accumulate (2) = 19;
     plus 2 per (pair, d) for the rotated phase and 2 per (pair, c) for the outer sum."""
     P = L * (L - 1) // 2
     per_pair = 28
     if literal:
-        per_pair += nc * nc * 21 + 4 * nc
+        per_pair += nc * nc * 19 + 4 * nc
     else:
-        per_pair += 21
+        per_pair += 19
     return P * per_pair
 
 
@@ -437,6 +435,33 @@ def run_ours(args, world, rank, local):
     if rank == 0 and not args.no_ttc:
         ttc = time_to_oracle_cost(prec, stream)
 
+    # the precision form against the plain FP64 GPU solve of the same workload (untimed)
+    fp64cmp = None
+    if rank == 0 and prec == "fp32" and not args.no_fp64_check:
+        w32, c32 = fm.solve(None, niter=niter)
+        w32 = w32.double()
+        ref = FieldMap(vol.nx, vol.ny, vol.nz, ncoil=vol.ncoil, necho=vol.necho, precision="fp64", device=local,
+                       stream=stream)
+        ref.set_data(y_d.to(torch.complex128), s_d.to(torch.complex128) if s_d is not None else None, vol.te, m_d,
+                     vol.beta)
+        if wf:
+            ref.set_fat_model(vol.meta["fat_amps"], vol.meta["fat_freqs_khz"])
+            ref.set_data(y_d.to(torch.complex128), s_d.to(torch.complex128) if s_d is not None else None, vol.te,
+                         m_d, vol.beta)
+            w64_0 = ref.pwls_init(ref.wf_sweep(100), 10)
+            w64, c64 = ref.solve(w64_0, niter=niter)
+            w32_0 = fm.pwls_init(fm.wf_sweep(100), 10)
+            w32, c32 = fm.solve(w32_0, niter=niter)
+            w32 = w32.double()
+        else:
+            w64, c64 = ref.solve(None, niter=niter)
+        ref.close()
+        mk = m_d.bool()
+        dhz = (w32 - w64)[mk].abs() * 1000.0 / (2 * math.pi)
+        fp64cmp = {"final_cost_rel": abs(c32[-1] - c64[-1]) / abs(c64[-1]),
+                   "rmse_hz": float(dhz.pow(2).mean().sqrt()), "max_abs_hz": float(dhz.max()),
+                   "what": f"FP32 path vs the FP64 GPU path, {niter} iterations each, over the mask"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, units = oracle_sample(vol, 4)
@@ -458,7 +483,7 @@ def run_ours(args, world, rank, local):
                        "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (2.1 GB streamed per step)",
                        "masked_voxel_iters_per_s": world * nmask * niter / t_step},
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "kernels": kernels, "clocks": clk,
-            "cpu_baseline": cpu, "time_to_oracle_cost": ttc}
+            "cpu_baseline": cpu, "time_to_oracle_cost": ttc, "fp32_vs_fp64_gpu": fp64cmp}
     if rank == 0:
         print(json.dumps(line), flush=True)
     fm.close()
@@ -493,6 +518,7 @@ def run_batch(args, world, rank, local):
     for k, v in enumerate(vols):
         b.set_data(k, dev_in[k][0], dev_in[k][1], v.te, dev_in[k][2], v.beta)
     frac, _ = b.autotune(niter_probe=4)
+    _, order_w = b.schedule()
     ws = [b.empty(k) for k in range(len(vols))]
     ptrs = (C.c_void_p * len(vols))(*[w.data_ptr() for w in ws])
 
@@ -525,15 +551,39 @@ def run_batch(args, world, rank, local):
     t_b = max_over_ranks(timed(step_batch), world, dev)
     clk = clocks.stop()
     t_s = max_over_ranks(timed(step_seq), world, dev)
+
+    # the batched FP32 maps against plain FP64 GPU solves of a sample of the volumes (untimed)
+    cmp = None
+    if rank == 0 and args.precision == "fp32":
+        step_batch()
+        torch.cuda.synchronize(dev)
+        order = sorted(range(len(vols)), key=lambda k: vols[k].nvox)
+        sample = sorted({order[0], order[len(order) // 3], order[2 * len(order) // 3], order[-1]})
+        worst = {"rmse_hz": 0.0, "max_abs_hz": 0.0}
+        for k in sample:
+            v = vols[k]
+            ref = FieldMap(v.nx, v.ny, v.nz, ncoil=v.ncoil, necho=v.necho, precision="fp64", device=local,
+                           stream=stream)
+            s64 = dev_in[k][1].to(torch.complex128) if dev_in[k][1] is not None else None
+            ref.set_data(dev_in[k][0].to(torch.complex128), s64, v.te, dev_in[k][2], v.beta)
+            w64, _ = ref.solve(None, niter=niter, want_history=False)
+            ref.close()
+            mk = dev_in[k][2].bool()
+            dhz = (ws[k].double() - w64)[mk].abs() * 1000.0 / (2 * math.pi)
+            worst["rmse_hz"] = max(worst["rmse_hz"], float(dhz.pow(2).mean().sqrt()))
+            worst["max_abs_hz"] = max(worst["max_abs_hz"], float(dhz.max()))
+        cmp = dict(worst, volumes=[f"{vols[k].nx}x{vols[k].ny}x{vols[k].nz}_c{vols[k].ncoil}" for k in sample],
+                   what=f"batched FP32 maps vs plain FP64 GPU solves, {niter} iterations, over the mask (worst)")
     line = {"metric": "voxel-NCG-iters/s", "value": world * nvox * niter / t_b, "unit": "voxel-iter/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t_b,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": WORKLOADS["batch"]["desc"], "volumes": len(vols), "voxels": nvox, "niter": niter,
-                       "grid_fraction": frac, "parallelism": f"replicas{world}"},
+                       "grid_fraction": frac, "ic_tile_order_weights": list(order_w),
+                       "parallelism": f"replicas{world}"},
             "sequential": {"value": world * nvox * niter / t_s, "ms_per_step": 1000 * t_s,
                            "what": "the same 32 volumes, fm_set_data + fm_solve one after another"},
-            "speedup_vs_sequential": t_s / t_b, "clocks": clk}
+            "speedup_vs_sequential": t_s / t_b, "fp32_vs_fp64_gpu": cmp, "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)
     for f in singles:
@@ -764,6 +814,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttc", action="store_true")
+    ap.add_argument("--no-fp64-check", action="store_true")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if world > 1:

@@ -47,6 +47,7 @@ struct fm_ctx {
     int* icint = nullptr;  // [0] fwd ticket, [1] bwd ticket, [2] bwd done, [3] pad, flags fwd[nt], flags bwd[nt]
     int* order = nullptr;
     int ntx = 0, nty = 0, ntz = 0, ntiles = 0;
+    int ic_wxy = 2, ic_wz = 1;  // forward tile claim order weights
     int nsm = 0, grid_data = 0, grid_ls = 0, grid_ic = 0;
     int base_data = 0, base_ls = 0, base_ic = 0;  // grids chosen at creation (batch autotuning scales them)
     int last_niter = 0;
@@ -506,6 +507,30 @@ int implicit_t(fm_ctx* c, const void* y, const void* smap, const void* w_hat, co
     return FM_OK;
 }
 
+// Tile claim orders: a weighted tile hyperplane wxy (X + Y) + wz Z (ties: z, y, x).  Every
+// weight is positive, so a tile's -x, -y, -z neighbours always come first.  The forward sweep
+// streams faces, and a tile there starts about twice as many steps behind its x / y
+// predecessors as behind its z predecessor, so it takes wxy : wz (default 2 : 1).  The
+// tile-by-tile back substitution walks the plain hyperplane X + Y + Z backwards.  Uploads
+// both orders synchronously.
+bool set_ic_order(fm_ctx* c, int wxy, int wz) {
+    std::vector<int> ord(2 * (size_t)c->ntiles);
+    const int ntx = c->ntx, nty = c->nty;
+    for (int pass = 0; pass < 2; ++pass) {
+        const int a_xy = pass == 0 ? wxy : 1, a_z = pass == 0 ? wz : 1;
+        auto first = ord.begin() + (size_t)pass * c->ntiles;
+        for (int t = 0; t < c->ntiles; ++t) first[t] = t;
+        std::stable_sort(first, first + c->ntiles, [&](int a, int b) {
+            const int ha = a_xy * (a % ntx + (a / ntx) % nty) + a_z * (a / (ntx * nty));
+            const int hb = a_xy * (b % ntx + (b / ntx) % nty) + a_z * (b / (ntx * nty));
+            return ha != hb ? ha < hb : a < b;
+        });
+    }
+    c->ic_wxy = wxy;
+    c->ic_wz = wz;
+    return cudaMemcpy(c->order, ord.data(), ord.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
 // Cooperative line-search grid: every block must be co-resident, so the grid follows the
 // occupancy of the kernel variant the context launches.
 template <typename T>
@@ -654,30 +679,13 @@ int fm_create(fm_ctx** out, int nx, int ny, int nz, int ncoil, int necho, const 
     A(&c->icint, (4 + 2 * (size_t)c->ntiles) * sizeof(int));
     A(&c->order, 2 * (size_t)c->ntiles * sizeof(int));  // forward order, then the back substitution's
     if (!ok) { cudaGetLastError(); return bail(FM_ERR_OOM); }
-    // Tiles in order of a weighted tile hyperplane wxy (X + Y) + wz Z (ties: z, y, x).  Every
-    // weight is positive, so a tile's -x, -y, -z neighbours always come first.  The forward
-    // sweep streams faces and a tile starts about 2x more steps behind its x / y
-    // predecessors than behind its z predecessor, hence 2 : 1; the tile-by-tile back
-    // substitution (which walks its order backwards) uses the plain hyperplane X + Y + Z.
 #ifndef FM_IC_WXY
 #define FM_IC_WXY 2
 #endif
 #ifndef FM_IC_WZ
 #define FM_IC_WZ 1
 #endif
-    std::vector<int> ord(2 * (size_t)c->ntiles);
-    const int ntx = c->ntx, nty = c->nty;
-    for (int pass = 0; pass < 2; ++pass) {
-        const int wxy = pass == 0 ? FM_IC_WXY : 1, wz = pass == 0 ? FM_IC_WZ : 1;
-        auto first = ord.begin() + (size_t)pass * c->ntiles;
-        for (int t = 0; t < c->ntiles; ++t) first[t] = t;
-        std::stable_sort(first, first + c->ntiles, [&](int a, int b) {
-            const int ha = wxy * (a % ntx + (a / ntx) % nty) + wz * (a / (ntx * nty));
-            const int hb = wxy * (b % ntx + (b / ntx) % nty) + wz * (b / (ntx * nty));
-            return ha != hb ? ha < hb : a < b;
-        });
-    }
-    if (cudaMemcpy(c->order, ord.data(), ord.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+    if (!set_ic_order(c, FM_IC_WXY, FM_IC_WZ) ||
         cudaMemset(c->scal, 0, S_NSCAL * sizeof(double)) != cudaSuccess ||
         cudaMemset(c->istate, 0, I_NISTATE * sizeof(int)) != cudaSuccess ||
         cudaMemset(c->nb, 0, (size_t)c->nv) != cudaSuccess)
@@ -1246,33 +1254,50 @@ int fm_batch_autotune(fm_batch* b, int niter_probe, double* best_fraction, doubl
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     ok = ok && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
     const double cand[4] = {1.0, 0.5, 0.25, 0.125};
+    const int wcand[3][2] = {{2, 1}, {1, 1}, {3, 2}};  // forward tile claim order weights (X + Y, Z)
     double bestf = b->fraction, bestt = 1e300;
+    int bestw = 0;
     int rc = ok ? FM_OK : FM_ERR_OOM;
-    for (int q = 0; q < 4 && rc == FM_OK; ++q) {
-        b->fraction = cand[q];
-        batch_apply_fraction(b);
-        rc = batch_solve(b, w.data(), 1, niter_probe, nullptr);  // warm-up and capture
-        if (rc != FM_OK) break;
-        cudaEventRecord(e0, b->origin);
-        rc = batch_solve(b, w.data(), 1, niter_probe, nullptr);
-        cudaEventRecord(e1, b->origin);
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (rc == FM_OK && ms < bestt) {
-            bestt = ms;
-            bestf = cand[q];
+    for (int wq = 0; wq < 3 && rc == FM_OK; ++wq) {
+        for (fm_ctx* c : b->v)
+            if (!set_ic_order(c, wcand[wq][0], wcand[wq][1])) rc = FM_ERR_CUDA;
+        for (int q = 0; q < 4 && rc == FM_OK; ++q) {
+            b->fraction = cand[q];
+            batch_apply_fraction(b);
+            rc = batch_solve(b, w.data(), 1, niter_probe, nullptr);  // warm-up and capture
+            if (rc != FM_OK) break;
+            cudaEventRecord(e0, b->origin);
+            rc = batch_solve(b, w.data(), 1, niter_probe, nullptr);
+            cudaEventRecord(e1, b->origin);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rc == FM_OK && ms < bestt) {
+                bestt = ms;
+                bestf = cand[q];
+                bestw = wq;
+            }
         }
     }
     for (void* p : w)
         if (p) cudaFree(p);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
+    for (fm_ctx* c : b->v)
+        if (!set_ic_order(c, wcand[bestw][0], wcand[bestw][1]) && rc == FM_OK) rc = FM_ERR_CUDA;
     b->fraction = bestf;
     batch_apply_fraction(b);
     if (best_fraction) *best_fraction = bestf;
     if (best_ms) *best_ms = bestt;
     return rc;
+}
+
+int fm_batch_schedule(const fm_batch* b, double* fraction, int* order_wxy, int* order_wz) {
+    if (!b || b->v.empty()) return FM_ERR_ARG;
+    if (fraction) *fraction = b->fraction;
+    if (order_wxy) *order_wxy = b->v[0]->ic_wxy;
+    if (order_wz) *order_wz = b->v[0]->ic_wz;
+    return FM_OK;
 }
 
 fm_ctx* fm_batch_ctx(fm_batch* b, int k) {

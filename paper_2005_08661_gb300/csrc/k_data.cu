@@ -32,18 +32,17 @@ __device__ __forceinline__ double wrap_angle(double t) {
     return t - 6.283185307179586476925286766559 * rint(t * 0.15915494309189533576888376337251);
 }
 
-// sin(u)/u on the wrapped interval [-pi, pi] as a degree-6 polynomial in v = u^2: the
-// discrete minimax fit derived by csrc/sinc_poly.py (truncation error 7.7e-10, below float
-// rounding; 8.9e-8 overall in float Horner form).
+// sin(u)/u on the wrapped interval [-pi, pi] as a degree-5 polynomial in v = u^2: the
+// discrete minimax fit derived by csrc/sinc_poly.py (truncation error 6.4e-8, 2.3e-7 overall
+// in float Horner form, the level of float rounding of the weights).
 __device__ __forceinline__ float sinc_wrapped(float u) {
     const float v = u * u;
-    float p = 1.360021817387036e-10f;
-    p = fmaf(p, v, -2.4725343550358048e-08f);
-    p = fmaf(p, v, 2.753550461420673e-06f);
-    p = fmaf(p, v, -0.00019840517779812217f);
-    p = fmaf(p, v, 0.00833332072943449f);
-    p = fmaf(p, v, -0.1666666567325592f);
-    return fmaf(p, v, 1.0f);
+    float p = -2.0676877099390367e-08f;
+    p = fmaf(p, v, 2.708367901504971e-06f);
+    p = fmaf(p, v, -0.00019817284191958606f);
+    p = fmaf(p, v, 0.008332781493663788f);
+    p = fmaf(p, v, -0.1666661947965622f);
+    return fmaf(p, v, 0.9999999403953552f);
 }
 __device__ __forceinline__ double sinc_wrapped(double u) { return u == 0.0 ? 1.0 : sin(u) / u; }
 

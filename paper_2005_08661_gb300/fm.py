@@ -44,6 +44,7 @@ EXPORTS = ["fm_default_opts", "fm_create", "fm_set_data", "fm_init_omega", "fm_c
            "fm_ic_apply", "fm_solve", "fm_get_history", "fm_set_profiling", "fm_kernel_times", "fm_destroy",
            "fm_strerror", "fm_last_error", "fm_cost_grad_noalloc", "fm_batch_create", "fm_batch_set_data",
            "fm_batch_solve", "fm_batch_autotune", "fm_batch_set_fraction", "fm_batch_ctx", "fm_batch_destroy",
+           "fm_batch_schedule",
            "fm_true_curv", "fm_adjoint_solve", "fm_implicit_grad", "fm_set_fat_model", "fm_wf_sweep",
            "fm_pwls_init", "fm_wf_amplitudes"]
 KERNELS = ["grad", "ic_fwd", "ic_bwd", "dir", "ls"]
@@ -99,11 +100,12 @@ def load_library(path=None):
         lib.fm_batch_solve.argtypes = [vp, C.POINTER(vp), i, i, C.POINTER(C.POINTER(d))]
         lib.fm_batch_autotune.argtypes = [vp, i, C.POINTER(d), C.POINTER(d)]
         lib.fm_batch_set_fraction.argtypes = [vp, d]
+        lib.fm_batch_schedule.argtypes = [vp, C.POINTER(d), C.POINTER(i), C.POINTER(i)]
         lib.fm_batch_ctx.argtypes = [vp, i]
         lib.fm_batch_ctx.restype = vp
         lib.fm_batch_destroy.argtypes = [vp]
         for fn in ("fm_batch_create", "fm_batch_set_data", "fm_batch_solve", "fm_batch_autotune",
-                   "fm_batch_set_fraction", "fm_batch_destroy"):
+                   "fm_batch_set_fraction", "fm_batch_destroy", "fm_batch_schedule"):
             getattr(lib, fn).restype = C.c_int
         lib.fm_strerror.argtypes = [i]
         lib.fm_strerror.restype = C.c_char_p
@@ -423,6 +425,12 @@ class FieldMapBatch:
 
     def set_fraction(self, f):
         self._check(self.lib.fm_batch_set_fraction(self._h, float(f)), "fm_batch_set_fraction")
+
+    def schedule(self):
+        """(grid fraction, (X + Y weight, Z weight) of the forward tile order) in effect."""
+        f, wxy, wz = C.c_double(), C.c_int(), C.c_int()
+        self._check(self.lib.fm_batch_schedule(self._h, C.byref(f), C.byref(wxy), C.byref(wz)), "fm_batch_schedule")
+        return f.value, (wxy.value, wz.value)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -53,6 +53,8 @@ def test_batch_autotune_picks_a_candidate_and_results_stay_correct():
         b.set_data(k, y, s, v.te, m, v.beta)
     f, ms = b.autotune(niter_probe=2)
     assert f in (1.0, 0.5, 0.25, 0.125) and ms > 0
+    frac, weights = b.schedule()
+    assert frac == f and weights in ((2, 1), (1, 1), (3, 2))
     ws, costs = b.solve(niter=4)
     for k, v in enumerate(vols):
         r = Oracle.from_volume(v).solve(niter=4, nls=5)
