@@ -501,8 +501,12 @@ __global__ void __launch_bounds__(kThreadsIC) k_ic_fwd(IcArgs a, int mode, PivSc
             P out_ip = Ops::zero();
             T out_v = 0;
             bool bad = false;
-            for (int s = 0; s < kSteps; ++s) {
-                if (s % kCS == 0) wait_chunk(&s_ready, s / kCS, wlimit, a.istate);
+            for (int c = 0; c < kNch; ++c) {
+              wait_chunk(&s_ready, c, wlimit, a.istate);
+#pragma unroll
+              for (int q = 0; q < kCS; ++q) {
+                const int s = c * kCS + q;
+                if (kSteps % kCS != 0 && s >= kSteps) break;
                 const P up_ip = shfl_up(out_ip);
                 const T up_v = __shfl_up_sync(0xffffffffu, out_v, 1);
                 const int lx = s - l0;
@@ -560,7 +564,8 @@ __global__ void __launch_bounds__(kThreadsIC) k_ic_fwd(IcArgs a, int mode, PivSc
                     }
                 }
                 bar_compute();
-                if (tid == 0 && ((s + 1) % kCS == 0 || s == kSteps - 1)) st_rel_cta(&s_done, s + 1);
+              }
+              if (tid == 0) st_rel_cta(&s_done, min((c + 1) * kCS, kSteps));
             }
             if (bad) set_err(a.istate, FM_ERR_NOT_PD);
             // write back row-coalesced (warp lz writes its 32 rows, lane = x)
