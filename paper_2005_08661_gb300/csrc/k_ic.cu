@@ -221,6 +221,10 @@ constexpr int kCompute = 32 * kTZ;  // compute threads
 constexpr bool kSplit = FM_IC_SPLIT != 0;  // separate warps fetch faces and publish progress
 constexpr int kThreadsIC = kCompute + (kSplit ? 64 : 32);
 constexpr unsigned kSleepMax = FM_IC_SLEEP;  // cap of the streaming warps' poll backoff (ns)
+#ifndef FM_IC_BWD_UNROLL
+#define FM_IC_BWD_UNROLL 7
+#endif
+constexpr int kBwdUnroll = FM_IC_BWD_UNROLL;  // unroll factor of the back substitution's step loop
 
 // Face layout per tile (counts of values): x face [TZ][32] (lz, ly), y face [TZ][32]
 // (lz, lx), z face [32][32] (ly, lx).
@@ -658,6 +662,7 @@ __global__ void __launch_bounds__(32 * kTZ) k_ic_bwd(IcArgs a) {
         const T* fz = f_p + FN::z + ly * 32;
         const int zr = (lz < kTZ - 1 ? lz + 1 : lz) * 32 + ly, zw = lz * 32 + ly;
         T out = 0;
+#pragma unroll kBwdUnroll
         for (int s = kSteps - 1; s >= 0; --s) {
             const T dn = __shfl_down_sync(0xffffffffu, out, 1);
             const int lx = s - l0;
