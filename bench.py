@@ -39,8 +39,11 @@ if ROOT not in sys.path:
 # kernel), from one capture of the full workload (profiles/traffic_full_256x256x128_c8.md);
 # an entry is removed when its kernel changes.
 NCU_TRAFFIC_BYTES = {
-    ("full", "ic_bwd"): 134266496 + 17990656,
-    ("full", "dir"): 64359680 + 1216640,
+    ("full", "ls"): 1944660352 + 214784,
+    ("full", "grad"): 504742656 + 21807232,
+    ("full", "ic_fwd"): 78002944 + 34450176,
+    ("full", "ic_bwd"): 134262016 + 18184704,
+    ("full", "dir"): 64362240 + 1252096,
 }
 
 WORKLOADS = {
@@ -401,34 +404,40 @@ def run_ours(args, world, rank, local):
     per_iter = {k: v[0] for k, v in kt.items() if v[1] > 0}
     dom = max(per_iter, key=per_iter.get) if per_iter else None
     literal = vol.ncoil > 1
-    roof = None
-    if dom is not None:
-        ms = per_iter[dom]
-        evals = {"grad": 1, "ls": 4}.get(dom, 0)
+    def kernel_roofline(name, ms):
+        """Algorithmic work of one launch of kernel class `name` against its bound."""
+        evals = {"grad": 1, "ls": 4}.get(name, 0)
+        ts = 4 if prec == "fp32" else 8
         if evals and literal:
             flops = evals * nmask * data_eval_flops(vol.ncoil, vol.necho, True)
             ach = flops / (ms * 1e-3) / 1e12
-            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
+            return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
                     "frac": ach / peaks["fp32_tflops"], "peak_src": "derived: 2 flops x 128 FP32 lanes x "
-                    f"{nsm} SMs x {sm_max:.0f} MHz", "ms_per_launch": ms,
-                    "algorithmic_flops_per_launch": flops,
-                    "traffic": NCU_TRAFFIC_BYTES.get((args.workload, dom))}
-        else:
-            ts = 4 if prec == "fp32" else 8
-            if evals:
-                byts = evals * (nmask * data_eval_bytes(vol.ncoil, vol.necho, literal, ts) + nv)
-            elif dom == "ic_fwd":
-                byts = nv * (1 + 2 * ts + 2 * ts)
-            elif dom == "ic_bwd":
-                byts = nv * (1 + 2 * ts + 3 * ts)
-            else:  # direction pass over the mask list: index, bits, p, z, w, g, d in, z out
-                byts = nmask * (4 + 1 + 6 * ts)
-            ach = byts / (ms * 1e-3) / 1e9
-            roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / peaks["hbm_gbs"], "peak_src": peaks["hbm_src"], "ms_per_launch": ms,
-                    "algorithmic_bytes_per_launch": byts, "traffic": NCU_TRAFFIC_BYTES.get((args.workload, dom))}
-    kernels = {k: {"ms_per_launch": v[0], "share_of_iteration": (v[0] / sum(per_iter.values()) if per_iter else None)}
-               for k, v in kt.items() if v[1] > 0}
+                    f"{nsm} SMs x {sm_max:.0f} MHz", "ms_per_launch": ms, "algorithmic_flops_per_launch": flops,
+                    "traffic": NCU_TRAFFIC_BYTES.get((args.workload, name))}
+        if evals:
+            byts = evals * (nmask * data_eval_bytes(vol.ncoil, vol.necho, literal, ts) + nv)
+        elif name == "ic_fwd":  # per grid voxel: bits, d and g in, pivots and v out
+            byts = nv * (1 + 2 * ts + 2 * ts)
+        elif name == "ic_bwd":  # per grid voxel: bits, v, pivots, g, g_prev in, p out
+            byts = nv * (1 + 2 * ts + 3 * ts)
+        else:  # direction pass over the mask list: index, bits, p, z, w, g, d in, z out
+            byts = nmask * (4 + 1 + 6 * ts)
+        ach = byts / (ms * 1e-3) / 1e9
+        out = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+               "frac": ach / peaks["hbm_gbs"], "peak_src": peaks["hbm_src"], "ms_per_launch": ms,
+               "algorithmic_bytes_per_launch": byts, "traffic": NCU_TRAFFIC_BYTES.get((args.workload, name))}
+        if name.startswith("ic"):
+            out["note"] = "latency-bound wavefront: the HBM fraction is reported for reference only"
+        return out
+
+    roof = kernel_roofline(dom, per_iter[dom]) if dom is not None else None
+    kernels = {}
+    for k, v in kt.items():
+        if v[1] > 0:
+            r = kernel_roofline(k, v[0])
+            kernels[k] = {"ms_per_launch": v[0], "share_of_iteration": v[0] / sum(per_iter.values()),
+                          "bound": r["bound"], "achieved": r["achieved"], "unit": r["unit"], "frac": r["frac"]}
 
     # time to the oracle's final cost on the small workload (stored by tests/golden/make_golden.py)
     ttc = None
