@@ -438,6 +438,9 @@ def run_ours(args, world, rank, local):
             r = kernel_roofline(k, v[0])
             kernels[k] = {"ms_per_launch": v[0], "share_of_iteration": v[0] / sum(per_iter.values()),
                           "bound": r["bound"], "achieved": r["achieved"], "unit": r["unit"], "frac": r["frac"]}
+            tb = NCU_TRAFFIC_BYTES.get((args.workload, k))
+            if tb:  # ncu DRAM bytes of one launch over its CUDA-event time, against the HBM peak
+                kernels[k]["hbm_traffic_frac"] = tb / (v[0] * 1e-3) / 1e9 / peaks["hbm_gbs"]
 
     # time to the oracle's final cost on the small workload (stored by tests/golden/make_golden.py)
     ttc = None
