@@ -48,8 +48,8 @@ struct fm_ctx {
     int* order = nullptr;
     int ntx = 0, nty = 0, ntz = 0, ntiles = 0;
     int ic_wxy = 2, ic_wz = 1;  // forward tile claim order weights
-    int nsm = 0, grid_data = 0, grid_ls = 0, grid_ic = 0;
-    int base_data = 0, base_ls = 0, base_ic = 0;  // grids chosen at creation (batch autotuning scales them)
+    int nsm = 0, grid_data = 0, grid_ls = 0, grid_ic = 0, grid_icb = 0;  // grid_icb: backward IC sweep
+    int base_data = 0, base_ls = 0, base_ic = 0, base_icb = 0;  // grids chosen at creation (batch autotuning scales them)
     int last_niter = 0;
     cudaGraphExec_t gexec = nullptr;
     cudaGraphExec_t cg_gexec = nullptr;  // adjoint CG iterations (tolerance and limit are arguments)
@@ -218,7 +218,7 @@ cudaError_t run_ic(fm_ctx* c, const void* d, const void* g, void* p, const void*
     b.gpdot = gpdot;
     b.tile_part = (gdot || gpdot) ? c->tile_part : nullptr;
     if (slot >= 0 && c->profiling) cudaEventRecordWithFlags(c->ev[slot][FM_K_IC_BWD][0], c->stream, cudaEventRecordExternal);
-    e = launch_ic_bwd<T>(b, c->grid_ic, c->stream);
+    e = launch_ic_bwd<T>(b, c->grid_icb, c->stream);
     if (slot >= 0 && c->profiling) {
         cudaEventRecordWithFlags(c->ev[slot][FM_K_IC_BWD][1], c->stream, cudaEventRecordExternal);
         c->ev_rec[slot][FM_K_IC_BWD] = true;
@@ -650,13 +650,19 @@ int fm_create(fm_ctx** out, int nx, int ny, int nz, int ncoil, int necho, const 
     c->ntz = (nz + tz - 1) / tz;
     c->ntiles = c->ntx * c->nty * c->ntz;
     {
-        const int occ = o.precision == FM_FP64 ? ic_max_blocks_per_sm<double>() : ic_max_blocks_per_sm<float>();
-        if (occ < 1) return bail(FM_ERR_CUDA);
-        c->grid_ic = std::max(1, std::min(c->ntiles, occ * c->nsm));
+        // the two sweeps claim tiles from their own tickets, so each takes as many
+        // resident blocks as its own footprint allows
+        const bool f64 = o.precision == FM_FP64;
+        const int occ_f = f64 ? ic_max_blocks_per_sm<double>(false) : ic_max_blocks_per_sm<float>(false);
+        const int occ_b = f64 ? ic_max_blocks_per_sm<double>(true) : ic_max_blocks_per_sm<float>(true);
+        if (occ_f < 1 || occ_b < 1) return bail(FM_ERR_CUDA);
+        c->grid_ic = std::max(1, std::min(c->ntiles, occ_f * c->nsm));
+        c->grid_icb = std::max(1, std::min(c->ntiles, occ_b * c->nsm));
     }
     c->base_data = c->grid_data;
     c->base_ls = c->grid_ls;
     c->base_ic = c->grid_ic;
+    c->base_icb = c->grid_icb;
     const size_t vb = (size_t)c->nv * c->ts;
     const int P = necho * (necho - 1) / 2;
     bool ok = true;
@@ -1083,6 +1089,7 @@ void batch_apply_fraction(fm_batch* b) {
         c->grid_data = std::max(1, (int)std::lround(c->base_data * b->fraction));
         c->grid_ls = std::max(1, (int)std::lround(c->base_ls * b->fraction));
         c->grid_ic = std::max(1, (int)std::lround(c->base_ic * b->fraction));
+        c->grid_icb = std::max(1, (int)std::lround(c->base_icb * b->fraction));
         if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
     }
     if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }

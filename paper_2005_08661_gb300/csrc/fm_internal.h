@@ -332,7 +332,7 @@ template <typename T> cudaError_t launch_wf_sweep(const AdjArgs& a, int nsweep, 
 template <typename T> cudaError_t launch_wf_amp(const AdjArgs& a, int grid, cudaStream_t s);
 template <typename T> int ic_tz();
 template <typename T> size_t ic_face_bytes_per_tile();
-template <typename T> int ic_max_blocks_per_sm();
+template <typename T> int ic_max_blocks_per_sm(bool bwd);  // resident IC sweep blocks per SM
 
 constexpr int kThreads = 256;     // data-term / stencil kernels
 constexpr int kTileX = 32, kTileY = 32;

@@ -745,15 +745,13 @@ static cudaError_t prep() {
 }
 
 template <typename T>
-int ic_max_blocks_per_sm() {
+int ic_max_blocks_per_sm(bool bwd) {
     if (prep<T>() != cudaSuccess) return 0;
-    int a = 0, b = 0;
-    const int nt = kThreadsIC;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_ic_fwd<T>, nt, FwdSmem<T>::bytes) != cudaSuccess)
-        return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ic_bwd<T>, 32 * kTZ, BwdSmem<T>::bytes) != cudaSuccess)
-        return 0;
-    return a < b ? a : b;
+    int n = 0;
+    const cudaError_t e =
+        bwd ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ic_bwd<T>, 32 * kTZ, BwdSmem<T>::bytes)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ic_fwd<T>, kThreadsIC, FwdSmem<T>::bytes);
+    return e == cudaSuccess ? n : 0;
 }
 
 static PivScal piv_scal(double beta) {
@@ -787,7 +785,7 @@ cudaError_t launch_ic_bwd(const IcArgs& a, int grid, cudaStream_t s) {
     template cudaError_t launch_ic_bwd<T>(const IcArgs&, int, cudaStream_t);  \
     template int ic_tz<T>();                                                  \
     template size_t ic_face_bytes_per_tile<T>();                              \
-    template int ic_max_blocks_per_sm<T>();
+    template int ic_max_blocks_per_sm<T>(bool);
 FM_INST(float)
 FM_INST(double)
 
