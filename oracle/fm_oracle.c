@@ -27,6 +27,10 @@
  *   Eq. 9  H = diag(d) + beta C'C over the mask voxels.
  *   Eq. 12 IC(0): a generic incomplete Cholesky on H's nonzero pattern, textbook
  *          right-looking k,i,j loop, natural (x fastest, then y, then z) order.
+ *   Sec. III-B  IC with a drop tolerance (the paper's L_t): the same factorisation with
+ *          fill-in allowed, where every off-diagonal factor entry smaller in magnitude
+ *          than tau = droptol * H_max (H_max: the largest |H_jk|, recomputed for every
+ *          outer iteration) is set to zero; generic left-looking column code (orc_ict).
  *   Eq. 6  w0_j = angle(conj(sum_c conj(s_c) y_c1) * sum_d conj(s_d) y_d2) / (t_2 - t_1).
  *   Algorithm box + Eq. 13-16: preconditioned Polak-Ribiere NCG, z = -p + mu z with
  *          mu^0 = 0, mu^i = (g^i - g^{i-1})'p^i / ((g^{i-1})'p^{i-1}); monotonic line
@@ -58,6 +62,7 @@ typedef struct {
     double *rabs, *rang; /* [nm][T] modulus and angle of r_cdmnj */
     double *dt;          /* [T] t_m - t_n of each tuple */
     int curv_mode;       /* 0: literal Eq. 10 sum; 1: coil-combined pair weights (labelled variant) */
+    double droptol;      /* drop tolerance of the thresholded IC, relative to H_max (default 1e-3) */
     int has_gam;         /* 0: Gamma_mn = 1/L; 1: gam holds a complex L x L Gamma */
     double gam[2 * ORC_MAXL * ORC_MAXL];
 } orc_t;
@@ -155,6 +160,7 @@ int orc_create(orc_t **out, int nx, int ny, int nz, int nc, int L, const double 
     h->nx = nx; h->ny = ny; h->nz = nz; h->nc = nc; h->L = L;
     h->nv = (long)nx * ny * nz;
     h->beta = beta;
+    h->droptol = 1e-3;
     for (int l = 0; l < L; ++l) h->te[l] = te[l];
     h->T = (long)nc * nc * L * L;
     h->mask = (unsigned char *)malloc(h->nv);
@@ -645,11 +651,164 @@ int orc_precondition(const orc_t *h, const double *d, const double *g, double *p
 }
 
 /* ---------------------------------------------------------------------------------
+ * IC with a drop tolerance (Sec. III-B: the paper's L_t and its NCG-MLS-IC).  Incomplete
+ * Cholesky of H = diag(d) + beta C'C over the mask voxels in natural order, computed
+ * column by column (left-looking): column j of L is H(j:, j) minus L(j:, k) L_jk summed
+ * over the earlier columns k with L_jk != 0, divided by L_jj = sqrt of its diagonal
+ * entry.  Every off-diagonal entry -- an entry of H or fill-in -- whose magnitude is
+ * below tau is set to zero as soon as it is computed, so later columns use the dropped
+ * factor; the diagonal is never dropped.  tau = 0 gives the complete Cholesky factor.
+ * On success *colptr, *rowidx, *val (L in compressed-column form, diagonal first, rows
+ * ascending) and *umap (voxel of each unknown) are malloc'ed: release them with orc_free.
+ * ------------------------------------------------------------------------------- */
+void orc_free(void *p) { free(p); }
+
+static int cmp_long(const void *a, const void *b) {
+    long x = *(const long *)a, y = *(const long *)b;
+    return (x > y) - (x < y);
+}
+
+int orc_ict(int nx, int ny, int nz, const unsigned char *mask, const double *d, double beta, double tau,
+            long **colptr_out, long **rowidx_out, double **val_out, long **umap_out, long *n_out,
+            long *nnz_out) {
+    long nv = (long)nx * ny * nz, nxy = (long)nx * ny;
+    long *uidx = (long *)malloc(sizeof(long) * nv), *umap = (long *)malloc(sizeof(long) * nv);
+    long n = 0;
+    if (!uidx || !umap) { free(uidx); free(umap); return ORC_ERR_OOM; }
+    for (long j = 0; j < nv; ++j) {
+        if (mask == NULL || mask[j]) { uidx[j] = n; umap[n++] = j; } else { uidx[j] = -1; }
+    }
+    long cap = 8 * n + 16, nnz = 0;
+    long *colptr = (long *)malloc(sizeof(long) * (n + 1));
+    long *rowidx = (long *)malloc(sizeof(long) * cap);
+    double *val = (double *)malloc(sizeof(double) * cap);
+    /* row lists: for every row i, its entries L_ik (k < i) in increasing k, threaded
+       through the positions p of the column storage (nextp[p]; colof[p] = k) */
+    long *nextp = (long *)malloc(sizeof(long) * cap), *colof = (long *)malloc(sizeof(long) * cap);
+    long *rhead = (long *)malloc(sizeof(long) * (n ? n : 1)), *rtail = (long *)malloc(sizeof(long) * (n ? n : 1));
+    double *w = (double *)calloc(n ? n : 1, sizeof(double));
+    unsigned char *mark = (unsigned char *)calloc(n ? n : 1, 1);
+    long *pat = (long *)malloc(sizeof(long) * (n ? n : 1));
+    int st = ORC_OK;
+    if (!colptr || !rowidx || !val || !nextp || !colof || !rhead || !rtail || !w || !mark || !pat) {
+        st = ORC_ERR_OOM;
+        goto fail;
+    }
+    for (long i = 0; i < n; ++i) rhead[i] = rtail[i] = -1;
+    for (long j = 0; j < n; ++j) {
+        long vj = umap[j];
+        colptr[j] = nnz; /* also closes column j - 1, whose rows the loop below scans */
+        long x = vj % nx, y = (vj / nx) % ny, z = vj / nxy;
+        long nb[6] = {x > 0 ? vj - 1 : -1, x + 1 < nx ? vj + 1 : -1, y > 0 ? vj - nx : -1,
+                      y + 1 < ny ? vj + nx : -1, z > 0 ? vj - nxy : -1, z + 1 < nz ? vj + nxy : -1};
+        int cnt = 0;
+        long np = 0;
+        for (int q = 0; q < 6; ++q) if (nb[q] >= 0 && uidx[nb[q]] >= 0) ++cnt;
+        /* scatter H(j:, j) */
+        w[j] = d[vj] + beta * cnt;
+        mark[j] = 1;
+        pat[np++] = j;
+        for (int q = 0; q < 6; ++q) {
+            long u = nb[q] >= 0 ? uidx[nb[q]] : -1;
+            if (u > j) { w[u] = -beta; mark[u] = 1; pat[np++] = u; }
+        }
+        /* subtract L(j:, k) L_jk for every earlier column k with L_jk kept */
+        for (long pj = rhead[j]; pj >= 0; pj = nextp[pj]) {
+            long k = colof[pj];
+            double ljk = val[pj];
+            for (long p = pj; p < colptr[k + 1]; ++p) { /* rows >= j of column k */
+                long i = rowidx[p];
+                if (!mark[i]) { mark[i] = 1; w[i] = 0.0; pat[np++] = i; }
+                w[i] -= val[p] * ljk;
+            }
+        }
+        if (!(w[j] > 0.0)) { st = ORC_ERR_NOT_PD; goto fail; }
+        double ljj = sqrt(w[j]);
+        if (np > 2) qsort(pat + 1, (size_t)(np - 1), sizeof(long), cmp_long);
+        if (nnz + np > cap) {
+            long nc = 2 * cap + np;
+            long *r2 = (long *)realloc(rowidx, sizeof(long) * nc);
+            if (r2) rowidx = r2;
+            double *v2 = (double *)realloc(val, sizeof(double) * nc);
+            if (v2) val = v2;
+            long *n2 = (long *)realloc(nextp, sizeof(long) * nc);
+            if (n2) nextp = n2;
+            long *c2 = (long *)realloc(colof, sizeof(long) * nc);
+            if (c2) colof = c2;
+            if (!r2 || !v2 || !n2 || !c2) { st = ORC_ERR_OOM; goto fail; }
+            cap = nc;
+        }
+        rowidx[nnz] = j;
+        val[nnz] = ljj;
+        ++nnz;
+        for (long q = 1; q < np; ++q) {
+            long i = pat[q];
+            double c = w[i] / ljj;
+            if (fabs(c) >= tau) { /* kept: append to row i's list */
+                rowidx[nnz] = i;
+                val[nnz] = c;
+                colof[nnz] = j;
+                nextp[nnz] = -1;
+                if (rtail[i] >= 0) nextp[rtail[i]] = nnz; else rhead[i] = nnz;
+                rtail[i] = nnz;
+                ++nnz;
+            }
+        }
+        for (long q = 0; q < np; ++q) { mark[pat[q]] = 0; w[pat[q]] = 0.0; }
+    }
+    colptr[n] = nnz;
+    free(uidx); free(nextp); free(colof); free(rhead); free(rtail); free(w); free(mark); free(pat);
+    *colptr_out = colptr; *rowidx_out = rowidx; *val_out = val; *umap_out = umap;
+    *n_out = n; *nnz_out = nnz;
+    return ORC_OK;
+fail:
+    free(uidx); free(umap); free(colptr); free(rowidx); free(val); free(nextp); free(colof);
+    free(rhead); free(rtail); free(w); free(mark); free(pat);
+    return st;
+}
+
+/* H_max of Sec. III-B: the largest |H_jk| of H = diag(d) + beta C'C over the mask voxels */
+double orc_hmax(const orc_t *h, const double *d) {
+    double m = 0.0;
+    for (long j = 0; j < h->nv; ++j) {
+        if (!h->mask[j]) continue;
+        int cnt = 0;
+        for (int ax = 0; ax < 3; ++ax) cnt += (fwd_nbr(h, j, ax) >= 0) + (bwd_nbr(h, j, ax) >= 0);
+        double hjj = fabs(d[j] + h->beta * cnt);
+        if (hjj > m) m = hjj;
+        if (cnt > 0 && fabs(h->beta) > m) m = fabs(h->beta);
+    }
+    return m;
+}
+
+void orc_set_droptol(orc_t *h, double droptol) { h->droptol = droptol; }
+
+/* p = (L L')^{-1} g with the drop-tolerance factor of H(w) = diag(d) + beta C'C, absolute
+ * tolerance tau; voxel-indexed arrays */
+int orc_precondition_ict(const orc_t *h, const double *d, const double *g, double *p, double tau) {
+    long *colptr = NULL, *rowidx = NULL, *umap = NULL, n = 0, nnz = 0;
+    double *val = NULL;
+    int st = orc_ict(h->nx, h->ny, h->nz, h->mask, d, h->beta, tau, &colptr, &rowidx, &val, &umap, &n, &nnz);
+    if (st != ORC_OK) return st;
+    double *gb = (double *)malloc(sizeof(double) * (n ? n : 1)), *pb = (double *)malloc(sizeof(double) * (n ? n : 1));
+    if (!gb || !pb) {
+        st = ORC_ERR_OOM;
+    } else {
+        for (long u = 0; u < n; ++u) gb[u] = g[umap[u]];
+        orc_ic0_solve(n, colptr, rowidx, val, gb, pb);
+        for (long j = 0; j < h->nv; ++j) p[j] = 0.0;
+        for (long u = 0; u < n; ++u) p[umap[u]] = pb[u];
+    }
+    free(gb); free(pb); free(colptr); free(rowidx); free(val); free(umap);
+    return st;
+}
+
+/* ---------------------------------------------------------------------------------
  * Preconditioned NCG with the monotonic line search (Algorithm box, Eq. 13-16).
  * w: [nv] in/out (read as the start point unless init != 0, which applies Eq. 6).
  * cost_hist [niter+1], alpha_hist [niter], mu_hist [niter], inner_cost [niter*nls]
  * (Psi after each inner step) may be NULL.  precond: 0 = IC(0), 1 = diagonal of H,
- * 2 = none, 3 = red-black IC(0).
+ * 2 = none, 3 = red-black IC(0), 4 = IC with the drop tolerance droptol * H_max.
  * ------------------------------------------------------------------------------- */
 int orc_solve(const orc_t *h, double *w, int init, int niter, int nls, int precond, double *cost_hist,
               double *alpha_hist, double *mu_hist, double *inner_cost) {
@@ -669,6 +828,9 @@ int orc_solve(const orc_t *h, double *w, int init, int niter, int nls, int preco
         orc_curv(h, w, d);
         if (precond == 0 || precond == 3) {
             st = orc_precondition_ordered(h, d, g, p, precond == 3 ? 1 : 0);
+            if (st != ORC_OK) goto done;
+        } else if (precond == 4) { /* tolerance H_max^i * droptol, this iteration's H */
+            st = orc_precondition_ict(h, d, g, p, h->droptol * orc_hmax(h, d));
             if (st != ORC_OK) goto done;
         } else {
             for (long j = 0; j < nv; ++j) {

@@ -89,6 +89,19 @@ def _lib():
         lib.orc_ic0_ordered.restype = C.c_int
         lib.orc_precondition_ordered.argtypes = [vp, _dp, _dp, _dp, C.c_int]
         lib.orc_precondition_ordered.restype = C.c_int
+        lpp = C.POINTER(C.POINTER(C.c_long))
+        dpp = C.POINTER(C.POINTER(C.c_double))
+        lib.orc_ict.argtypes = [C.c_int, C.c_int, C.c_int, vp, _dp, C.c_double, C.c_double, lpp, lpp, dpp, lpp,
+                                C.POINTER(C.c_long), C.POINTER(C.c_long)]
+        lib.orc_ict.restype = C.c_int
+        lib.orc_free.argtypes = [vp]
+        lib.orc_free.restype = None
+        lib.orc_hmax.argtypes = [vp, _dp]
+        lib.orc_hmax.restype = C.c_double
+        lib.orc_set_droptol.argtypes = [vp, C.c_double]
+        lib.orc_set_droptol.restype = None
+        lib.orc_precondition_ict.argtypes = [vp, _dp, _dp, _dp, C.c_double]
+        lib.orc_precondition_ict.restype = C.c_int
         lib.orc_voxel.argtypes = [C.c_int, C.c_int, _dp, _dp, vp, C.c_double, _dp]
         lib.orc_voxel.restype = C.c_int
         lib.orc_voxel_r.argtypes = [C.c_int, C.c_int, _dp, vp, _dp, _dp]
@@ -307,6 +320,23 @@ class Oracle:
             raise RuntimeError(f"orc_precondition failed: {st}")
         return p.reshape(self.shape)
 
+    def precondition_ict(self, d, g, tau):
+        """(L L')^{-1} g with the drop-tolerance IC factor (absolute tolerance tau) of
+        diag(d) + beta C'C (Sec. III-B, L_t)."""
+        p = np.zeros(int(np.prod(self.shape)), np.float64)
+        st = self._lib.orc_precondition_ict(self._h, self._w(d), self._w(g), p, float(tau))
+        if st != ORC_OK:
+            raise RuntimeError(f"orc_precondition_ict failed: {st}")
+        return p.reshape(self.shape)
+
+    def hmax(self, d):
+        """H_max of Sec. III-B: the largest |H_jk| of diag(d) + beta C'C on the mask."""
+        return float(self._lib.orc_hmax(self._h, self._w(d)))
+
+    def set_droptol(self, droptol):
+        """Drop tolerance of solve(precond=4), relative to each iteration's H_max."""
+        self._lib.orc_set_droptol(self._h, float(droptol))
+
     def solve(self, w0=None, niter=10, nls=5, precond=0, inner=False):
         """Run the NCG-MLS solve; returns dict(w, cost, alpha, mu[, inner])."""
         w = np.zeros(int(np.prod(self.shape)), np.float64) if w0 is None else self._w(w0).copy()
@@ -358,6 +388,32 @@ def ic0_factor(shape, mask, d, beta, order=0):
         raise RuntimeError(f"orc_ic0 failed: {st}")
     n, nnz = n.value, nnz.value
     return colptr[: n + 1].copy(), rowidx[:nnz].copy(), val[:nnz].copy(), umap[:n].copy()
+
+
+def ict_factor(shape, mask, d, beta, tau):
+    """Generic drop-tolerance IC of H = diag(d) + beta C'C on the mask voxels, natural
+    order, absolute tolerance tau (Sec. III-B, L_t).  Same return form as ic0_factor."""
+    lib = _lib()
+    nz, ny, nx = shape
+    d = np.ascontiguousarray(d, dtype=np.float64).reshape(-1)
+    m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+    cp, ri, um = C.POINTER(C.c_long)(), C.POINTER(C.c_long)(), C.POINTER(C.c_long)()
+    va = C.POINTER(C.c_double)()
+    n, nnz = C.c_long(), C.c_long()
+    st = lib.orc_ict(nx, ny, nz, _ptr(m), d, float(beta), float(tau), C.byref(cp), C.byref(ri), C.byref(va),
+                     C.byref(um), C.byref(n), C.byref(nnz))
+    if st != ORC_OK:
+        raise RuntimeError(f"orc_ict failed: {st}")
+    n, nnz = n.value, nnz.value
+    try:
+        out = (np.ctypeslib.as_array(cp, shape=(n + 1,)).astype(np.int64).copy(),
+               np.ctypeslib.as_array(ri, shape=(max(nnz, 1),))[:nnz].astype(np.int64).copy(),
+               np.ctypeslib.as_array(va, shape=(max(nnz, 1),))[:nnz].copy(),
+               np.ctypeslib.as_array(um, shape=(max(n, 1),))[:n].astype(np.int64).copy())
+    finally:
+        for ptr in (cp, ri, va, um):
+            lib.orc_free(C.cast(ptr, C.c_void_p))
+    return out
 
 
 def ic0_solve(colptr, rowidx, val, b):
