@@ -58,6 +58,8 @@ extern "C" {
 #define FM_ERR_NONFINITE (-6) /* a global reduction (cost, dot, step) was not finite */
 #define FM_ERR_OOM (-7)       /* device or host allocation failed */
 #define FM_ERR_SIZE (-8)      /* problem larger than a fixed-size buffer of the call allows */
+#define FM_ERR_FILL (-9)      /* FM_PC_ICT: the drop tolerance keeps an entry outside the
+                                 held pattern (see FM_PC_ICT) */
 
 #define FM_FP64 0
 #define FM_FP32 1
@@ -67,6 +69,15 @@ extern "C" {
 #define FM_PC_NONE 2 /* identity: the paper's NCG-MLS comparison (Sec. IV) */
 #define FM_PC_RB 3   /* IC(0) in red-black order (x + y + z even first): a labelled multicolour
                         variant, two parallel stencil passes instead of the wavefronts */
+#define FM_PC_ICT 4  /* IC with a drop tolerance (Sec. III-B, the paper's L_t, and its
+                        NCG-MLS-IC): natural order, every off-diagonal factor entry (fill-in
+                        included) smaller in magnitude than tau = droptol * H_max is set to
+                        zero, H_max being the largest |H_jk| of each outer iteration's H.  The
+                        factor is held on IC(0)'s pattern plus the level-1 fill offsets
+                        (x+1, y-1, z), (x+1, y, z-1), (x, y+1, z-1); it is exact whenever the
+                        tolerance keeps nothing outside that pattern, and a factorisation that
+                        would is reported as FM_ERR_FILL at the next synchronising call.  The
+                        sweeps run level by level (x + 2y + 3z), slower than IC(0)'s. */
 
 #define FM_CURV_LITERAL 0  /* d_j summed over every (c, d, m, n) term (Eq. 10) */
 #define FM_CURV_COMBINED 1 /* d_j from the coil-combined pair weights (labelled variant) */
@@ -79,11 +90,12 @@ typedef struct fm_ctx fm_ctx; /* opaque, owned by the library */
 typedef struct fm_opts {
     int precision;       /* FM_FP32 (default) or FM_FP64 */
     int nls;             /* monotonic line-search steps per outer iteration (N_i), >= 1; default 5 */
-    int precond;         /* FM_PC_IC0 (default) | FM_PC_DIAG | FM_PC_NONE */
+    int precond;         /* FM_PC_IC0 (default) | FM_PC_DIAG | FM_PC_NONE | FM_PC_RB | FM_PC_ICT */
     int curvature;       /* FM_CURV_LITERAL (default) | FM_CURV_COMBINED */
     long long spin_limit;/* polls (at most about 0.3 us apart) before a device-side wait gives
                             up with FM_ERR_TIMEOUT; default 1<<21 (about half a second) */
     int use_graph;       /* 1: replay the outer iteration as a captured CUDA graph (default 1) */
+    double droptol;      /* FM_PC_ICT only: tolerance relative to H_max, finite, >= 0; default 1e-3 */
 } fm_opts;
 
 /* Fill *opts with the defaults listed above.  opts must not be NULL. */
@@ -142,11 +154,13 @@ FM_API int fm_cost_grad(fm_ctx *ctx, const void *omega, double *cost, void *grad
  * Form H = diag(d(omega)) + beta C'C (Eq. 9) and its IC(0) factor (Eq. 12), natural
  * x-fastest order (red-black order when fm_opts.precond is FM_PC_RB), zero fill-in:
  * L = (Pi + E) Pi^{-1/2} with E the strict lower triangle of H in that order and pivots
- * pi_j = H_jj - sum_k E_jk^2 / pi_k.  The factor is kept
- * in the context for fm_ic_apply.  inv_pivot (device [nz][ny][nx] of the voxel type,
- * nullable) receives 1/pi_j (0 outside the mask).  Pivots are computed in double.
+ * pi_j = H_jj - sum_k E_jk^2 / pi_k.  With FM_PC_ICT it is instead the drop-tolerance
+ * factor of FM_PC_ICT (tau = droptol * H_max(omega)), with pi_j = L_jj^2.  The factor
+ * is kept in the context for fm_ic_apply.  inv_pivot (device [nz][ny][nx] of the voxel
+ * type, nullable) receives 1/pi_j (0 outside the mask).  Pivots are computed in double.
  * Errors: FM_ERR_STATE, FM_ERR_NOT_PD (some pivot <= 0; reported at the next
- * synchronising call), FM_ERR_TIMEOUT.
+ * synchronising call), FM_ERR_TIMEOUT, FM_ERR_FILL (FM_PC_ICT only; also reported at
+ * the next synchronising call).
  */
 FM_API int fm_ic_factor(fm_ctx *ctx, const void *omega, void *inv_pivot);
 

@@ -6,9 +6,9 @@ the C ABI of include/fm.h; :class:`FieldMap` is a thin ctypes binding of that AB
 """
 from .fm import (FieldMap, FieldMapBatch, FmError, FmOpts, load_library, lib_path, EXPORTS, FM_OK, FM_ERR_ARG,
                  FM_ERR_STATE, FM_ERR_CUDA, FM_ERR_NOT_PD, FM_ERR_TIMEOUT, FM_ERR_NONFINITE, FM_ERR_OOM,
-                 FM_ERR_SIZE)
+                 FM_ERR_SIZE, FM_ERR_FILL)
 from .autograd import field_map_cost, field_map_solve
 
 __all__ = ["FieldMap", "FieldMapBatch", "FmError", "FmOpts", "load_library", "lib_path", "EXPORTS", "FM_OK", "FM_ERR_ARG",
            "FM_ERR_STATE", "FM_ERR_CUDA", "FM_ERR_NOT_PD", "FM_ERR_TIMEOUT", "FM_ERR_NONFINITE", "FM_ERR_OOM",
-           "FM_ERR_SIZE", "field_map_cost", "field_map_solve"]
+           "FM_ERR_SIZE", "FM_ERR_FILL", "field_map_cost", "field_map_solve"]

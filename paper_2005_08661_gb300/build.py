@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["fm_api.cu", "k_setup.cu", "k_data.cu", "k_ic.cu", "k_adj.cu", "k_wf.cu", "k_rb.cu", "fm_noalloc.cu"]
+SOURCES = ["fm_api.cu", "k_setup.cu", "k_data.cu", "k_ic.cu", "k_adj.cu", "k_wf.cu", "k_rb.cu", "k_ict.cu", "fm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

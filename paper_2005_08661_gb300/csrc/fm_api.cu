@@ -49,7 +49,9 @@ struct fm_ctx {
     int ntx = 0, nty = 0, ntz = 0, ntiles = 0;
     int ic_wxy = 2, ic_wz = 1;  // forward tile claim order weights
     int nsm = 0, grid_data = 0, grid_ls = 0, grid_ic = 0, grid_icb = 0;  // grid_icb: backward IC sweep
-    int base_data = 0, base_ls = 0, base_ic = 0, base_icb = 0;  // grids chosen at creation (batch autotuning scales them)
+    int base_data = 0, base_ls = 0, base_ic = 0, base_icb = 0;
+    int grid_ict = 0, base_ict = 0;  // drop-tolerance IC sweeps (persistent, level barriers)
+    double* ict_L = nullptr;         // drop-tolerance IC factor planes [kIctPlanes][nv]  // grids chosen at creation (batch autotuning scales them)
     int last_niter = 0;
     cudaGraphExec_t gexec = nullptr;
     cudaGraphExec_t cg_gexec = nullptr;  // adjoint CG iterations (tolerance and limit are arguments)
@@ -107,7 +109,7 @@ void free_all(fm_ctx* c) {
                 if (e) cudaEventDestroy(e);
     void* bufs[] = {c->pairs, c->coils, c->w0, c->nb, c->vlist, c->chunk_off, c->w[0], c->w[1], c->z[0], c->z[1], c->g[0],
                     c->g[1], c->d, c->p, c->v, c->ip, c->scal, c->partials, c->face, c->tile_part, c->rho,
-                    c->hist_cost, c->hist_alpha, c->hist_mu, c->istate, c->icint, c->order};
+                    c->hist_cost, c->hist_alpha, c->hist_mu, c->istate, c->icint, c->order, c->ict_L};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -124,6 +126,7 @@ int check_dev(fm_ctx* c) {
         const char* what = e == FM_ERR_NOT_PD ? "IC(0) pivot <= 0 (H not positive definite on the mask)"
                          : e == FM_ERR_TIMEOUT ? "device-side wait exceeded spin_limit"
                          : e == FM_ERR_NONFINITE ? "non-finite global reduction"
+                         : e == FM_ERR_FILL ? "drop tolerance keeps fill-in outside the held pattern"
                          : "device error";
         return fail(c, e, what);
     }
@@ -183,8 +186,8 @@ cudaError_t run_grad(fm_ctx* c, const void* w_in, const void* zdir, void* w_out,
 
 // forward (pivots when d != null) + backward substitution: p = (L L')^{-1} g
 template <typename T>
-cudaError_t run_ic(fm_ctx* c, const void* d, const void* g, void* p, const void* gdot, const void* gpdot,
-                   int slot = -1) {
+cudaError_t run_ic0(fm_ctx* c, const void* d, const void* g, void* p, const void* gdot, const void* gpdot,
+                    int slot) {
     const size_t nint = 4 + 2 * (size_t)c->ntiles;
     cudaError_t e = cudaMemsetAsync(c->icint, 0, nint * sizeof(int), c->stream);
     if (e != cudaSuccess) return e;
@@ -226,6 +229,63 @@ cudaError_t run_ic(fm_ctx* c, const void* d, const void* g, void* p, const void*
     return e;
 }
 
+// The same with the drop-tolerance IC (k_ict.cu): tau from H_max, factor + forward sweep,
+// the exactness check, back sweep; or, with d null, the two sweeps on the stored factor.
+template <typename T>
+cudaError_t run_ict(fm_ctx* c, const void* d, const void* g, void* p, const void* gdot, const void* gpdot,
+                    int slot) {
+    cudaError_t e = cudaSuccess;
+    IctArgs a{};
+    a.geo = Geo{c->nx, c->ny, c->nz, c->nv};
+    a.beta = c->beta;
+    a.nb = c->nb;
+    a.vlist = c->vlist;
+    a.d = d;
+    a.g = g;
+    a.L = c->ict_L;
+    a.ip_out = d ? c->ip : nullptr;
+    a.p = p;
+    a.gdot = gdot;
+    a.gpdot = gpdot;
+    a.scal = c->scal;
+    a.partials = c->partials;
+    a.istate = c->istate;
+    a.spin_limit = c->o.spin_limit;
+    const bool prof = slot >= 0 && c->profiling;
+    if (d) {
+        DataArgs t = base_args(c);
+        t.d = const_cast<void*>(d);  // read only here
+        e = launch_ict_tau<T>(t, c->o.droptol, c->grid_data, c->stream);
+        if (e != cudaSuccess) return e;
+    }
+    if (prof) cudaEventRecordWithFlags(c->ev[slot][FM_K_IC_FWD][0], c->stream, cudaEventRecordExternal);
+    e = launch_ict_fwd<T>(a, c->grid_ict, c->stream);
+    if (prof) {
+        cudaEventRecordWithFlags(c->ev[slot][FM_K_IC_FWD][1], c->stream, cudaEventRecordExternal);
+        c->ev_rec[slot][FM_K_IC_FWD] = true;
+    }
+    if (e != cudaSuccess) return e;
+    if (d) {  // exact only while nothing outside the held pattern survives: FM_ERR_FILL otherwise
+        e = launch_ict_check<T>(a, c->grid_data, c->stream);
+        if (e != cudaSuccess) return e;
+    }
+    if (prof) cudaEventRecordWithFlags(c->ev[slot][FM_K_IC_BWD][0], c->stream, cudaEventRecordExternal);
+    e = launch_ict_bwd<T>(a, c->grid_ict, c->stream);
+    if (prof) {
+        cudaEventRecordWithFlags(c->ev[slot][FM_K_IC_BWD][1], c->stream, cudaEventRecordExternal);
+        c->ev_rec[slot][FM_K_IC_BWD] = true;
+    }
+    return e;
+}
+
+// p = (L L')^{-1} g with the context's incomplete factor (recomputed from d when non-null)
+template <typename T>
+cudaError_t run_ic(fm_ctx* c, const void* d, const void* g, void* p, const void* gdot, const void* gpdot,
+                   int slot = -1) {
+    if (c->o.precond == FM_PC_ICT) return run_ict<T>(c, d, g, p, gdot, gpdot, slot);
+    return run_ic0<T>(c, d, g, p, gdot, gpdot, slot);
+}
+
 // Brackets one kernel class of iteration slot `cur` with events when profiling.
 struct Mark {
     fm_ctx* c;
@@ -251,7 +311,7 @@ cudaError_t iteration(fm_ctx* c, int cur) {
         e = run_grad<T>(c, c->w[cur], c->z[cur], c->w[nxt], c->g[cur], c->d, c->hist_cost);
     }
     if (e != cudaSuccess) return e;
-    if (c->o.precond == FM_PC_IC0) {
+    if (c->o.precond == FM_PC_IC0 || c->o.precond == FM_PC_ICT) {
         e = run_ic<T>(c, c->d, c->g[cur], c->p, c->g[cur], c->g[nxt], cur);
     } else if (c->o.precond == FM_PC_RB) {
         DataArgs a = base_args(c);
@@ -576,8 +636,10 @@ bool set_ls_grid(fm_ctx* c) {
 
 bool valid_opts(const fm_opts& o) {
     return (o.precision == FM_FP32 || o.precision == FM_FP64) && o.nls >= 1 && o.nls <= 1000 &&
-           (o.precond == FM_PC_IC0 || o.precond == FM_PC_DIAG || o.precond == FM_PC_NONE || o.precond == FM_PC_RB) &&
-           (o.curvature == FM_CURV_LITERAL || o.curvature == FM_CURV_COMBINED) && o.spin_limit >= 1;
+           (o.precond == FM_PC_IC0 || o.precond == FM_PC_DIAG || o.precond == FM_PC_NONE || o.precond == FM_PC_RB ||
+            o.precond == FM_PC_ICT) &&
+           (o.curvature == FM_CURV_LITERAL || o.curvature == FM_CURV_COMBINED) && o.spin_limit >= 1 &&
+           std::isfinite(o.droptol) && o.droptol >= 0.0;
 }
 
 }  // namespace
@@ -592,6 +654,7 @@ void fm_default_opts(fm_opts* o) {
     o->curvature = FM_CURV_LITERAL;
     o->spin_limit = 1LL << 21;
     o->use_graph = 1;
+    o->droptol = 1e-3;
 }
 
 const char* fm_strerror(int s) {
@@ -605,6 +668,7 @@ const char* fm_strerror(int s) {
         case FM_ERR_NONFINITE: return "non-finite reduction";
         case FM_ERR_OOM: return "out of memory";
         case FM_ERR_SIZE: return "problem exceeds a fixed-size buffer of the call";
+        case FM_ERR_FILL: return "drop tolerance keeps fill-in beyond level 1 (FM_PC_ICT's held pattern)";
         default: return "unknown status";
     }
 }
@@ -650,19 +714,29 @@ int fm_create(fm_ctx** out, int nx, int ny, int nz, int ncoil, int necho, const 
     c->ntz = (nz + tz - 1) / tz;
     c->ntiles = c->ntx * c->nty * c->ntz;
     {
-        // the two sweeps claim tiles from their own tickets, so each takes as many
-        // resident blocks as its own footprint allows
+        // the two sweeps claim tiles from their own tickets, so each sizes its own grid: the
+        // forward sweep by its footprint (1 block/SM), the back substitution by its footprint
+        // capped at 2 blocks/SM -- a third block per SM only adds tiles waiting on their
+        // successors' flags (256x256x128 volume: 0.328 / 0.284 / 0.293 ms per sweep at 1 / 2 / 3)
         const bool f64 = o.precision == FM_FP64;
         const int occ_f = f64 ? ic_max_blocks_per_sm<double>(false) : ic_max_blocks_per_sm<float>(false);
         const int occ_b = f64 ? ic_max_blocks_per_sm<double>(true) : ic_max_blocks_per_sm<float>(true);
         if (occ_f < 1 || occ_b < 1) return bail(FM_ERR_CUDA);
         c->grid_ic = std::max(1, std::min(c->ntiles, occ_f * c->nsm));
-        c->grid_icb = std::max(1, std::min(c->ntiles, occ_b * c->nsm));
+        c->grid_icb = std::max(1, std::min(c->ntiles, std::min(occ_b, 2) * c->nsm));
     }
     c->base_data = c->grid_data;
     c->base_ls = c->grid_ls;
     c->base_ic = c->grid_ic;
     c->base_icb = c->grid_icb;
+    if (o.precond == FM_PC_ICT) {
+        // one thread per (y, z) column of the level sweep, every block resident (grid barrier)
+        const int occ = o.precision == FM_FP64 ? ict_max_blocks_per_sm<double>() : ict_max_blocks_per_sm<float>();
+        if (occ < 1) return bail(FM_ERR_CUDA);
+        const long long cols = (long long)ny * nz;
+        c->grid_ict = (int)std::max(1LL, std::min<long long>((cols + kThreads - 1) / kThreads, (long long)occ * c->nsm));
+        c->base_ict = c->grid_ict;
+    }
     const size_t vb = (size_t)c->nv * c->ts;
     const int P = necho * (necho - 1) / 2;
     bool ok = true;
@@ -684,6 +758,7 @@ int fm_create(fm_ctx** out, int nx, int ny, int nz, int ncoil, int necho, const 
     A(&c->istate, I_NISTATE * sizeof(int));
     A(&c->icint, (4 + 2 * (size_t)c->ntiles) * sizeof(int));
     A(&c->order, 2 * (size_t)c->ntiles * sizeof(int));  // forward order, then the back substitution's
+    if (o.precond == FM_PC_ICT) A(&c->ict_L, (size_t)kIctPlanes * c->nv * sizeof(double));
     if (!ok) { cudaGetLastError(); return bail(FM_ERR_OOM); }
 #ifndef FM_IC_WXY
 #define FM_IC_WXY 2
@@ -798,6 +873,9 @@ int fm_set_data(fm_ctx* c, const void* y, const void* smap, const double* te, co
     cudaError_t e = c->o.precision == FM_FP64 ? launch_setup<double>(a, c->stream)
                                               : launch_setup<float>(a, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "setup kernel");
+    // rows outside the new mask must read as empty in the drop-tolerance factor
+    if (c->ict_L)
+        FM_CK(cudaMemsetAsync(c->ict_L, 0, (size_t)kIctPlanes * c->nv * sizeof(double), c->stream), "clear factor");
     c->have_data = true;
     c->have_factor = false;
     return FM_OK;
@@ -1090,6 +1168,7 @@ void batch_apply_fraction(fm_batch* b) {
         c->grid_ls = std::max(1, (int)std::lround(c->base_ls * b->fraction));
         c->grid_ic = std::max(1, (int)std::lround(c->base_ic * b->fraction));
         c->grid_icb = std::max(1, (int)std::lround(c->base_icb * b->fraction));
+        if (c->base_ict) c->grid_ict = std::max(1, (int)std::lround(c->base_ict * b->fraction));
         if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
     }
     if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }

@@ -35,11 +35,16 @@ enum Scal {
     S_CG_RR,       // adjoint CG: ||r||^2 after the last update
     S_CG_BB,       // adjoint CG: ||b||^2
     S_ADJ_DOT,     // lambda' C'C w (implicit derivative with respect to beta)
+    S_ICT_TAU,     // drop-tolerance IC: this factorisation's tolerance droptol * H_max
     S_NSCAL
 };
 
 // Integer device state.
-enum IState { I_ERR = 0, I_ITER, I_DONE0, I_DONE1, I_BAR_COUNT, I_BAR_GEN, I_NMASK, I_CG_IT, I_CG_DONE, I_NISTATE };
+enum IState {
+    I_ERR = 0, I_ITER, I_DONE0, I_DONE1, I_BAR_COUNT, I_BAR_GEN, I_NMASK, I_CG_IT, I_CG_DONE,
+    I_ICT_BAD,  // drop-tolerance IC: a pivot <= 0 on the held pattern (reported after the fill check)
+    I_NISTATE
+};
 
 // Setup works on chunks of 1024 consecutive voxels (mask compaction keeps voxel order).
 constexpr int kChunk = 1024;
@@ -270,6 +275,28 @@ struct IcArgs {
     long long spin_limit;
 };
 
+// IC with a drop tolerance (k_ict.cu) on the pattern of IC(0) plus the level-1 fill offsets.
+// Factor planes, each [nv] double: L_ii, then L_{i,i+o} for the offsets o = (-1,0,0),
+// (0,-1,0), (0,0,-1), (1,-1,0), (1,0,-1), (0,1,-1), then the substitution vector.
+constexpr int kIctPlanes = 8;
+struct IctArgs {
+    Geo geo;
+    double beta;
+    const uint8_t* nb;
+    const int* vlist;
+    const void* d;         // T [nv]: factor (forward sweep), or null: apply the stored factor
+    const void* g;         // T [nv] right-hand side
+    double* L;             // [kIctPlanes][nv]
+    void* ip_out;          // T [nv] or null: 1/L_ii^2 (the pivots' inverses), factor mode
+    void* p;               // T [nv] result (back substitution)
+    const void* gdot;      // T [nv] or null: g for g'p
+    const void* gpdot;     // T [nv] or null: g_prev for g_prev'p
+    double* scal;
+    double* partials;
+    int* istate;
+    long long spin_limit;
+};
+
 // Implicit differentiation of the converged field map: true curvature, the adjoint CG on
 // H_true = diag(h) + beta C'C, and the derivatives with respect to beta and the images.
 struct AdjArgs {
@@ -330,6 +357,11 @@ template <typename T> cudaError_t launch_pwls_init(const AdjArgs& a, int grid, c
 template <typename T> cudaError_t launch_wf_sweep(const AdjArgs& a, int nsweep, double wlo, double whi, int grid,
                                                   cudaStream_t s);
 template <typename T> cudaError_t launch_wf_amp(const AdjArgs& a, int grid, cudaStream_t s);
+template <typename T> cudaError_t launch_ict_tau(const DataArgs& a, double droptol, int grid, cudaStream_t s);
+template <typename T> cudaError_t launch_ict_fwd(const IctArgs& a, int grid, cudaStream_t s);
+template <typename T> cudaError_t launch_ict_bwd(const IctArgs& a, int grid, cudaStream_t s);
+template <typename T> cudaError_t launch_ict_check(const IctArgs& a, int grid, cudaStream_t s);
+template <typename T> int ict_max_blocks_per_sm();
 template <typename T> int ic_tz();
 template <typename T> size_t ic_face_bytes_per_tile();
 template <typename T> int ic_max_blocks_per_sm(bool bwd);  // resident IC sweep blocks per SM

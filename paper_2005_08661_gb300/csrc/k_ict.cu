@@ -1,0 +1,316 @@
+// k_ict.cu -- IC with a drop tolerance (Sec. III-B: the paper's L_t and the preconditioner
+// of its NCG-MLS-IC; FM_PC_ICT).
+//
+// The paper zeroes every factor entry whose magnitude is below tau = droptol * H_max, H_max
+// being the largest |H_jk| of the outer iteration's H = diag(d) + beta C'C.  Unlike IC(0)
+// this keeps fill-in.  Eliminating an earlier neighbour k of two voxels i > j couples them:
+// in natural order the first fill lands at the three "level-1" offsets (x+1, y-1, z),
+// (x+1, y, z-1) and (x, y+1, z-1) from a row's voxel.  The kernels here hold the pattern P
+// of IC(0)'s offsets a = (-1,0,0), b = (0,-1,0), c = (0,0,-1) plus those fill offsets
+// d = (1,-1,0), e = (1,0,-1), f = (0,1,-1); row i of L has L_ii and L_{i,i+o}, o in P.
+//
+// Row i, in increasing column order c, e, f, b, d, a (each entry needs the row's earlier
+// entries and the neighbour row j = i + o):
+//   L_{i,j} = (H_ij - sum_{k < j} L_ik L_jk) / L_jj, set to 0 if |L_{i,j}| < tau,
+//   L_ii = sqrt(H_ii - sum_o L_{i,i+o}^2),
+// where the sums run over the common earlier neighbours inside P -- by offset arithmetic
+// a: (b, d), (c, e); b: (c, f); c: none; d: (b, a), (e, f); e: (c, a); f: (c, b), (e, d),
+// each pair (p1, p2) meaning L_{i,i+p1} L_{j,j+p2}.  The forward substitution L y = g is
+// fused with the factorisation; the back substitution solves L' x = y.
+//
+// Schedule.  The fill offsets d, e, f link voxels of one x + y + z hyperplane, so the IC(0)
+// wavefront does not apply.  With level t = x + 2y + 3z every offset in P points to a strictly
+// lower level (t(a) = t(d) = t(f) = -1, t(b) = t(e) = -2, t(c) = -3), so one persistent kernel
+// sweeps the levels in order -- thread <-> (y, z) column, voxel x = t - 2y - 3z -- with a
+// bounded grid barrier between levels; the back substitution sweeps them in reverse.
+//
+// Exactness.  This is the exact drop-tolerance factor as long as no entry outside P
+// survives.  With the factor on P in hand, k_ict_check forms every would-be entry just
+// outside P -- at the six offsets q = p1 - p2 (p1, p2 in P, q outside P, pointing to an
+// earlier voxel): (-1,1,-1): (c,d); (-1,2,-1): (f,d); (0,2,-1): (f,b); (1,1,-1): (e,b),
+// (f,a); (2,-1,0): (d,a); (2,0,-1): (e,a) -- and reports FM_ERR_FILL if one reaches tau.  If
+// none does, no entry outside P ever appears (by induction over the columns); otherwise the
+// first column where one does sees exactly this value, since all earlier columns agree.
+//
+// A pivot <= 0 is reported (FM_ERR_NOT_PD) by the back sweep, after the check, so that
+// FM_ERR_FILL wins when fill outside P is the cause.
+//
+// Arithmetic is double in both precision modes (the voxel type only for d, g and p): the
+// sweeps are latency-bound, not bound by the FP64 pipe.
+#include "fm_internal.h"
+
+namespace fm {
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// ------------------------------------------------------------------ tau = droptol * H_max
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_ict_tau(DataArgs a, double droptol) {
+    __shared__ double sbuf[32];
+    __shared__ bool s_last;
+    const T* d = (const T*)a.d;
+    const double beta = a.beta;
+    const long long nm = a.istate[I_NMASK];
+    double m = 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nm;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long j = a.vlist[k];
+        const int n = __popc((unsigned)(a.nb[j] >> 1) & 0x3fu);
+        m = fmax(m, fabs((double)d[j] + beta * (double)n));  // H_jj
+        if (n > 0) m = fmax(m, fabs(beta));                 // H_jk = -beta
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    m = warp_max(m);
+    if (lane == 0) sbuf[wid] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nw; ++w) m = fmax(m, sbuf[w]);
+        a.partials[blockIdx.x] = m;
+        __threadfence();
+        const unsigned prev = atomicAdd((unsigned*)(a.istate + I_DONE0), 1u);
+        s_last = prev == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double h = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) h = fmax(h, __ldcg(a.partials + i));
+    h = warp_max(h);
+    __syncthreads();
+    if (lane == 0) sbuf[wid] = h;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nw; ++w) h = fmax(h, sbuf[w]);
+        a.scal[S_ICT_TAU] = droptol * h;
+        a.istate[I_DONE0] = 0;
+        if (!isfinite(h)) set_err(a.istate, FM_ERR_NONFINITE);
+    }
+}
+
+// ------------------------------------------------------------------ the sweeps
+
+// Plane indices of the factor storage.
+enum : int { PL_D = 0, PL_A, PL_B, PL_C, PL_D1, PL_E, PL_F, PL_Y };
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_ict_fwd(IctArgs a) {
+    const int nx = a.geo.nx, ny = a.geo.ny, nz = a.geo.nz;
+    const long long nxy = (long long)nx * ny, nv = a.geo.nv;
+    double* Lp = a.L;
+    auto P = [&](int k, long long j) -> double* { return Lp + (size_t)k * nv + j; };
+    const T* d = (const T*)a.d;
+    const T* g = (const T*)a.g;
+    T* ipo = (T*)a.ip_out;
+    const bool factor = d != nullptr;
+    const double beta = a.beta;
+    const double tau = factor ? a.scal[S_ICT_TAU] : 0.0;
+    const int npair = ny * nz;
+    const int tmax = (nx - 1) + 2 * (ny - 1) + 3 * (nz - 1);
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+    bool bad = false;
+    for (int t = 0; t <= tmax; ++t) {
+        for (int pr = gtid; pr < npair; pr += nthr) {
+            const int y = pr % ny, z = pr / ny, x = t - 2 * y - 3 * z;
+            if (x < 0 || x >= nx) continue;
+            const long long i = x + (long long)nx * y + nxy * z;
+            const uint8_t b = a.nb[i];
+            if (!(b & NB_IN)) continue;
+            const long long ja = i - 1, jb = i - nx, jc = i - nxy, jd = i + 1 - nx, je = i + 1 - nxy, jf = i + nx - nxy;
+            const bool ha = b & NB_XM, hb = b & NB_YM, hc = b & NB_ZM;
+            const bool hd = x + 1 < nx && y > 0 && (a.nb[jd] & NB_IN);
+            const bool he = x + 1 < nx && z > 0 && (a.nb[je] & NB_IN);
+            const bool hf = y + 1 < ny && z > 0 && (a.nb[jf] & NB_IN);
+            double la = 0, lb = 0, lc = 0, ld = 0, le = 0, lf = 0, lii;
+            if (factor) {
+                auto keep = [&](double v) { return fabs(v) >= tau ? v : 0.0; };
+                if (hc) lc = keep(-beta / __ldcg(P(PL_D, jc)));
+                if (he) le = keep(-(lc * __ldcg(P(PL_A, je))) / __ldcg(P(PL_D, je)));
+                if (hf) lf = keep(-(lc * __ldcg(P(PL_B, jf)) + le * __ldcg(P(PL_D1, jf))) / __ldcg(P(PL_D, jf)));
+                if (hb) lb = keep((-beta - lc * __ldcg(P(PL_F, jb))) / __ldcg(P(PL_D, jb)));
+                if (hd) ld = keep(-(lb * __ldcg(P(PL_A, jd)) + le * __ldcg(P(PL_F, jd))) / __ldcg(P(PL_D, jd)));
+                if (ha)
+                    la = keep((-beta - lb * __ldcg(P(PL_D1, ja)) - lc * __ldcg(P(PL_E, ja))) / __ldcg(P(PL_D, ja)));
+                const double h = (double)d[i] + beta * (double)__popc((unsigned)(b >> 1) & 0x3fu);
+                const double s = h - (((la * la + lb * lb) + (lc * lc + ld * ld)) + (le * le + lf * lf));
+                if (!(s > 0.0)) bad = true;
+                lii = s > 0.0 ? sqrt(s) : 1.0;  // the error is reported; keep the arithmetic finite
+                *P(PL_D, i) = lii;
+                *P(PL_A, i) = la;
+                *P(PL_B, i) = lb;
+                *P(PL_C, i) = lc;
+                *P(PL_D1, i) = ld;
+                *P(PL_E, i) = le;
+                *P(PL_F, i) = lf;
+                if (ipo) ipo[i] = (T)(1.0 / (lii * lii));
+            } else {
+                lii = *P(PL_D, i);
+                la = *P(PL_A, i);
+                lb = *P(PL_B, i);
+                lc = *P(PL_C, i);
+                ld = *P(PL_D1, i);
+                le = *P(PL_E, i);
+                lf = *P(PL_F, i);
+            }
+            double acc = (double)g[i];
+            if (hc) acc -= lc * __ldcg(P(PL_Y, jc));
+            if (he) acc -= le * __ldcg(P(PL_Y, je));
+            if (hf) acc -= lf * __ldcg(P(PL_Y, jf));
+            if (hb) acc -= lb * __ldcg(P(PL_Y, jb));
+            if (hd) acc -= ld * __ldcg(P(PL_Y, jd));
+            if (ha) acc -= la * __ldcg(P(PL_Y, ja));
+            *P(PL_Y, i) = acc / lii;
+        }
+        if (t < tmax && !grid_barrier(a.istate, a.spin_limit)) return;
+    }
+    // reported by the back sweep, after k_ict_check: fill beyond the held pattern (which can
+    // itself make a pivot of the restricted factor non-positive) takes precedence
+    if (bad) atomicExch(a.istate + I_ICT_BAD, 1);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_ict_bwd(IctArgs a) {
+    __shared__ double sbuf[2 * 32];
+    const int nx = a.geo.nx, ny = a.geo.ny, nz = a.geo.nz;
+    const long long nxy = (long long)nx * ny, nv = a.geo.nv;
+    double* Lp = a.L;
+    auto P = [&](int k, long long j) -> double* { return Lp + (size_t)k * nv + j; };
+    T* p = (T*)a.p;
+    const T* gd = (const T*)a.gdot;
+    const T* gpd = (const T*)a.gpdot;
+    const int npair = ny * nz;
+    const int tmax = (nx - 1) + 2 * (ny - 1) + 3 * (nz - 1);
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+    double acc2[2] = {0.0, 0.0};
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.istate[I_ICT_BAD]) {
+        set_err(a.istate, FM_ERR_NOT_PD);
+        a.istate[I_ICT_BAD] = 0;
+    }
+    for (int t = tmax; t >= 0; --t) {
+        for (int pr = gtid; pr < npair; pr += nthr) {
+            const int y = pr % ny, z = pr / ny, x = t - 2 * y - 3 * z;
+            if (x < 0 || x >= nx) continue;
+            const long long i = x + (long long)nx * y + nxy * z;
+            const uint8_t b = a.nb[i];
+            if (!(b & NB_IN)) {
+                p[i] = T(0);
+                continue;
+            }
+            // the later rows r = i - o that hold an entry in column i: L_{r,i} = plane o of row r
+            const long long ra = i + 1, rb = i + nx, rc = i + nxy, rd = i - 1 + nx, re = i - 1 + nxy, rf = i - nx + nxy;
+            const bool ha = b & NB_XP, hb = b & NB_YP, hc = b & NB_ZP;
+            const bool hd = x > 0 && y + 1 < ny && (a.nb[rd] & NB_IN);
+            const bool he = x > 0 && z + 1 < nz && (a.nb[re] & NB_IN);
+            const bool hf = y > 0 && z + 1 < nz && (a.nb[rf] & NB_IN);
+            double s = *P(PL_Y, i);
+            if (ha) s -= __ldcg(P(PL_A, ra)) * __ldcg(P(PL_Y, ra));
+            if (hd) s -= __ldcg(P(PL_D1, rd)) * __ldcg(P(PL_Y, rd));
+            if (hf) s -= __ldcg(P(PL_F, rf)) * __ldcg(P(PL_Y, rf));
+            if (hb) s -= __ldcg(P(PL_B, rb)) * __ldcg(P(PL_Y, rb));
+            if (he) s -= __ldcg(P(PL_E, re)) * __ldcg(P(PL_Y, re));
+            if (hc) s -= __ldcg(P(PL_C, rc)) * __ldcg(P(PL_Y, rc));
+            const double xi = s / *P(PL_D, i);
+            *P(PL_Y, i) = xi;  // y_i becomes x_i: every row that still needs y_i is this one
+            p[i] = (T)xi;
+            if (gd) acc2[0] += (double)gd[i] * (double)(T)xi;
+            if (gpd) acc2[1] += (double)gpd[i] * (double)(T)xi;
+        }
+        if (t > 0 && !grid_barrier(a.istate, a.spin_limit)) return;
+    }
+    if (gd || gpd) {
+        double out[2];
+        if (last_block_reduce<2>(acc2, a.partials, (unsigned*)(a.istate + I_DONE0), out, sbuf)) {
+            if (threadIdx.x == 0) {
+                a.scal[S_GP] = out[0];
+                a.scal[S_GPREVP] = out[1];
+                if (!isfinite(out[0]) || !isfinite(out[1])) set_err(a.istate, FM_ERR_NONFINITE);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ fill beyond P
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_ict_check(IctArgs a) {
+    const int nx = a.geo.nx, ny = a.geo.ny, nz = a.geo.nz;
+    const long long nxy = (long long)nx * ny, nv = a.geo.nv;
+    const double* Lp = a.L;
+    auto P = [&](int k, long long j) -> double { return Lp[(size_t)k * nv + j]; };
+    const double tau = a.scal[S_ICT_TAU];
+    const long long nm = a.istate[I_NMASK];
+    bool fill = false;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nm;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long i = a.vlist[k];
+        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / nxy);
+        const double lc = P(PL_C, i), ld = P(PL_D1, i), le = P(PL_E, i), lf = P(PL_F, i);
+        // would-be entry at j = i + (qx, qy, qz): -(sum of the listed products) / L_jj
+        auto test = [&](int qx, int qy, int qz, double s) {
+            if (s == 0.0) return;
+            const int xj = x + qx, yj = y + qy, zj = z + qz;
+            if (xj < 0 || xj >= nx || yj < 0 || yj >= ny || zj < 0 || zj >= nz) return;
+            const long long j = xj + (long long)nx * yj + nxy * zj;
+            if (!(a.nb[j] & NB_IN)) return;
+            fill |= fabs(s / P(PL_D, j)) >= tau;
+        };
+        auto at = [&](int qx, int qy, int qz, int plane) -> double {
+            const int xj = x + qx, yj = y + qy, zj = z + qz;
+            if (xj < 0 || xj >= nx || yj < 0 || yj >= ny || zj < 0 || zj >= nz) return 0.0;
+            return P(plane, xj + (long long)nx * yj + nxy * zj);
+        };
+        if (lc != 0.0) test(-1, 1, -1, lc * at(-1, 1, -1, PL_D1));
+        if (lf != 0.0) test(-1, 2, -1, lf * at(-1, 2, -1, PL_D1));
+        if (lf != 0.0) test(0, 2, -1, lf * at(0, 2, -1, PL_B));
+        if (le != 0.0 || lf != 0.0) test(1, 1, -1, le * at(1, 1, -1, PL_B) + lf * at(1, 1, -1, PL_A));
+        if (ld != 0.0) test(2, -1, 0, ld * at(2, -1, 0, PL_A));
+        if (le != 0.0) test(2, 0, -1, le * at(2, 0, -1, PL_A));
+    }
+    if (fill) set_err(a.istate, FM_ERR_FILL);
+}
+
+// ------------------------------------------------------------------ launches
+
+template <typename T>
+int ict_max_blocks_per_sm() {
+    int f = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&f, k_ict_fwd<T>, kThreads, 0) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ict_bwd<T>, kThreads, 0) != cudaSuccess) return 0;
+    return f < b ? f : b;
+}
+
+template <typename T>
+cudaError_t launch_ict_tau(const DataArgs& a, double droptol, int grid, cudaStream_t s) {
+    k_ict_tau<T><<<grid, kThreads, 0, s>>>(a, droptol);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_ict_fwd(const IctArgs& a, int grid, cudaStream_t s) {
+    k_ict_fwd<T><<<grid, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_ict_bwd(const IctArgs& a, int grid, cudaStream_t s) {
+    k_ict_bwd<T><<<grid, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_ict_check(const IctArgs& a, int grid, cudaStream_t s) {
+    k_ict_check<T><<<grid, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+#define FM_ICT_INST(T)                                                                   \
+    template cudaError_t launch_ict_tau<T>(const DataArgs&, double, int, cudaStream_t); \
+    template cudaError_t launch_ict_fwd<T>(const IctArgs&, int, cudaStream_t);          \
+    template cudaError_t launch_ict_bwd<T>(const IctArgs&, int, cudaStream_t);          \
+    template cudaError_t launch_ict_check<T>(const IctArgs&, int, cudaStream_t);        \
+    template int ict_max_blocks_per_sm<T>();
+FM_ICT_INST(float)
+FM_ICT_INST(double)
+
+}  // namespace fm

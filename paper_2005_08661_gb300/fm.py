@@ -16,13 +16,13 @@ from . import build as _build
 
 FM_OK, FM_ERR_ARG, FM_ERR_STATE, FM_ERR_CUDA = 0, -1, -2, -3
 FM_ERR_NOT_PD, FM_ERR_TIMEOUT, FM_ERR_NONFINITE, FM_ERR_OOM = -4, -5, -6, -7
-FM_ERR_SIZE = -8
+FM_ERR_SIZE, FM_ERR_FILL = -8, -9
 FM_FP64, FM_FP32 = 0, 1
-FM_PC_IC0, FM_PC_DIAG, FM_PC_NONE, FM_PC_RB = 0, 1, 2, 3
+FM_PC_IC0, FM_PC_DIAG, FM_PC_NONE, FM_PC_RB, FM_PC_ICT = 0, 1, 2, 3, 4
 FM_CURV_LITERAL, FM_CURV_COMBINED = 0, 1
 
 _PREC = {"fp32": FM_FP32, "fp64": FM_FP64}
-_PC = {"ic0": FM_PC_IC0, "diag": FM_PC_DIAG, "none": FM_PC_NONE, "rb": FM_PC_RB}
+_PC = {"ic0": FM_PC_IC0, "diag": FM_PC_DIAG, "none": FM_PC_NONE, "rb": FM_PC_RB, "ict": FM_PC_ICT}
 _CURV = {"literal": FM_CURV_LITERAL, "combined": FM_CURV_COMBINED}
 
 
@@ -34,7 +34,7 @@ class FmError(RuntimeError):
 
 class FmOpts(C.Structure):
     _fields_ = [("precision", C.c_int), ("nls", C.c_int), ("precond", C.c_int), ("curvature", C.c_int),
-                ("spin_limit", C.c_longlong), ("use_graph", C.c_int)]
+                ("spin_limit", C.c_longlong), ("use_graph", C.c_int), ("droptol", C.c_double)]
 
 
 _LIB = None
@@ -124,7 +124,9 @@ class FieldMap:
     """One volume's field-map estimator on one GPU (a handle on an fm_ctx)."""
 
     def __init__(self, nx, ny, nz, ncoil=1, necho=3, precision="fp32", nls=5, precond="ic0",
-                 curvature="literal", spin_limit=1 << 21, use_graph=True, device=None, stream=None):
+                 curvature="literal", spin_limit=1 << 21, use_graph=True, device=None, stream=None, droptol=1e-3):
+        """precond: "ic0" (the paper's IC(0)), "ict" (IC with the drop tolerance droptol * H_max,
+        Sec. III-B's L_t), "rb" (red-black IC(0)), "diag" or "none"."""
         import torch
         self._torch = torch
         self.lib = load_library()
@@ -146,6 +148,7 @@ class FieldMap:
         o.curvature = _CURV[curvature]
         o.spin_limit = int(spin_limit)
         o.use_graph = 1 if use_graph else 0
+        o.droptol = float(droptol)
         self.opts = o
         h = C.c_void_p()
         sp = stream.cuda_stream if stream is not None else 0
@@ -357,7 +360,7 @@ class FieldMapBatch:
     advances every volume's outer iteration."""
 
     def __init__(self, shapes, precision="fp32", nls=5, precond="ic0", curvature="literal", spin_limit=1 << 21,
-                 device=None, stream=None):
+                 device=None, stream=None, droptol=1e-3):
         """shapes: list of (nx, ny, nz, ncoil, necho)."""
         import torch
         self._torch = torch
@@ -378,6 +381,7 @@ class FieldMapBatch:
         o.precond = _PC[precond]
         o.curvature = _CURV[curvature]
         o.spin_limit = int(spin_limit)
+        o.droptol = float(droptol)
         dims = (C.c_int * (5 * len(shapes)))(*[v for sh in self.shapes for v in sh])
         h = C.c_void_p()
         sp = stream.cuda_stream if stream is not None else 0

@@ -1,0 +1,177 @@
+"""IC with a drop tolerance on the GPU (FM_PC_ICT; Sec. III-B's L_t and the paper's
+NCG-MLS-IC).  The kernels hold IC(0)'s pattern plus the level-1 fill offsets and report
+FM_ERR_FILL exactly when the drop tolerance keeps an entry outside it.  Checked here against
+the oracle's generic left-looking threshold IC:
+
+* the factor's inverse pivots and the apply, on volumes whose factor keeps level-1 fill
+  (echoes 0/1/2.3 ms, tolerance 1e-2 H_max) and on volumes that keep none (echoes 0/2/10 ms,
+  the paper's 1e-3 H_max), with grids spanning several columns' worth of levels and ragged
+  edges;
+* FM_ERR_FILL exactly where the oracle's factor has an entry outside the held pattern;
+* the solve's per-iteration cost against the oracle's solve with the same preconditioner;
+* at full size (256x256x128, 8 coils, FP32), the pivots' recurrence at sampled voxels."""
+import numpy as np
+import pytest
+
+from gpu_util import open_fm, to_dev, to_np
+from oracle import Oracle, ict_factor
+from synth import make_volume
+
+pytestmark = pytest.mark.gpu
+
+PHANTOM_TE = (0.0, 1.0, 2.3)
+HELD = {(-1, 0, 0), (0, -1, 0), (0, 0, -1), (1, -1, 0), (1, 0, -1), (0, 1, -1)}
+LEVEL1 = {(1, -1, 0), (1, 0, -1), (0, 1, -1)}
+
+# (nx, ny, nz, ncoil, echo times, drop tolerance relative to H_max)
+KEEPS_LEVEL1 = [(45, 33, 9, 4, PHANTOM_TE, 1e-2), (70, 37, 19, 2, PHANTOM_TE, 1e-2),
+                (13, 9, 10, 3, PHANTOM_TE, 1e-2), (33, 1, 17, 2, PHANTOM_TE, 1e-2)]
+KEEPS_NONE = [(70, 37, 19, 1, (0.0, 2.0, 10.0), 1e-3), (1, 1, 1, 1, (0.0, 2.0, 10.0), 1e-3)]
+KEEPS_MORE = [(45, 33, 9, 4, PHANTOM_TE, 1e-3), (1, 40, 9, 2, PHANTOM_TE, 1e-2)]
+
+
+def _vol(nx, ny, nz, nc, te):
+    seed = {(45, 33, 9): 11, (70, 37, 19): 12 if te == PHANTOM_TE else 16, (13, 9, 10): 13, (1, 40, 9): 14,
+            (33, 1, 17): 15}.get((nx, ny, nz), 17)
+    return make_volume(nx, ny, nz, ncoil=nc, te=te, snr_db=20.0, seed=seed, fmax_hz=150.0, nblobs=3,
+                       beta=2.0 ** -3)
+
+
+def _offsets(shape, mask, d, beta, tau):
+    """Offsets (column voxel - row voxel) of the oracle factor's off-diagonal entries."""
+    colptr, rowidx, _, umap = ict_factor(shape, mask, d, beta, tau)
+    nz, ny, nx = shape
+    cols = np.repeat(np.arange(colptr.size - 1), np.diff(colptr))
+    vi, vj = umap[rowidx], umap[cols]
+    off = vi != vj
+
+    def vec(a):
+        return np.stack([a % nx, (a // nx) % ny, a // (nx * ny)], 1)
+    return [tuple(int(t) for t in v) for v in vec(vj[off]) - vec(vi[off])]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", KEEPS_LEVEL1 + KEEPS_NONE)
+def test_ict_factor_and_apply_match_oracle(prec, case):
+    *dims, te, droptol = case
+    vol = _vol(*dims, te)
+    o = Oracle.from_volume(vol)
+    rng = np.random.default_rng(5)
+    w = o.init()
+    g = rng.standard_normal(vol.mask.shape) * vol.mask
+    d = o.curv(w)
+    tau = droptol * o.hmax(d)
+    offs = _offsets(o.shape, vol.mask, d, vol.beta, tau)
+    assert all(v in HELD for v in offs)
+    if case in KEEPS_LEVEL1:
+        assert sum(v in LEVEL1 for v in offs) > 50  # the case exercises the fill entries
+    colptr, rowidx, val, umap = ict_factor(o.shape, vol.mask, d, vol.beta, tau)
+    ip_ref = np.zeros(vol.mask.size)
+    ip_ref[umap] = 1.0 / val[colptr[:-1]] ** 2
+    p_ref = o.precondition_ict(d, g, tau)
+    fm = open_fm(vol, prec, precond="ict", droptol=droptol)
+    wd = to_dev(w, prec)
+    ip = to_np(fm.ic_factor(wd)).reshape(-1)
+    p = to_np(fm.ic_apply(to_dev(g, prec)))
+    fm.cost_grad(wd)  # synchronises: no FM_ERR_FILL, no FM_ERR_NOT_PD
+    tol = 1e-11 if prec == "fp64" else 2e-4
+    assert np.max(np.abs(ip - ip_ref)) <= tol * np.max(np.abs(ip_ref))
+    assert np.max(np.abs(p - p_ref)) <= tol * np.max(np.abs(p_ref))
+    assert np.all(p[vol.mask == 0] == 0)
+    fm.close()
+
+
+@pytest.mark.parametrize("case", KEEPS_MORE + [(45, 33, 17, 2, (0.0, 2.0, 10.0), 0.0),
+                                               (45, 33, 17, 2, (0.0, 2.0, 10.0), 1e-9)])
+def test_fill_outside_the_held_pattern_is_reported(case):
+    from paper_2005_08661_gb300 import FmError, FM_ERR_FILL
+    *dims, te, droptol = case
+    vol = _vol(*dims, te)
+    o = Oracle.from_volume(vol)
+    w = o.init()
+    d = o.curv(w)
+    offs = _offsets(o.shape, vol.mask, d, vol.beta, droptol * o.hmax(d))
+    assert any(v not in HELD for v in offs)
+    fm = open_fm(vol, "fp64", precond="ict", droptol=droptol)
+    wd = to_dev(w, "fp64")
+    fm.ic_factor(wd)
+    with pytest.raises(FmError) as e:
+        fm.cost_grad(wd)
+    assert e.value.status == FM_ERR_FILL
+    # the error word is cleared and the context stays usable
+    fm.cost_grad(wd)
+    fm.close()
+
+
+@pytest.mark.parametrize("case", [KEEPS_LEVEL1[0], KEEPS_LEVEL1[2], KEEPS_NONE[0]])
+def test_fp64_ict_solve_matches_oracle_per_iteration(case):
+    """A fill outside the held pattern at any iterate would raise FM_ERR_FILL here."""
+    *dims, te, droptol = case
+    vol = _vol(*dims, te)
+    o = Oracle.from_volume(vol)
+    o.set_droptol(droptol)
+    ref = o.solve(niter=15, nls=5, precond=4)
+    fm = open_fm(vol, "fp64", precond="ict", droptol=droptol)
+    w, cost = fm.solve(niter=15)
+    np.testing.assert_allclose(cost, ref["cost"], rtol=1e-10)
+    np.testing.assert_allclose(to_np(w), ref["w"], rtol=0, atol=1e-9)
+    fm.close()
+
+
+def test_fp32_ict_solve_decreases_the_cost():
+    *dims, te, droptol = KEEPS_LEVEL1[1]
+    vol = _vol(*dims, te)
+    fm = open_fm(vol, "fp32", precond="ict", droptol=droptol)
+    _, cost = fm.solve(niter=30)
+    assert np.all(np.diff(cost) <= 2e-6 * np.abs(cost[:-1])) and cost[-1] < cost[0]
+    fm.close()
+
+
+def _nbr_count(mask):
+    m = mask.astype(bool)
+    n = np.zeros(m.shape, int)
+    for ax in range(3):
+        a = np.swapaxes(m, 0, ax)
+        c = np.zeros(a.shape, int)
+        c[1:] += a[:-1]
+        c[:-1] += a[1:]
+        n += np.swapaxes(c, 0, ax)
+    return n * m
+
+
+def test_full_size_pivots_follow_the_recurrence():
+    """256x256x128, 8 coils, FP32, the paper's tolerance 1e-3 H_max: the data dominate H, so
+    no fill survives and each column of IC(0) is kept or dropped whole: at sampled voxels the
+    stored pivots obey pi_j = H_jj - beta^2 sum over the earlier in-mask neighbours k with
+    beta / sqrt(pi_k) >= tau of 1/pi_k, with H_jj from the GPU's own curvature."""
+    import torch
+    from synth import full_config
+    vol = full_config()
+    fm = open_fm(vol, "fp32", precond="ict")
+    w = fm.init_omega()
+    _, _, d = fm.cost_grad(w, want_cost=False, want_grad=False, want_curv=True)
+    ip = fm.ic_factor(w)
+    fm.cost_grad(w)  # synchronising: FM_ERR_FILL / FM_ERR_NOT_PD would raise here
+    torch.cuda.synchronize()
+    ip = to_np(ip)
+    d = to_np(d)
+    mask = vol.mask > 0
+    beta = vol.beta
+    h = d + beta * _nbr_count(vol.mask)
+    tau = 1e-3 * float(h[mask].max())
+    kept = beta * np.sqrt(ip) >= tau
+    zz, yy, xx = np.nonzero(mask)
+    pick = np.random.default_rng(7).choice(zz.size, 20000, replace=False)
+    s = np.zeros(pick.size)
+    for dz, dy, dx in ((0, 0, 1), (0, 1, 0), (1, 0, 0)):
+        z, y, x = zz[pick] - dz, yy[pick] - dy, xx[pick] - dx
+        ok = (z >= 0) & (y >= 0) & (x >= 0)
+        z, y, x = np.where(ok, z, 0), np.where(ok, y, 0), np.where(ok, x, 0)
+        ok &= mask[z, y, x] & kept[z, y, x]
+        s += np.where(ok, ip[z, y, x], 0.0)
+    pi = h[zz[pick], yy[pick], xx[pick]] - beta * beta * s
+    rel = np.abs(1.0 / ip[zz[pick], yy[pick], xx[pick]] - pi) / pi
+    assert rel.max() <= 2e-6
+    frac = kept[mask].mean()
+    assert 0.0 < frac < 0.5  # only the weakly weighted voxels' columns reach the tolerance
+    fm.close()
