@@ -50,7 +50,7 @@ struct fm_ctx {
     int ic_wxy = 2, ic_wz = 1;  // forward tile claim order weights
     int nsm = 0, grid_data = 0, grid_ls = 0, grid_ic = 0, grid_icb = 0;  // grid_icb: backward IC sweep
     int base_data = 0, base_ls = 0, base_ic = 0, base_icb = 0;
-    int grid_ict = 0, base_ict = 0;  // drop-tolerance IC sweeps (persistent, level barriers)
+    int grid_ict = 0, base_ict = 0, block_ict = 0;  // drop-tolerance IC sweeps (persistent, level barriers)
     double* ict_L = nullptr;         // drop-tolerance IC factor planes [kIctPlanes][nv]  // grids chosen at creation (batch autotuning scales them)
     int last_niter = 0;
     cudaGraphExec_t gexec = nullptr;
@@ -259,7 +259,7 @@ cudaError_t run_ict(fm_ctx* c, const void* d, const void* g, void* p, const void
         if (e != cudaSuccess) return e;
     }
     if (prof) cudaEventRecordWithFlags(c->ev[slot][FM_K_IC_FWD][0], c->stream, cudaEventRecordExternal);
-    e = launch_ict_fwd<T>(a, c->grid_ict, c->stream);
+    e = launch_ict_fwd<T>(a, c->grid_ict, c->block_ict, c->stream);
     if (prof) {
         cudaEventRecordWithFlags(c->ev[slot][FM_K_IC_FWD][1], c->stream, cudaEventRecordExternal);
         c->ev_rec[slot][FM_K_IC_FWD] = true;
@@ -270,7 +270,7 @@ cudaError_t run_ict(fm_ctx* c, const void* d, const void* g, void* p, const void
         if (e != cudaSuccess) return e;
     }
     if (prof) cudaEventRecordWithFlags(c->ev[slot][FM_K_IC_BWD][0], c->stream, cudaEventRecordExternal);
-    e = launch_ict_bwd<T>(a, c->grid_ict, c->stream);
+    e = launch_ict_bwd<T>(a, c->grid_ict, c->block_ict, c->stream);
     if (prof) {
         cudaEventRecordWithFlags(c->ev[slot][FM_K_IC_BWD][1], c->stream, cudaEventRecordExternal);
         c->ev_rec[slot][FM_K_IC_BWD] = true;
@@ -730,11 +730,16 @@ int fm_create(fm_ctx** out, int nx, int ny, int nz, int ncoil, int necho, const 
     c->base_ic = c->grid_ic;
     c->base_icb = c->grid_icb;
     if (o.precond == FM_PC_ICT) {
-        // one thread per (y, z) column of the level sweep, every block resident (grid barrier)
-        const int occ = o.precision == FM_FP64 ? ict_max_blocks_per_sm<double>() : ict_max_blocks_per_sm<float>();
-        if (occ < 1) return bail(FM_ERR_CUDA);
+        // one thread per (y, z) column of the level sweep, the columns spread over every SM
+        // (the sweeps are bound by FP64 issue), every block resident (grid barrier)
         const long long cols = (long long)ny * nz;
-        c->grid_ict = (int)std::max(1LL, std::min<long long>((cols + kThreads - 1) / kThreads, (long long)occ * c->nsm));
+        const long long per_sm = (cols + c->nsm - 1) / c->nsm;
+        c->block_ict = (int)std::min<long long>(kIctThreads, std::max<long long>(32, (per_sm + 31) / 32 * 32));
+        const int occ = o.precision == FM_FP64 ? ict_max_blocks_per_sm<double>(c->block_ict)
+                                               : ict_max_blocks_per_sm<float>(c->block_ict);
+        if (occ < 1) return bail(FM_ERR_CUDA);
+        c->grid_ict = (int)std::max(1LL, std::min<long long>((cols + c->block_ict - 1) / c->block_ict,
+                                                             (long long)occ * c->nsm));
         c->base_ict = c->grid_ict;
     }
     const size_t vb = (size_t)c->nv * c->ts;

@@ -148,32 +148,38 @@ __device__ __forceinline__ bool spin_until(const int* flag, int want, long long 
     return true;
 }
 
-// Grid-wide barrier for a cooperative launch (all blocks co-resident).  Bounded: on
-// timeout it records FM_ERR_TIMEOUT and returns false (the caller then exits).
+// Grid-wide barrier for a launch whose blocks are all co-resident (grids sized by
+// occupancy).  Bounded: on timeout it records FM_ERR_TIMEOUT and returns false (the caller
+// then exits).  Generation counting: thread 0 of each block reads the generation, then
+// arrives with one acquire-release atomic (releasing the block's writes, which the block
+// barrier has ordered before it); the last to arrive resets the count and publishes the next
+// generation with a release store; the others poll it with acquire loads -- tightly at
+// first, since most waits last a few microseconds, then with backoff.
+__device__ __forceinline__ int atom_add_acq_rel(int* p, int v) {
+    int old;
+    asm volatile("atom.add.acq_rel.gpu.global.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 __device__ __forceinline__ bool grid_barrier(int* istate, long long limit) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int* count = istate + I_BAR_COUNT;
         int* gen = istate + I_BAR_GEN;
-        int g0 = ld_acquire(gen);
-        __threadfence();
-        int arrived = atomicAdd(count, 1);
+        const int g0 = ld_acquire(gen);
+        const int arrived = atom_add_acq_rel(count, 1);
         int ok = 1;
         if (arrived == (int)gridDim.x - 1) {
             atomicExch(count, 0);
-            __threadfence();
             st_release(gen, g0 + 1);
         } else {
             long long n = 0;
-            unsigned ns = 32;
             while (ld_acquire(gen) == g0) {
                 if (++n > limit) { ok = 0; break; }
-                __nanosleep(ns);
-                if (ns < 256) ns <<= 1;
+                if (n > 64) __nanosleep(n > 4096 ? 256 : 32);
             }
         }
-        __threadfence();
         if (!ok) atomicCAS(istate + I_ERR, 0, FM_ERR_TIMEOUT);
         s_ok = ok;
     }
@@ -276,9 +282,10 @@ struct IcArgs {
 };
 
 // IC with a drop tolerance (k_ict.cu) on the pattern of IC(0) plus the level-1 fill offsets.
-// Factor planes, each [nv] double: L_ii, then L_{i,i+o} for the offsets o = (-1,0,0),
+// Factor planes, each [nv] double: 1 / L_ii, then L_{i,i+o} for the offsets o = (-1,0,0),
 // (0,-1,0), (0,0,-1), (1,-1,0), (1,0,-1), (0,1,-1), then the substitution vector.
 constexpr int kIctPlanes = 8;
+constexpr int kIctThreads = 1024;  // most threads per block of the level sweeps (one per (y, z) column)
 struct IctArgs {
     Geo geo;
     double beta;
@@ -358,10 +365,10 @@ template <typename T> cudaError_t launch_wf_sweep(const AdjArgs& a, int nsweep, 
                                                   cudaStream_t s);
 template <typename T> cudaError_t launch_wf_amp(const AdjArgs& a, int grid, cudaStream_t s);
 template <typename T> cudaError_t launch_ict_tau(const DataArgs& a, double droptol, int grid, cudaStream_t s);
-template <typename T> cudaError_t launch_ict_fwd(const IctArgs& a, int grid, cudaStream_t s);
-template <typename T> cudaError_t launch_ict_bwd(const IctArgs& a, int grid, cudaStream_t s);
+template <typename T> cudaError_t launch_ict_fwd(const IctArgs& a, int grid, int block, cudaStream_t s);
+template <typename T> cudaError_t launch_ict_bwd(const IctArgs& a, int grid, int block, cudaStream_t s);
 template <typename T> cudaError_t launch_ict_check(const IctArgs& a, int grid, cudaStream_t s);
-template <typename T> int ict_max_blocks_per_sm();
+template <typename T> int ict_max_blocks_per_sm(int block);
 template <typename T> int ic_tz();
 template <typename T> size_t ic_face_bytes_per_tile();
 template <typename T> int ic_max_blocks_per_sm(bool bwd);  // resident IC sweep blocks per SM

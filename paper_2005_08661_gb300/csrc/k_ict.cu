@@ -22,7 +22,12 @@
 // wavefront does not apply.  With level t = x + 2y + 3z every offset in P points to a strictly
 // lower level (t(a) = t(d) = t(f) = -1, t(b) = t(e) = -2, t(c) = -3), so one persistent kernel
 // sweeps the levels in order -- thread <-> (y, z) column, voxel x = t - 2y - 3z -- with a
-// bounded grid barrier between levels; the back substitution sweeps them in reverse.
+// barrier between levels; the back substitution sweeps them in reverse.  A level's work is
+// FP64 arithmetic on the active columns, so the blocks are sized to spread the columns over
+// every SM (a volume with few columns runs one-warp blocks), and the barrier is the bounded
+// grid barrier -- or a block barrier when one block holds every column.  The factor
+// stores 1 / L_ii, so every entry costs a multiply, and each row issues all of its loads
+// from the earlier rows before the dependency chain starts.
 //
 // Exactness.  This is the exact drop-tolerance factor as long as no entry outside P
 // survives.  With the factor on P in hand, k_ict_check forms every would-be entry just
@@ -95,10 +100,37 @@ __global__ void __launch_bounds__(kThreads) k_ict_tau(DataArgs a, double droptol
 // ------------------------------------------------------------------ the sweeps
 
 // Plane indices of the factor storage.
-enum : int { PL_D = 0, PL_A, PL_B, PL_C, PL_D1, PL_E, PL_F, PL_Y };
+enum : int { PL_R = 0, PL_A, PL_B, PL_C, PL_D1, PL_E, PL_F, PL_Y };  // PL_R: 1 / L_ii
+
+// 1 / sqrt(s) for s > 0 in double: a float seed refined by two Newton-Raphson steps
+// r <- r (3 - s r^2) / 2, each of which squares the relative error (about 2^-22 for the
+// seed, so the second step reaches double rounding).  The GB300 FP64 pipe issues about
+// 1/64 as fast as FP32, and this chain sits on every row's critical path.
+__device__ __forceinline__ double rsqrt_nr(double s) {
+    double r = (double)rsqrtf((float)s);
+    const double hs = 0.5 * s;
+    r = r * fma(-hs * r, r, 1.5);
+    r = r * fma(-hs * r, r, 1.5);
+    return r;
+}
+
+// A value another thread wrote at an earlier level: with one block the writer shares this
+// SM's L1 and the block barrier orders the two, so a plain (L1-cached) load is safe; across
+// blocks the load must bypass L1.
+__device__ __forceinline__ double ld_level(const double* p) { return gridDim.x == 1 ? *p : __ldcg(p); }
+
+// Separates two levels: a block barrier when one block holds every column, else the
+// bounded grid barrier (every block is resident: the grid is sized by occupancy).
+__device__ __forceinline__ bool level_sync(const IctArgs& a) {
+    if (gridDim.x == 1) {
+        __syncthreads();
+        return true;
+    }
+    return grid_barrier(a.istate, a.spin_limit);
+}
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_ict_fwd(IctArgs a) {
+__global__ void __launch_bounds__(kIctThreads) k_ict_fwd(IctArgs a) {
     const int nx = a.geo.nx, ny = a.geo.ny, nz = a.geo.nz;
     const long long nxy = (long long)nx * ny, nv = a.geo.nv;
     double* Lp = a.L;
@@ -125,47 +157,49 @@ __global__ void __launch_bounds__(kThreads) k_ict_fwd(IctArgs a) {
             const bool hd = x + 1 < nx && y > 0 && (a.nb[jd] & NB_IN);
             const bool he = x + 1 < nx && z > 0 && (a.nb[je] & NB_IN);
             const bool hf = y + 1 < ny && z > 0 && (a.nb[jf] & NB_IN);
-            double la = 0, lb = 0, lc = 0, ld = 0, le = 0, lf = 0, lii;
+            auto ld = [&](bool h, int k, long long j) { return h ? ld_level(P(k, j)) : 0.0; };
+            // every value from the earlier rows first (independent loads), then the chain
+            const double yc = ld(hc, PL_Y, jc), ye = ld(he, PL_Y, je), yf = ld(hf, PL_Y, jf),
+                         yb = ld(hb, PL_Y, jb), yd = ld(hd, PL_Y, jd), ya = ld(ha, PL_Y, ja);
+            double la, lb, lc, l_d, le, lf, rii;
             if (factor) {
-                auto keep = [&](double v) { return fabs(v) >= tau ? v : 0.0; };
-                if (hc) lc = keep(-beta / __ldcg(P(PL_D, jc)));
-                if (he) le = keep(-(lc * __ldcg(P(PL_A, je))) / __ldcg(P(PL_D, je)));
-                if (hf) lf = keep(-(lc * __ldcg(P(PL_B, jf)) + le * __ldcg(P(PL_D1, jf))) / __ldcg(P(PL_D, jf)));
-                if (hb) lb = keep((-beta - lc * __ldcg(P(PL_F, jb))) / __ldcg(P(PL_D, jb)));
-                if (hd) ld = keep(-(lb * __ldcg(P(PL_A, jd)) + le * __ldcg(P(PL_F, jd))) / __ldcg(P(PL_D, jd)));
-                if (ha)
-                    la = keep((-beta - lb * __ldcg(P(PL_D1, ja)) - lc * __ldcg(P(PL_E, ja))) / __ldcg(P(PL_D, ja)));
+                const double rc = ld(hc, PL_R, jc), re = ld(he, PL_R, je), rf = ld(hf, PL_R, jf),
+                             rb = ld(hb, PL_R, jb), rd = ld(hd, PL_R, jd), ra = ld(ha, PL_R, ja);
+                const double e_a = ld(he, PL_A, je), f_b = ld(hf, PL_B, jf), f_d = ld(hf, PL_D1, jf),
+                             b_f = ld(hb, PL_F, jb), d_a = ld(hd, PL_A, jd), d_f = ld(hd, PL_F, jd),
+                             a_d = ld(ha, PL_D1, ja), a_e = ld(ha, PL_E, ja);
+                auto keep = [&](bool h, double v) { return h && fabs(v) >= tau ? v : 0.0; };
+                lc = keep(hc, -beta * rc);
+                le = keep(he, -(lc * e_a) * re);
+                lf = keep(hf, -(lc * f_b + le * f_d) * rf);
+                lb = keep(hb, (-beta - lc * b_f) * rb);
+                l_d = keep(hd, -(lb * d_a + le * d_f) * rd);
+                la = keep(ha, (-beta - lb * a_d - lc * a_e) * ra);
                 const double h = (double)d[i] + beta * (double)__popc((unsigned)(b >> 1) & 0x3fu);
-                const double s = h - (((la * la + lb * lb) + (lc * lc + ld * ld)) + (le * le + lf * lf));
+                const double s = h - (((la * la + lb * lb) + (lc * lc + l_d * l_d)) + (le * le + lf * lf));
                 if (!(s > 0.0)) bad = true;
-                lii = s > 0.0 ? sqrt(s) : 1.0;  // the error is reported; keep the arithmetic finite
-                *P(PL_D, i) = lii;
+                rii = s > 0.0 ? rsqrt_nr(s) : 1.0;  // the error is reported; keep the arithmetic finite
+                *P(PL_R, i) = rii;
                 *P(PL_A, i) = la;
                 *P(PL_B, i) = lb;
                 *P(PL_C, i) = lc;
-                *P(PL_D1, i) = ld;
+                *P(PL_D1, i) = l_d;
                 *P(PL_E, i) = le;
                 *P(PL_F, i) = lf;
-                if (ipo) ipo[i] = (T)(1.0 / (lii * lii));
+                if (ipo) ipo[i] = (T)(rii * rii);
             } else {
-                lii = *P(PL_D, i);
+                rii = *P(PL_R, i);
                 la = *P(PL_A, i);
                 lb = *P(PL_B, i);
                 lc = *P(PL_C, i);
-                ld = *P(PL_D1, i);
+                l_d = *P(PL_D1, i);
                 le = *P(PL_E, i);
                 lf = *P(PL_F, i);
             }
-            double acc = (double)g[i];
-            if (hc) acc -= lc * __ldcg(P(PL_Y, jc));
-            if (he) acc -= le * __ldcg(P(PL_Y, je));
-            if (hf) acc -= lf * __ldcg(P(PL_Y, jf));
-            if (hb) acc -= lb * __ldcg(P(PL_Y, jb));
-            if (hd) acc -= ld * __ldcg(P(PL_Y, jd));
-            if (ha) acc -= la * __ldcg(P(PL_Y, ja));
-            *P(PL_Y, i) = acc / lii;
+            const double acc = (double)g[i] - ((lc * yc + le * ye) + (lf * yf + lb * yb) + (l_d * yd + la * ya));
+            *P(PL_Y, i) = acc * rii;
         }
-        if (t < tmax && !grid_barrier(a.istate, a.spin_limit)) return;
+        if (t < tmax && !level_sync(a)) return;
     }
     // reported by the back sweep, after k_ict_check: fill beyond the held pattern (which can
     // itself make a pivot of the restricted factor non-positive) takes precedence
@@ -173,7 +207,7 @@ __global__ void __launch_bounds__(kThreads) k_ict_fwd(IctArgs a) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_ict_bwd(IctArgs a) {
+__global__ void __launch_bounds__(kIctThreads) k_ict_bwd(IctArgs a) {
     __shared__ double sbuf[2 * 32];
     const int nx = a.geo.nx, ny = a.geo.ny, nz = a.geo.nz;
     const long long nxy = (long long)nx * ny, nv = a.geo.nv;
@@ -206,20 +240,17 @@ __global__ void __launch_bounds__(kThreads) k_ict_bwd(IctArgs a) {
             const bool hd = x > 0 && y + 1 < ny && (a.nb[rd] & NB_IN);
             const bool he = x > 0 && z + 1 < nz && (a.nb[re] & NB_IN);
             const bool hf = y > 0 && z + 1 < nz && (a.nb[rf] & NB_IN);
-            double s = *P(PL_Y, i);
-            if (ha) s -= __ldcg(P(PL_A, ra)) * __ldcg(P(PL_Y, ra));
-            if (hd) s -= __ldcg(P(PL_D1, rd)) * __ldcg(P(PL_Y, rd));
-            if (hf) s -= __ldcg(P(PL_F, rf)) * __ldcg(P(PL_Y, rf));
-            if (hb) s -= __ldcg(P(PL_B, rb)) * __ldcg(P(PL_Y, rb));
-            if (he) s -= __ldcg(P(PL_E, re)) * __ldcg(P(PL_Y, re));
-            if (hc) s -= __ldcg(P(PL_C, rc)) * __ldcg(P(PL_Y, rc));
-            const double xi = s / *P(PL_D, i);
+            auto ld = [&](bool h, int k, long long j) { return h ? ld_level(P(k, j)) : 0.0; };
+            const double s = *P(PL_Y, i) - ((ld(ha, PL_A, ra) * ld(ha, PL_Y, ra) + ld(hd, PL_D1, rd) * ld(hd, PL_Y, rd)) +
+                                            (ld(hf, PL_F, rf) * ld(hf, PL_Y, rf) + ld(hb, PL_B, rb) * ld(hb, PL_Y, rb)) +
+                                            (ld(he, PL_E, re) * ld(he, PL_Y, re) + ld(hc, PL_C, rc) * ld(hc, PL_Y, rc)));
+            const double xi = s * *P(PL_R, i);
             *P(PL_Y, i) = xi;  // y_i becomes x_i: every row that still needs y_i is this one
             p[i] = (T)xi;
             if (gd) acc2[0] += (double)gd[i] * (double)(T)xi;
             if (gpd) acc2[1] += (double)gpd[i] * (double)(T)xi;
         }
-        if (t > 0 && !grid_barrier(a.istate, a.spin_limit)) return;
+        if (t > 0 && !level_sync(a)) return;
     }
     if (gd || gpd) {
         double out[2];
@@ -256,7 +287,7 @@ __global__ void __launch_bounds__(kThreads) k_ict_check(IctArgs a) {
             if (xj < 0 || xj >= nx || yj < 0 || yj >= ny || zj < 0 || zj >= nz) return;
             const long long j = xj + (long long)nx * yj + nxy * zj;
             if (!(a.nb[j] & NB_IN)) return;
-            fill |= fabs(s / P(PL_D, j)) >= tau;
+            fill |= fabs(s * P(PL_R, j)) >= tau;
         };
         auto at = [&](int qx, int qy, int qz, int plane) -> double {
             const int xj = x + qx, yj = y + qy, zj = z + qz;
@@ -276,10 +307,10 @@ __global__ void __launch_bounds__(kThreads) k_ict_check(IctArgs a) {
 // ------------------------------------------------------------------ launches
 
 template <typename T>
-int ict_max_blocks_per_sm() {
+int ict_max_blocks_per_sm(int block) {
     int f = 0, b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&f, k_ict_fwd<T>, kThreads, 0) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ict_bwd<T>, kThreads, 0) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&f, k_ict_fwd<T>, block, 0) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ict_bwd<T>, block, 0) != cudaSuccess) return 0;
     return f < b ? f : b;
 }
 
@@ -289,13 +320,13 @@ cudaError_t launch_ict_tau(const DataArgs& a, double droptol, int grid, cudaStre
     return cudaGetLastError();
 }
 template <typename T>
-cudaError_t launch_ict_fwd(const IctArgs& a, int grid, cudaStream_t s) {
-    k_ict_fwd<T><<<grid, kThreads, 0, s>>>(a);
+cudaError_t launch_ict_fwd(const IctArgs& a, int grid, int block, cudaStream_t s) {
+    k_ict_fwd<T><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
 template <typename T>
-cudaError_t launch_ict_bwd(const IctArgs& a, int grid, cudaStream_t s) {
-    k_ict_bwd<T><<<grid, kThreads, 0, s>>>(a);
+cudaError_t launch_ict_bwd(const IctArgs& a, int grid, int block, cudaStream_t s) {
+    k_ict_bwd<T><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
 template <typename T>
@@ -306,10 +337,10 @@ cudaError_t launch_ict_check(const IctArgs& a, int grid, cudaStream_t s) {
 
 #define FM_ICT_INST(T)                                                                   \
     template cudaError_t launch_ict_tau<T>(const DataArgs&, double, int, cudaStream_t); \
-    template cudaError_t launch_ict_fwd<T>(const IctArgs&, int, cudaStream_t);          \
-    template cudaError_t launch_ict_bwd<T>(const IctArgs&, int, cudaStream_t);          \
+    template cudaError_t launch_ict_fwd<T>(const IctArgs&, int, int, cudaStream_t);     \
+    template cudaError_t launch_ict_bwd<T>(const IctArgs&, int, int, cudaStream_t);     \
     template cudaError_t launch_ict_check<T>(const IctArgs&, int, cudaStream_t);        \
-    template int ict_max_blocks_per_sm<T>();
+    template int ict_max_blocks_per_sm<T>(int);
 FM_ICT_INST(float)
 FM_ICT_INST(double)
 
