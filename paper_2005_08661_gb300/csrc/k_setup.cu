@@ -89,6 +89,28 @@ __global__ void __launch_bounds__(1024) k_chunk_scan(int* counts, int n, int* to
     if (threadIdx.x == 0) *total = s_carry;
 }
 
+// Polar form of a coil-combined echo value w (the literal curvature's per-coil weights) or of
+// an echo-pair weight R_mn.
+// FP64 mode: IEEE double.  FP32 mode stores float, and the line search forms its phases in
+// float (|theta| up to about 16 rad, rounding near 1e-6 rad), so the angle comes from the
+// float atan2f of the rounded components (within 3 ulp) instead of a double atan2 -- the
+// FP64 pipe issues at about 1/64 of the FP32 rate and the double form dominated this
+// kernel.  The amplitude also enters the cost constant K, so it stays double-accurate: a
+// float square root refined by one Newton-Raphson step in double, f + (x - f^2) / (2 f).
+template <typename T>
+__device__ __forceinline__ double polar_amp(double wr, double wi) {
+    const double x = wr * wr + wi * wi;
+    if (sizeof(T) == 8) return sqrt(x);
+    const float f = sqrtf((float)x);
+    return f > 0.0f ? (double)f + fma(-(double)f, (double)f, x) * (double)(0.5f / f) : 0.0;
+}
+template <typename T>
+__device__ __forceinline__ T polar_angle(double wr, double wi) {
+    if (sizeof(T) == 8) return (T)((wr != 0.0 || wi != 0.0) ? atan2(wi, wr) : 0.0);
+    const float fr = (float)wr, fi = (float)wi;
+    return (T)((fr != 0.0f || fi != 0.0f) ? atan2f(fi, fr) : 0.0f);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kSetupThreads) k_setup(SetupArgs a) {
     using T2 = typename V2<T>::t;
@@ -159,14 +181,14 @@ __global__ void __launch_bounds__(kSetupThreads) k_setup(SetupArgs a) {
                 // conj(s) * y, scaled
                 const double wr = (sr * yr + si * yi) * scale;
                 const double wi = (sr * yi - si * yr) * scale;
-                const double amp = sqrt(wr * wr + wi * wi);
                 zr += wr;
                 zi += wi;
+                const double amp = polar_amp<T>(wr, wi);
                 am += amp;
                 if (coils) {
                     T2 o;
                     o.x = (T)amp;
-                    o.y = (T)(amp > 0.0 ? atan2(wi, wr) : 0.0);
+                    o.y = polar_angle<T>(wr, wi);
                     coils[((size_t)mm * nc + c) * nv + k] = o;
                 }
             }
@@ -186,8 +208,8 @@ __global__ void __launch_bounds__(kSetupThreads) k_setup(SetupArgs a) {
                 rr = tr;
             }
             T2 o;
-            o.x = (T)sqrt(rr * rr + ri * ri);
-            o.y = (T)((rr == 0.0 && ri == 0.0) ? 0.0 : atan2(ri, rr));
+            o.x = (T)polar_amp<T>(rr, ri);
+            o.y = polar_angle<T>(rr, ri);
             pairs[(size_t)p * nv + k] = o;
         }
         if (a.wf) {
@@ -196,7 +218,7 @@ __global__ void __launch_bounds__(kSetupThreads) k_setup(SetupArgs a) {
                 for (int n = 0; n < L; ++n) {
                     const double gr = a.lgam[2 * (mm * L + n)], gi = a.lgam[2 * (mm * L + n) + 1];
                     const double g = sqrt(gr * gr + gi * gi);
-                    const double zm = sqrt(Zr[mm] * Zr[mm] + Zi[mm] * Zi[mm]), zn = sqrt(Zr[n] * Zr[n] + Zi[n] * Zi[n]);
+                    const double zm = polar_amp<T>(Zr[mm], Zi[mm]), zn = polar_amp<T>(Zr[n], Zi[n]);
                     kj += g * (Am[mm] * Am[n] - zm * zn);
                     rj += g * Am[mm] * Am[n];
                 }
@@ -206,7 +228,7 @@ __global__ void __launch_bounds__(kSetupThreads) k_setup(SetupArgs a) {
             double sa = 0.0, sz = 0.0;
             for (int mm = 0; mm < L; ++mm) {
                 sa += Am[mm];
-                sz += sqrt(Zr[mm] * Zr[mm] + Zi[mm] * Zi[mm]);
+                sz += polar_amp<T>(Zr[mm], Zi[mm]);
             }
             if (S > 0.0) kacc += (sa - sz) * (sa + sz);
             if (a.rho) ((T*)a.rho)[k] = (T)(sa * sa);
