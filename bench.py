@@ -36,14 +36,14 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 # ncu DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch, by (workload,
-# kernel), from one capture of the full workload (profiles/traffic_full_256x256x128_c8.md);
-# an entry is removed when its kernel changes.
+# kernel), from one ncu capture of the full workload (its summary sits with the committed
+# profiles); an entry is removed when its kernel changes.
 NCU_TRAFFIC_BYTES = {
-    ("full", "ls"): 1944660352 + 214784,
-    ("full", "grad"): 504742656 + 21807232,
-    ("full", "ic_fwd"): 78002944 + 34450176,
-    ("full", "ic_bwd"): 134262016 + 18184704,
-    ("full", "dir"): 64362240 + 1252096,
+    ("full", "ls"): 1944679296 + 164864,
+    ("full", "grad"): 504675413 + 22891691,
+    ("full", "ic_fwd"): 77964032 + 34328064,
+    ("full", "ic_bwd"): 134320896 + 16416768,
+    ("full", "dir"): 64362368 + 586240,
 }
 
 WORKLOADS = {
