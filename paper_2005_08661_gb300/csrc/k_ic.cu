@@ -477,8 +477,11 @@ __global__ void __launch_bounds__(kThreadsIC) k_ic_fwd(IcArgs a, int mode, PivSc
                 T* dr = sd + tid * 32;
                 T* lr = sl + tid * 32;
                 const uint8_t* br = snb + tid * 32;
+                // each thread walks its own row; starting at column `lane` keeps the 32 lanes
+                // of a warp on 32 different banks (rows are 32 elements apart)
 #pragma unroll 4
-                for (int i = 0; i < 32; ++i) {
+                for (int k = 0; k < 32; ++k) {
+                    const int i = (k + lane) & 31;
                     const uint8_t b = br[i];
                     T hH = T(-1), hL = T(0);
                     if (b & NB_IN) Ops::form_h(dr[i], __popc((unsigned)(b >> 1) & 0x3fu), a.beta, pc, hH, hL);
