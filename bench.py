@@ -41,7 +41,6 @@ if ROOT not in sys.path:
 NCU_TRAFFIC_BYTES = {
     ("full", "ls"): 1944679296 + 164864,
     ("full", "grad"): 504675413 + 22891691,
-    ("full", "ic_fwd"): 77964032 + 34328064,
     ("full", "ic_bwd"): 134320896 + 16416768,
     ("full", "dir"): 64362368 + 586240,
 }
@@ -358,15 +357,20 @@ def run_ours(args, world, rank, local):
                                   torch.empty_like(m_d))]
         ev_copied = [torch.cuda.Event(), torch.cuda.Event()]
         ev_freed = [torch.cuda.Event(), torch.cuda.Event()]
+        copy_times = []  # (start, end) events of each step's host-to-device copy
 
         def issue_copy(k):
             yb, sb, mb = bufs[k % 2]
             copy_stream.wait_event(ev_freed[k % 2])
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             with torch.cuda.stream(copy_stream):
+                c0.record(copy_stream)
                 yb.copy_(y_h, non_blocking=True)
                 if sb is not None:
                     sb.copy_(s_h, non_blocking=True)
                 mb.copy_(m_h, non_blocking=True)
+                c1.record(copy_stream)
+            copy_times.append((c0, c1))
             ev_copied[k % 2].record(copy_stream)
 
         def compute(k):
@@ -386,6 +390,7 @@ def run_ours(args, world, rank, local):
         run_e2e(2)
         torch.cuda.synchronize(dev)
         barrier(world)
+        copy_times.clear()
         nst = max(1, args.steps)
         e0.record(stream)
         copy_stream.wait_event(e0)
@@ -394,8 +399,10 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize(dev)
         barrier(world)
         t_e2e = max_over_ranks(e0.elapsed_time(e1) / 1000.0 / nst, world, dev)
+        h2d_ms = sum(a.elapsed_time(b) for a, b in copy_times) / max(1, len(copy_times))
         e2e = {"value": world * nv * niter / t_e2e, "unit": "voxel-iter/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000 * t_e2e,
+               "h2d_ms_per_step": h2d_ms, "h2d_gbs": h2d / (h2d_ms * 1e-3) / 1e9 if h2d_ms > 0 else None,
                "pipelined": "step k+1's inputs copied on a second stream while step k computes"}
 
     # roofline of the kernel with the largest share of the outer iteration
