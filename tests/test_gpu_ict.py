@@ -8,7 +8,9 @@ the oracle's generic left-looking threshold IC:
   the paper's 1e-3 H_max), with grids spanning several columns' worth of levels and ragged
   edges;
 * FM_ERR_FILL exactly where the oracle's factor has an entry outside the held pattern;
-* the solve's per-iteration cost against the oracle's solve with the same preconditioner;
+* the solve's per-iteration cost against the oracle's solve with the same preconditioner,
+  alone and inside a batch;
+* the implicit-differentiation CG with this preconditioner reaches IC(0)'s solution;
 * at full size (256x256x128, 8 coils, FP32), the pivots' recurrence at sampled voxels."""
 import numpy as np
 import pytest
@@ -175,3 +177,49 @@ def test_full_size_pivots_follow_the_recurrence():
     frac = kept[mask].mean()
     assert 0.0 < frac < 0.5  # only the weakly weighted voxels' columns reach the tolerance
     fm.close()
+
+
+def test_adjoint_solution_does_not_depend_on_the_preconditioner():
+    """The implicit-differentiation CG (fm_adjoint_solve) with the drop-tolerance factor as its
+    preconditioner reaches the same lambda = H_true^{-1} b as with IC(0): the preconditioner
+    only changes the iteration count."""
+    *dims, te, droptol = KEEPS_LEVEL1[2]
+    vol = _vol(*dims, te)
+    ref = open_fm(vol, "fp64")
+    w, _ = ref.solve(niter=60)
+    b = to_dev(np.random.default_rng(9).standard_normal(vol.mask.shape) * vol.mask, "fp64")
+    lam0, it0, rr0 = ref.adjoint_solve(w, b, tol=1e-13, maxiter=3000)
+    ref.close()
+    fm = open_fm(vol, "fp64", precond="ict", droptol=droptol)
+    lam1, it1, rr1 = fm.adjoint_solve(w, b, tol=1e-13, maxiter=3000)
+    fm.close()
+    assert rr0 <= 1e-13 and rr1 <= 1e-13
+    l0, l1 = to_np(lam0), to_np(lam1)
+    assert np.max(np.abs(l1 - l0)) <= 1e-9 * np.max(np.abs(l0))
+
+
+def test_batched_drop_tolerance_solves_match_the_oracle_per_volume():
+    """FieldMapBatch with the drop-tolerance preconditioner: each volume's per-iteration cost
+    equals the oracle's solve of that volume alone (FP64)."""
+    from paper_2005_08661_gb300 import FieldMapBatch
+    from gpu_util import dev_inputs
+    droptol = 1e-2
+    cases = [KEEPS_LEVEL1[0], KEEPS_LEVEL1[2], KEEPS_NONE[0]]
+    vols = [_vol(*c[:4], c[4]) for c in cases]
+    refs = []
+    for v in vols:
+        o = Oracle.from_volume(v)
+        o.set_droptol(droptol)
+        refs.append(o.solve(niter=7, nls=5, precond=4))
+    b = FieldMapBatch([(v.nx, v.ny, v.nz, v.ncoil, v.necho) for v in vols], precision="fp64", precond="ict",
+                      droptol=droptol)
+    keep = []
+    for k, v in enumerate(vols):
+        y, s, m = dev_inputs(v, "fp64")
+        keep.append((y, s, m))
+        b.set_data(k, y, s, v.te, m, v.beta)
+    ws, costs = b.solve(niter=7)
+    for k in range(len(vols)):
+        np.testing.assert_allclose(costs[k], refs[k]["cost"], rtol=1e-10)
+        np.testing.assert_allclose(to_np(ws[k]), refs[k]["w"], rtol=0, atol=1e-9)
+    b.close()
