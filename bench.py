@@ -39,10 +39,11 @@ if ROOT not in sys.path:
 # kernel), from one ncu capture of the full workload (its summary sits with the committed
 # profiles); an entry is removed when its kernel changes.
 NCU_TRAFFIC_BYTES = {
-    ("full", "ls"): 1944679296 + 164864,
-    ("full", "grad"): 504675413 + 22891691,
-    ("full", "ic_bwd"): 134320896 + 16416768,
-    ("full", "dir"): 64362368 + 586240,
+    ("full", "ls"): 1944912384 + 101888,
+    ("full", "grad"): 504670208 + 21847424,
+    ("full", "ic_fwd"): 78444544 + 34418048,
+    ("full", "ic_bwd"): 134260480 + 16525056,
+    ("full", "dir"): 64357504 + 1170560,
 }
 
 WORKLOADS = {
