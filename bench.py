@@ -123,6 +123,9 @@ def data_eval_bytes(nc, L, literal, ts=4):
     return b
 
 
+HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal (the measured copy peak is the roofline)
+
+
 def peak_numbers(sm_max_mhz, nsm):
     peaks = {}
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -450,6 +453,7 @@ def run_ours(args, world, rank, local):
             tb = NCU_TRAFFIC_BYTES.get((args.workload, k))
             if tb:  # ncu DRAM bytes of one launch over its CUDA-event time, against the HBM peak
                 kernels[k]["hbm_traffic_frac"] = tb / (v[0] * 1e-3) / 1e9 / peaks["hbm_gbs"]
+                kernels[k]["hbm_traffic_frac_nominal"] = tb / (v[0] * 1e-3) / 1e9 / HBM_NOMINAL_GBS
 
     # time to the oracle's final cost on the small workload (stored by tests/golden/make_golden.py)
     ttc = None
