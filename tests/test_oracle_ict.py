@@ -147,3 +147,23 @@ def test_solve_with_the_papers_tolerance_is_monotone_and_beats_the_start():
     assert c[-1] < c[0]
     ic0 = o.solve(niter=12, precond=0)["cost"]
     assert abs(c[-1] - ic0[-1]) <= 1e-3 * abs(ic0[0] - ic0[-1])  # same minimiser reached
+
+
+def test_tolerance_between_fill_and_ic0_entries_gives_the_ic0_factor():
+    """With the data dominating H, every would-be fill entry is far smaller than every entry of
+    IC(0)'s factor; a tolerance between the two drops all fill and nothing else, so the
+    threshold factor equals the generic IC(0) factor (a separate routine of the oracle)."""
+    from oracle import ic0_factor
+    shape, mask, d, beta = _case(seed=40, shape=(6, 5, 7), lo=50.0, hi=100.0, beta=0.3, hole=0.2)
+    colptr0, rowidx0, val0, umap0 = ic0_factor(shape, mask, d, beta)
+    L0 = _L_sparse(colptr0, rowidx0, val0).toarray()
+    off = np.abs(L0[np.tril(np.ones(L0.shape, bool), -1) & (L0 != 0.0)])
+    # largest would-be fill entry: beta^2 / (pi_k sqrt(pi_j)) < beta^2 / min(H)^1.5
+    fill_bound = beta ** 2 / d[mask > 0].min() ** 1.5
+    assert fill_bound < 0.5 * off.min()
+    tau = 0.5 * (fill_bound + off.min())
+    colptr, rowidx, val, umap = ict_factor(shape, mask, d, beta, tau)
+    np.testing.assert_array_equal(umap, umap0)
+    np.testing.assert_array_equal(colptr, colptr0)
+    np.testing.assert_array_equal(rowidx, rowidx0)
+    np.testing.assert_allclose(val, val0, rtol=1e-14, atol=0)
