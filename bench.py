@@ -303,7 +303,7 @@ def run_ours(args, world, rank, local):
     nv = vol.nvox
     nmask = int(vol.mask.sum())
     fm = FieldMap(vol.nx, vol.ny, vol.nz, ncoil=vol.ncoil, necho=vol.necho, precision=prec, device=local,
-                  stream=stream)
+                  stream=stream, curvature=args.curvature)
     fm.set_profiling(True)
     w = torch.empty(vol.mask.shape, dtype=rd, device=dev)
     w_h = torch.empty(vol.mask.shape, dtype=rd).pin_memory()
@@ -415,7 +415,7 @@ def run_ours(args, world, rank, local):
     peaks = peak_numbers(sm_max, nsm)
     per_iter = {k: v[0] for k, v in kt.items() if v[1] > 0}
     dom = max(per_iter, key=per_iter.get) if per_iter else None
-    literal = vol.ncoil > 1
+    literal = vol.ncoil > 1 and args.curvature == "literal"
     def kernel_roofline(name, ms):
         """Algorithmic work of one launch of kernel class `name` against its bound."""
         evals = {"grad": 1, "ls": 4}.get(name, 0)
@@ -466,7 +466,7 @@ def run_ours(args, world, rank, local):
         w32, c32 = fm.solve(None, niter=niter)
         w32 = w32.double()
         ref = FieldMap(vol.nx, vol.ny, vol.nz, ncoil=vol.ncoil, necho=vol.necho, precision="fp64", device=local,
-                       stream=stream)
+                       stream=stream, curvature=args.curvature)
         ref.set_data(y_d.to(torch.complex128), s_d.to(torch.complex128) if s_d is not None else None, vol.te, m_d,
                      vol.beta)
         if wf:
@@ -505,6 +505,7 @@ def run_ours(args, world, rank, local):
             "config": {"workload": WORKLOADS[args.workload]["desc"], "voxels": nv, "mask_voxels": nmask,
                        "niter": niter, "nls": 5, "precision": ("fp32 voxel arithmetic, fp64 reductions and IC "
                                                                "pivots" if prec == "fp32" else "fp64"),
+                       "curvature": args.curvature,
                        "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (2.1 GB streamed per step)",
                        "masked_voxel_iters_per_s": world * nmask * niter / t_step},
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "kernels": kernels, "clocks": clk,
@@ -841,6 +842,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="full")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--curvature", choices=["literal", "combined"], default="literal",
+                    help="Huber curvature over every (c, d, m, n) term (the paper's) or from the "
+                         "coil-combined pair weights (labelled variant, HBM-bound)")
     ap.add_argument("--niter", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

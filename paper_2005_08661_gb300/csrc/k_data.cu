@@ -314,15 +314,52 @@ __global__ void __launch_bounds__(kThreads) k_ls(DataArgs a) {
         const T aT = (T)alpha;
         // each thread sums its few voxels in the voxel type, then the block and the grid in FP64
         T t1 = 0, t2 = 0;
-        for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nm;
-             k += (long long)gridDim.x * blockDim.x) {
-            const long long j = a.vlist[k];
-            const T zj = z[j];
-            if (zj == T(0)) continue;
-            T cst, gr, cu;
-            eval_any<T, NC, false, true>(a, k, w[j] + aT * zj, cst, gr, cu);
-            t1 += zj * gr;
-            t2 += zj * zj * cu;
+        if (NC == 1) {
+            // HBM-bound form (one coil, or the combined curvature): four voxels per pass with
+            // every load issued before the arithmetic, while all four exist; the rest one by
+            // one.  The voxels are visited in the same order as below, and a voxel with z = 0
+            // adds exactly 0 whether or not it is evaluated, so the sums are unchanged.
+            constexpr int U = 4;
+            const long long stride = (long long)gridDim.x * blockDim.x;
+            long long k0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+            for (; k0 + (U - 1) * stride < nm; k0 += U * stride) {
+                long long jj[U];
+                T zz[U], ww[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) jj[u] = a.vlist[k0 + u * stride];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    zz[u] = z[jj[u]];
+                    ww[u] = w[jj[u]];
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    T cst, gr, cu;
+                    eval_any<T, NC, false, true>(a, k0 + u * stride, ww[u] + aT * zz[u], cst, gr, cu);
+                    t1 += zz[u] * gr;
+                    t2 += zz[u] * zz[u] * cu;
+                }
+            }
+            for (long long k = k0; k < nm; k += stride) {
+                const long long j = a.vlist[k];
+                const T zj = z[j];
+                if (zj == T(0)) continue;
+                T cst, gr, cu;
+                eval_any<T, NC, false, true>(a, k, w[j] + aT * zj, cst, gr, cu);
+                t1 += zj * gr;
+                t2 += zj * zj * cu;
+            }
+        } else {
+            for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nm;
+                 k += (long long)gridDim.x * blockDim.x) {
+                const long long j = a.vlist[k];
+                const T zj = z[j];
+                if (zj == T(0)) continue;
+                T cst, gr, cu;
+                eval_any<T, NC, false, true>(a, k, w[j] + aT * zj, cst, gr, cu);
+                t1 += zj * gr;
+                t2 += zj * zj * cu;
+            }
         }
         double v[2] = {(double)t1, (double)t2};
         block_sum<2>(v, sbuf);
