@@ -81,3 +81,30 @@ def test_binding_refuses_to_run_without_the_library(tmp_path):
     from paper_2005_08661_gb300 import load_library
     with pytest.raises(RuntimeError, match="not built"):
         load_library(str(tmp_path / "libfm.so"))
+
+
+def test_opts_struct_layout_matches_the_header(lib):
+    """The ctypes mirror of fm_opts has the C struct's size and field offsets (compiled from
+    include/fm.h by the host C compiler), and a bad drop tolerance is refused up front."""
+    import subprocess
+    from paper_2005_08661_gb300 import FmOpts, FM_ERR_ARG
+    fields = [f for f, _ in FmOpts._fields_]
+    out_dir = os.path.join(ROOT, "paper_2005_08661_gb300", "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    src, exe = os.path.join(out_dir, "opts_layout.c"), os.path.join(out_dir, "opts_layout")
+    body = "".join(f'    printf(" %zu", offsetof(fm_opts, {f}));\n' for f in fields)
+    with open(src, "w") as fh:
+        fh.write("#include <stddef.h>\n#include <stdio.h>\n#include \"fm.h\"\n"
+                 "int main(void) {\n    printf(\"%zu\", sizeof(fm_opts));\n" + body + "    return 0;\n}\n")
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), src, "-o", exe])
+    vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
+    assert vals[0] == C.sizeof(FmOpts)
+    assert vals[1:] == [getattr(FmOpts, f).offset for f in fields]
+    o = FmOpts()
+    lib.fm_default_opts(C.byref(o))
+    assert o.droptol == 1e-3
+    h = C.c_void_p()
+    for bad in (-1e-3, float("nan"), float("inf")):
+        o.precond, o.droptol = 4, bad
+        assert lib.fm_create(C.byref(h), 4, 4, 4, 1, 3, C.byref(o), 0, None) == FM_ERR_ARG
+    assert h.value is None
