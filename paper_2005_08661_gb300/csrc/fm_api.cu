@@ -639,7 +639,7 @@ bool valid_opts(const fm_opts& o) {
            (o.precond == FM_PC_IC0 || o.precond == FM_PC_DIAG || o.precond == FM_PC_NONE || o.precond == FM_PC_RB ||
             o.precond == FM_PC_ICT) &&
            (o.curvature == FM_CURV_LITERAL || o.curvature == FM_CURV_COMBINED) && o.spin_limit >= 1 &&
-           std::isfinite(o.droptol) && o.droptol >= 0.0;
+           (o.precond != FM_PC_ICT || (std::isfinite(o.droptol) && o.droptol >= 0.0));
 }
 
 }  // namespace

@@ -108,3 +108,16 @@ def test_opts_struct_layout_matches_the_header(lib):
         o.precond, o.droptol = 4, bad
         assert lib.fm_create(C.byref(h), 4, 4, 4, 1, 3, C.byref(o), 0, None) == FM_ERR_ARG
     assert h.value is None
+
+
+def test_drop_tolerance_is_only_checked_where_it_applies(lib):
+    """fm_opts.droptol is read by FM_PC_ICT only: another preconditioner ignores its value."""
+    from paper_2005_08661_gb300 import FmOpts, FM_ERR_ARG
+    o = FmOpts()
+    lib.fm_default_opts(C.byref(o))
+    o.precond, o.droptol = 0, float("nan")
+    h = C.c_void_p()
+    # argument checks pass; creation then needs a GPU, so only "not an argument error" is checked
+    assert lib.fm_create(C.byref(h), 4, 4, 4, 1, 3, C.byref(o), 0, None) != FM_ERR_ARG
+    if h.value:
+        lib.fm_destroy(h)
