@@ -212,8 +212,9 @@ def barrier(world):
 
 # ------------------------------------------------------------------ oracle (CPU baseline / reference arm)
 
-def oracle_sample(vol, iters):
-    """Time the FP64 oracle, single-threaded, on a centred sub-volume; returns (seconds, units)."""
+def oracle_sample(vol, iters, curvature="literal"):
+    """Time the FP64 oracle, single-threaded, on a centred sub-volume; returns (seconds, units).
+    curvature "combined" selects the oracle's coil-combined curvature (the labelled variant)."""
     from oracle import Oracle, wf_gamma
     sub = sub_volume(vol, CPU_SAMPLE)
     if "fat_amps" in sub.meta:  # water-fat: the sweep + PWLS start, then the timed NCG iterations
@@ -229,6 +230,8 @@ def oracle_sample(vol, iters):
         return dt, sub.nvox * iters
     t0 = time.perf_counter()
     o = Oracle.from_volume(sub)
+    if curvature == "combined":
+        o.set_curvature("combined")
     o.solve(niter=iters, nls=5)
     dt = time.perf_counter() - t0
     o.close()
@@ -252,13 +255,13 @@ def run_reference(args, world, rank):
         return 0
     vol = make_workload(args.workload)
     sample = (f"FP64 C oracle, 1 thread, 1 NCG-MLS-IC(0) iteration (N_ls=5) per step on the centred "
-              f"{CPU_SAMPLE[0]}x{CPU_SAMPLE[1]}x{CPU_SAMPLE[2]} sub-volume of the workload ({vol.ncoil} coils), "
-              f"host {cpu_desc()}, nproc {os.cpu_count()}")
+              f"{CPU_SAMPLE[0]}x{CPU_SAMPLE[1]}x{CPU_SAMPLE[2]} sub-volume of the workload ({vol.ncoil} coils, "
+              f"{args.curvature} curvature), host {cpu_desc()}, nproc {os.cpu_count()}")
     for _ in range(args.warmup):
-        oracle_sample(vol, 1)
+        oracle_sample(vol, 1, args.curvature)
     times, units = [], 0
     for _ in range(args.steps):
-        dt, u = oracle_sample(vol, 1)
+        dt, u = oracle_sample(vol, 1, args.curvature)
         times.append(dt)
         units = u
     t = sum(times) / len(times)
@@ -489,11 +492,12 @@ def run_ours(args, world, rank, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, units = oracle_sample(vol, 4)
+        dt, units = oracle_sample(vol, 4, args.curvature)
         cpu = {"value": units / dt, "unit": "voxel-iter/s", "cores": 1, "kind": "oracle",
                "sample": f"FP64 C oracle, 1 thread, 4 NCG-MLS-IC(0) iterations (N_ls=5) on the centred "
                          f"{CPU_SAMPLE[0]}x{CPU_SAMPLE[1]}x{CPU_SAMPLE[2]} sub-volume of the workload "
-                         f"({vol.ncoil} coils), {dt:.1f} s, host {cpu_desc()}, nproc {os.cpu_count()}"}
+                         f"({vol.ncoil} coils, {args.curvature} curvature), {dt:.1f} s, host {cpu_desc()}, "
+                         f"nproc {os.cpu_count()}"}
 
     # per step: mask count, chunk scan, setup; 5 kernels per outer iteration; the final update
     # (water-fat adds the sweep, the PWLS start and 2 kernels per PWLS iteration, the amplitudes)
