@@ -257,3 +257,39 @@ def test_combined_curvature_variant_matches_oracle(prec):
         _, cost = fm.solve(niter=6)
         np.testing.assert_allclose(cost, r["cost"], rtol=1e-10)
     fm.close()
+
+
+def test_non_finite_input_inside_the_mask_is_reported_and_outside_is_ignored():
+    """A NaN image value at a mask voxel makes the cost constant non-finite: the next
+    synchronising call reports FM_ERR_NONFINITE.  Outside the mask the images are never read."""
+    from paper_2005_08661_gb300 import FmError, FM_ERR_NONFINITE
+    vol = make_volume(12, 10, 6, ncoil=2, snr_db=20.0, seed=77, fmax_hz=100.0, nblobs=2)
+    out = np.argwhere(vol.mask == 0)[0]
+    vol.y[0, 0, out[0], out[1], out[2]] = np.nan
+    fm = open_fm(vol, "fp64")
+    w = fm.init_omega()
+    cost, _, _ = fm.cost_grad(w)
+    assert np.isfinite(cost)
+    fm.close()
+    inside = np.argwhere(vol.mask > 0)[0]
+    vol.y[1, 1, inside[0], inside[1], inside[2]] = np.nan
+    fm = open_fm(vol, "fp64")
+    with pytest.raises(FmError) as e:
+        fm.cost_grad(fm.init_omega())
+    assert e.value.status == FM_ERR_NONFINITE
+    fm.close()
+
+
+def test_voxels_without_coil_sensitivity_carry_no_data_term():
+    """S_j = 0 (every coil sensitivity zero at a mask voxel): r = 0 there (reading of Eq. 3),
+    so only the regulariser acts; the FP64 solve still matches the oracle per iteration."""
+    vol = make_volume(14, 12, 7, ncoil=2, snr_db=20.0, seed=78, fmax_hz=100.0, nblobs=2)
+    inside = np.argwhere(vol.mask > 0)
+    for z, y, x in inside[len(inside) // 2: len(inside) // 2 + 5]:
+        vol.smap[:, z, y, x] = 0.0
+    ref = Oracle.from_volume(vol).solve(niter=10, nls=5)
+    fm = open_fm(vol, "fp64")
+    w, cost = fm.solve(niter=10)
+    np.testing.assert_allclose(cost, ref["cost"], rtol=1e-10)
+    np.testing.assert_allclose(to_np(w), ref["w"], rtol=0, atol=1e-9)
+    fm.close()
