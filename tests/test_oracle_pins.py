@@ -408,3 +408,23 @@ def test_combined_curvature_is_tighter_and_equal_for_one_coil():
         else:
             assert np.all(comb <= lit * (1 + 1e-12) + 1e-14)
             assert np.any(comb < lit * (1 - 1e-6))
+
+
+def test_noise_free_minimisers_repeat_with_the_gcd_of_the_echo_spacings():
+    """Noise-free data: Phi_j vanishes exactly on w_true + k 2 pi / gcd(t_m - t_n) and only
+    there (echoes 0/2/10 ms: spacings 2, 10, 8, gcd 2, period pi rad/ms)."""
+    rng = np.random.default_rng(17)
+    te = np.array([0.0, 2.0, 10.0])
+    for nc in (1, 3):
+        s = _rand_c(rng, nc) if nc > 1 else None
+        sv = s if s is not None else np.ones(1)
+        x = complex(rng.standard_normal(), rng.standard_normal())
+        w_true = float(rng.uniform(-1.0, 1.0))
+        y = (np.exp(1j * w_true * te)[:, None] * sv[None, :] * x).astype(np.complex128)
+        period = 2 * np.pi / 2.0
+        for k in (-3, -1, 0, 1, 2):
+            assert abs(voxel_terms(te, y, s, w_true + k * period)[0]) <= 1e-11 * abs(x) ** 2
+        grid = w_true + np.linspace(-period, period, 401)[1:-1]
+        off = np.abs(((grid - w_true) / period) - np.rint((grid - w_true) / period)) > 1e-3
+        vals = np.array([voxel_terms(te, y, s, w)[0] for w in grid[off]])
+        assert vals.min() > 1e-9 * abs(x) ** 2
