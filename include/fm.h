@@ -218,6 +218,14 @@ FM_API int fm_set_fat_model(fm_ctx *ctx, int npeak, const double *rel_amp, const
 FM_API int fm_wf_sweep(fm_ctx *ctx, int nsweep, double w_lo, double w_hi, void *omega_tilde);
 
 /*
+ * The paper's sweep range for fm_wf_sweep under the current fat model (Sec. III-A:
+ * [-|Delta_f / 2|, |Delta_f / 2|]), with Delta_f read as the frequency of the fat peak of
+ * largest relative amplitude (the first such peak on a tie): *w_lo = -pi |f|, *w_hi = pi |f|
+ * in rad per unit of te.  Errors: FM_ERR_ARG (NULL pointers), FM_ERR_STATE (no fat model).
+ */
+FM_API int fm_wf_sweep_range(const fm_ctx *ctx, double *w_lo, double *w_hi);
+
+/*
  * PWLS initialisation (Eq. w0_wf): niter conjugate-gradient iterations (no preconditioner;
  * the paper uses 10) on (2 diag(rho) + beta C'C) w = 2 rho omega_tilde, starting from
  * omega_tilde, with rho_j = sum_{c,d,m,n} |r_cdmnj| from fm_set_data.  omega_tilde, omega0:
@@ -332,6 +340,13 @@ FM_API fm_ctx *fm_batch_ctx(fm_batch *b, int k);
 /* Release the batch and its contexts.  NULL-safe. */
 FM_API int fm_batch_destroy(fm_batch *b);
 
+/*
+ * Change the bound on device-side waits (fm_opts.spin_limit) of an existing context, >= 1.
+ * A wait that exceeds it gives up with FM_ERR_TIMEOUT; the context stays usable and the
+ * next call starts from a clean barrier state.  Errors: FM_ERR_ARG.
+ */
+FM_API int fm_set_spin_limit(fm_ctx *ctx, long long spin_limit);
+
 /* Kernel classes timed by fm_kernel_times. */
 #define FM_K_GRAD 0   /* data term + stencil gradient pass (fused update of the previous step) */
 #define FM_K_IC_FWD 1 /* IC(0) pivots + forward substitution wavefront */
@@ -373,10 +388,14 @@ FM_API int fm_kernel_times(fm_ctx *ctx, double *avg_ms, int *count);
  * library keeps until the process exits.  Limit: nx*ny*nz <= 67,108,864 voxels
  * (16,384 blocks of 4,096 voxels); larger volumes return FM_ERR_SIZE before any device
  * work.  The first call on a device looks up that array's device address (once per
- * device); make that first call before any stream capture.  Every call reuses the same
- * array and clears its counter at the start, so calls whose kernels overlap on the GPU
- * (different streams or threads without ordering) race and must not be issued.
- * Errors: FM_ERR_ARG, FM_ERR_SIZE, FM_ERR_CUDA.
+ * device); make that first call before any stream capture.  The address is kept for the
+ * life of the process, so cudaDeviceReset between calls is not supported (the array may
+ * move when the library's module is loaded again).  Every call reuses the same array and
+ * clears its counter at the start, so calls whose kernels overlap on the GPU (different
+ * streams or threads without ordering) race and must not be issued.
+ * Errors: FM_ERR_ARG, FM_ERR_SIZE, FM_ERR_CUDA, FM_ERR_NONFINITE (cost requested and not
+ * finite, as fm_cost_grad reports a non-finite value inside the mask; the outputs are
+ * still written).
  */
 FM_API int fm_cost_grad_noalloc(int nx, int ny, int nz, int ncoil, int necho, const fm_opts *opts,
                                 const void *y, const void *smap, const double *te, const uint8_t *mask,

@@ -115,6 +115,17 @@ void free_all(fm_ctx* c) {
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
+// Clear the device error word and the grid barrier's arrival count.  A block that gives up
+// in grid_barrier (FM_ERR_TIMEOUT) leaves its arrival counted; if the count survived into the
+// next launch sequence, a later barrier would open before every block had arrived.  So
+// every launch sequence starts from a zero count, and an error read back clears it too
+// (stream-ordered after the launch that timed out has finished).
+cudaError_t reset_dev(fm_ctx* c) {
+    cudaError_t e = cudaMemsetAsync(c->istate + I_ERR, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->istate + I_BAR_COUNT, 0, sizeof(int), c->stream);
+    return e;
+}
+
 // Read back the device error word and clear it.
 int check_dev(fm_ctx* c) {
     int e = 0;
@@ -122,7 +133,7 @@ int check_dev(fm_ctx* c) {
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "synchronise");
     if (e != 0) {
-        cudaMemsetAsync(c->istate + I_ERR, 0, sizeof(int), c->stream);
+        reset_dev(c);
         const char* what = e == FM_ERR_NOT_PD ? "IC(0) pivot <= 0 (H not positive definite on the mask)"
                          : e == FM_ERR_TIMEOUT ? "device-side wait exceeded spin_limit"
                          : e == FM_ERR_NONFINITE ? "non-finite global reduction"
@@ -375,7 +386,7 @@ int solve_begin(fm_ctx* c, void* omega, int init, int niter) {
     }
     const size_t vb = (size_t)c->nv * c->ts;
     cudaStream_t s = c->stream;
-    FM_CK(cudaMemsetAsync(c->istate + I_ERR, 0, sizeof(int), s), "reset");
+    FM_CK(reset_dev(c), "reset");
     // the kernels write mask voxels only: every entry outside the mask starts (and stays) 0
     if (init) {
         FM_CK(cudaMemcpyAsync(c->w[0], c->w0, vb, cudaMemcpyDeviceToDevice, s), "copy omega");
@@ -486,7 +497,7 @@ int adjoint_t(fm_ctx* c, const void* w_hat, const void* rhs, void* lambda, doubl
     cudaStream_t s = c->stream;
     const size_t vb = (size_t)c->nv * c->ts;
     const double tol2 = tol * tol;
-    FM_CK(cudaMemsetAsync(c->istate + I_ERR, 0, sizeof(int), s), "reset");
+    FM_CK(reset_dev(c), "reset");
     // majoriser curvature d(w_hat) for the preconditioner (Eq. 9-12)
     FM_CK(run_grad<T>(c, w_hat, nullptr, c->w[1], c->g[1], c->d, nullptr), "curvature");
     void* zero[] = {c->w[0], c->g[0], c->z[0], c->z[1], c->g[1]};
@@ -553,7 +564,7 @@ int implicit_t(fm_ctx* c, const void* y, const void* smap, const void* w_hat, co
     a.y = y;
     a.smap = smap;
     a.dldy = dl_dy;
-    FM_CK(cudaMemsetAsync(c->istate + I_ERR, 0, sizeof(int), c->stream), "reset");
+    FM_CK(reset_dev(c), "reset");
     if (dl_dy) FM_CK(launch_dldy<T>(a, c->grid_data, c->stream), "image derivative kernel");
     if (dl_dbeta) {
         FM_CK(launch_lap_dot<T>(a, c->grid_data, c->stream), "beta derivative kernel");
@@ -597,7 +608,7 @@ template <typename T>
 int pwls_t(fm_ctx* c, const void* wt, int niter, void* w0) {
     cudaStream_t s = c->stream;
     const size_t vb = (size_t)c->nv * c->ts;
-    FM_CK(cudaMemsetAsync(c->istate + I_ERR, 0, sizeof(int), s), "reset");
+    FM_CK(reset_dev(c), "reset");
     void* zero[] = {c->w[0], c->g[0], c->z[0], c->z[1], c->g[1]};
     for (void* b : zero) FM_CK(cudaMemsetAsync(b, 0, vb, s), "clear CG vectors");
     AdjArgs a = adj_args(c);
@@ -922,6 +933,7 @@ int fm_ic_factor(fm_ctx* c, const void* omega, void* inv_pivot) {
     if (!c->have_data) return fail(c, FM_ERR_STATE, "fm_set_data first");
     DevGuard guard(c->device);
     const bool f64 = c->o.precision == FM_FP64;
+    FM_CK(cudaMemsetAsync(c->istate + I_BAR_COUNT, 0, sizeof(int), c->stream), "reset barrier");
     cudaError_t e = f64 ? run_grad<double>(c, omega, nullptr, c->w[0], c->g[0], c->d, nullptr)
                         : run_grad<float>(c, omega, nullptr, c->w[0], c->g[0], c->d, nullptr);
     if (e != cudaSuccess) return cuda_fail(c, e, "gradient kernel");
@@ -949,6 +961,7 @@ int fm_ic_apply(fm_ctx* c, const void* g, void* p) {
     if (!g || !p || g == p) return fail(c, FM_ERR_ARG, "g and p must be distinct device arrays");
     if (!c->have_factor) return fail(c, FM_ERR_STATE, "fm_ic_factor first");
     DevGuard guard(c->device);
+    FM_CK(cudaMemsetAsync(c->istate + I_BAR_COUNT, 0, sizeof(int), c->stream), "reset barrier");
     cudaError_t e;
     if (c->o.precond == FM_PC_RB) {
         DataArgs a = base_args(c);
@@ -1056,6 +1069,20 @@ int fm_wf_sweep(fm_ctx* c, int nsweep, double w_lo, double w_hi, void* omega_til
     return FM_OK;
 }
 
+int fm_wf_sweep_range(const fm_ctx* c, double* w_lo, double* w_hi) {
+    if (!c || !w_lo || !w_hi) return FM_ERR_ARG;
+    if (!c->wf || c->fat_amp.empty()) return FM_ERR_STATE;
+    // reading of Sec. III-A's |Delta_f|: the frequency of the largest-amplitude fat peak (the
+    // first one on a tie); the half-width |Delta_f / 2| in cycles is pi |f| in radians
+    size_t q = 0;
+    for (size_t k = 1; k < c->fat_amp.size(); ++k)
+        if (c->fat_amp[k] > c->fat_amp[q]) q = k;
+    const double half = 3.14159265358979323846264338327950 * std::fabs(c->fat_freq[q]);
+    *w_lo = -half;
+    *w_hi = half;
+    return FM_OK;
+}
+
 int fm_pwls_init(fm_ctx* c, const void* omega_tilde, int niter, void* omega0) {
     if (!c) return FM_ERR_ARG;
     if (!omega_tilde || !omega0) return fail(c, FM_ERR_ARG, "omega_tilde and omega0 are required");
@@ -1082,6 +1109,17 @@ int fm_wf_amplitudes(fm_ctx* c, const void* y, const void* smap, const void* ome
     cudaError_t e = c->o.precision == FM_FP64 ? launch_wf_amp<double>(a, c->grid_data, c->stream)
                                               : launch_wf_amp<float>(a, c->grid_data, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "amplitude kernel");
+    return FM_OK;
+}
+
+int fm_set_spin_limit(fm_ctx* c, long long spin_limit) {
+    if (!c) return FM_ERR_ARG;
+    if (spin_limit < 1) return fail(c, FM_ERR_ARG, "spin_limit must be >= 1");
+    DevGuard guard(c->device);
+    c->o.spin_limit = spin_limit;
+    // the limit is a kernel argument of the captured graphs
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    if (c->cg_gexec) { cudaGraphExecDestroy(c->cg_gexec); c->cg_gexec = nullptr; }
     return FM_OK;
 }
 

@@ -254,6 +254,8 @@ extern "C" int fm_cost_grad_noalloc(int nx, int ny, int nz, int ncoil, int necho
     if (e == cudaSuccess && cost) {
         e = cudaMemcpyAsync(cost, &scr->result, sizeof(double), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        // as fm_cost_grad: a non-finite input inside the mask makes the cost non-finite
+        if (e == cudaSuccess && !(*cost - *cost == 0.0)) rc = FM_ERR_NONFINITE;
     }
     if (e != cudaSuccess) rc = FM_ERR_CUDA;
     if (prev >= 0 && prev != device) cudaSetDevice(prev);

@@ -120,7 +120,7 @@ __device__ __forceinline__ double rsqrt_nr(double s) {
 __device__ __forceinline__ double ld_level(const double* p) { return gridDim.x == 1 ? *p : __ldcg(p); }
 
 // Separates two levels: a block barrier when one block holds every column, else the
-// bounded grid barrier (every block is resident: the grid is sized by occupancy).
+// bounded grid barrier (every block is resident: cooperative launch, grid sized by occupancy).
 __device__ __forceinline__ bool level_sync(const IctArgs& a) {
     if (gridDim.x == 1) {
         __syncthreads();
@@ -319,15 +319,20 @@ cudaError_t launch_ict_tau(const DataArgs& a, double droptol, int grid, cudaStre
     k_ict_tau<T><<<grid, kThreads, 0, s>>>(a, droptol);
     return cudaGetLastError();
 }
+// The level sweeps wait at a grid barrier, so every block must be resident at once.  A
+// cooperative launch guarantees that (or refuses the launch) even when other kernels run
+// beside the sweep, e.g. the other volumes' branches of a batched graph.
 template <typename T>
 cudaError_t launch_ict_fwd(const IctArgs& a, int grid, int block, cudaStream_t s) {
-    k_ict_fwd<T><<<grid, block, 0, s>>>(a);
-    return cudaGetLastError();
+    IctArgs copy = a;
+    void* args[] = {&copy};
+    return cudaLaunchCooperativeKernel((const void*)k_ict_fwd<T>, dim3(grid), dim3(block), args, 0, s);
 }
 template <typename T>
 cudaError_t launch_ict_bwd(const IctArgs& a, int grid, int block, cudaStream_t s) {
-    k_ict_bwd<T><<<grid, block, 0, s>>>(a);
-    return cudaGetLastError();
+    IctArgs copy = a;
+    void* args[] = {&copy};
+    return cudaLaunchCooperativeKernel((const void*)k_ict_bwd<T>, dim3(grid), dim3(block), args, 0, s);
 }
 template <typename T>
 cudaError_t launch_ict_check(const IctArgs& a, int grid, cudaStream_t s) {

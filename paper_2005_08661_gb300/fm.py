@@ -46,7 +46,7 @@ EXPORTS = ["fm_default_opts", "fm_create", "fm_set_data", "fm_init_omega", "fm_c
            "fm_batch_solve", "fm_batch_autotune", "fm_batch_set_fraction", "fm_batch_ctx", "fm_batch_destroy",
            "fm_batch_schedule",
            "fm_true_curv", "fm_adjoint_solve", "fm_implicit_grad", "fm_set_fat_model", "fm_wf_sweep",
-           "fm_pwls_init", "fm_wf_amplitudes"]
+           "fm_pwls_init", "fm_wf_amplitudes", "fm_wf_sweep_range", "fm_set_spin_limit"]
 KERNELS = ["grad", "ic_fwd", "ic_bwd", "dir", "ls"]
 
 
@@ -92,8 +92,10 @@ def load_library(path=None):
         lib.fm_wf_sweep.argtypes = [vp, i, d, d, vp]
         lib.fm_pwls_init.argtypes = [vp, vp, i, vp]
         lib.fm_wf_amplitudes.argtypes = [vp, vp, vp, vp, vp, vp]
+        lib.fm_wf_sweep_range.argtypes = [vp, C.POINTER(d), C.POINTER(d)]
+        lib.fm_set_spin_limit.argtypes = [vp, C.c_longlong]
         for fn in ("fm_true_curv", "fm_adjoint_solve", "fm_implicit_grad", "fm_set_fat_model", "fm_wf_sweep",
-                   "fm_pwls_init", "fm_wf_amplitudes"):
+                   "fm_pwls_init", "fm_wf_amplitudes", "fm_wf_sweep_range", "fm_set_spin_limit"):
             getattr(lib, fn).restype = C.c_int
         lib.fm_batch_create.argtypes = [C.POINTER(vp), i, C.POINTER(i), C.POINTER(FmOpts), i, vp]
         lib.fm_batch_set_data.argtypes = [vp, i, vp, vp, C.POINTER(d), vp, d]
@@ -236,13 +238,17 @@ class FieldMap:
         self._check(self.lib.fm_set_fat_model(self._h, n, a, f), "fm_set_fat_model")
         self.fat_model = (tuple(amps), tuple(freqs)) if n else None
 
+    def wf_sweep_range(self):
+        """The library's default sweep range (fm_wf_sweep_range) for the current fat model."""
+        lo, hi = C.c_double(), C.c_double()
+        self._check(self.lib.fm_wf_sweep_range(self._h, C.byref(lo), C.byref(hi)), "fm_wf_sweep_range")
+        return lo.value, hi.value
+
     def wf_sweep(self, nsweep=100, w_lo=None, w_hi=None, out=None):
-        """Voxel-wise sweep initialisation; the default range is +-pi |f| of the largest fat peak
-        (+-|Delta_f / 2| in rad per unit of te)."""
+        """Voxel-wise sweep initialisation; the default range is the library's
+        (fm_wf_sweep_range)."""
         if w_lo is None or w_hi is None:
-            amps, freqs = self.fat_model
-            half = float(np.pi * abs(freqs[int(np.argmax(amps))]))
-            w_lo, w_hi = -half, half
+            w_lo, w_hi = self.wf_sweep_range()
         out = self.empty() if out is None else self._vec(out, "out")
         self._check(self.lib.fm_wf_sweep(self._h, int(nsweep), float(w_lo), float(w_hi), _dptr(out)), "fm_wf_sweep")
         return out
@@ -326,6 +332,10 @@ class FieldMap:
         m = (C.c_double * max(n, 1))()
         self._check(self.lib.fm_get_history(self._h, a, m, int(n)), "fm_get_history")
         return np.array(a[:n]), np.array(m[:n])
+
+    def set_spin_limit(self, n):
+        """Bound on device-side waits (polls) for the following calls."""
+        self._check(self.lib.fm_set_spin_limit(self._h, int(n)), "fm_set_spin_limit")
 
     def set_profiling(self, on=True):
         self._check(self.lib.fm_set_profiling(self._h, 1 if on else 0), "fm_set_profiling")

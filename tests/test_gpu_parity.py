@@ -228,6 +228,27 @@ def test_wavefront_wait_limit_reports_timeout_and_the_device_stays_usable():
     fm.close()
 
 
+@pytest.mark.parametrize("precond,pc", [("ic0", 0), ("ict", 4)])
+def test_a_timed_out_solve_leaves_the_same_context_usable(precond, pc):
+    """A wait that gives up (spin_limit = 1: the IC tile flags, the line search's and the
+    drop-tolerance sweeps' grid barriers) leaves its barrier arrival counted; the next call
+    on the same context must start from a clean barrier, so a solve with the normal limit
+    then matches the oracle per iteration."""
+    from paper_2005_08661_gb300 import FmError, FM_ERR_TIMEOUT
+    vol = _vol(128, 96, 24, 1, seed=14, holes=False)
+    fm = open_fm(vol, "fp64", precond=precond)
+    fm.set_spin_limit(1)
+    with pytest.raises(FmError) as e:
+        fm.solve(niter=3)
+    assert e.value.status == FM_ERR_TIMEOUT
+    fm.set_spin_limit(1 << 21)
+    ref = Oracle.from_volume(vol).solve(niter=4, nls=5, precond=pc)
+    w, cost = fm.solve(niter=4)
+    np.testing.assert_allclose(cost, ref["cost"], rtol=1e-10)
+    np.testing.assert_allclose(to_np(w), ref["w"], rtol=0, atol=1e-9)
+    fm.close()
+
+
 def test_binding_rejects_wrong_dtypes():
     import torch
     vol = _vol(8, 8, 8, 1, holes=False)
