@@ -25,89 +25,107 @@ def lib_path():
     return os.path.join(_BUILD, "liboracle.so")
 
 
+def source_path():
+    return _SRC
+
+
+def compile_oracle(src, out):
+    """Compile a C source of the oracle (fm_oracle.c or a test's modified copy) into the shared
+    library out, with plain IEEE double semantics (no fused contractions)."""
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
+                           "-fno-fast-math", "-o", tmp, src, "-lm"])
+    os.replace(tmp, out)
+    return out
+
+
 def build_oracle(force=False):
-    """Compile fm_oracle.c with plain IEEE double semantics (no fused contractions)."""
+    """Compile fm_oracle.c into oracle/_build/liboracle.so unless it is up to date."""
     out = lib_path()
     if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
         return out
     os.makedirs(_BUILD, exist_ok=True)
-    tmp = out + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
-                           "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
-    os.replace(tmp, out)
-    return out
+    return compile_oracle(_SRC, out)
 
 
 def _lib():
     global _LIB
     with _LOCK:
-        if _LIB is not None:
-            return _LIB
-        lib = C.CDLL(build_oracle())
-        vp = C.c_void_p
-        lib.orc_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
-                                   _dp, vp, _dp, vp, C.c_double]
-        lib.orc_create.restype = C.c_int
-        lib.orc_destroy.argtypes = [vp]
-        for name in ("orc_phi", "orc_reg", "orc_cost"):
-            getattr(lib, name).argtypes = [vp, _dp]
-            getattr(lib, name).restype = C.c_double
-        for name in ("orc_grad", "orc_grad_phi", "orc_curv"):
-            getattr(lib, name).argtypes = [vp, _dp, _dp]
-            getattr(lib, name).restype = None
-        lib.orc_init.argtypes = [vp, _dp]
-        lib.orc_hess_diag.argtypes = [vp, _dp, _dp]
-        lib.orc_hess_diag.restype = None
-        lib.orc_dgrad_dy.argtypes = [vp, _dp, _dp, _dp]
-        lib.orc_dgrad_dy.restype = None
-        lib.orc_dgrad_dy_adj.argtypes = [vp, _dp, _dp, _dp]
-        lib.orc_dgrad_dy_adj.restype = None
-        lib.orc_set_gamma.argtypes = [vp, _dp]
-        lib.orc_set_gamma.restype = C.c_int
-        lib.orc_phi_vox.argtypes = [vp, _dp, _dp]
-        lib.orc_phi_vox.restype = None
-        lib.orc_rho.argtypes = [vp, _dp]
-        lib.orc_rho.restype = None
-        lib.orc_wf_sweep.argtypes = [vp, C.c_int, C.c_double, C.c_double, _dp]
-        lib.orc_wf_sweep.restype = None
-        lib.orc_pwls.argtypes = [vp, _dp, C.c_int, _dp]
-        lib.orc_pwls.restype = C.c_int
-        lib.orc_set_curvature.argtypes = [vp, C.c_int]
-        lib.orc_set_curvature.restype = None
-        lib.orc_num_unknowns.argtypes = [vp]
-        lib.orc_num_unknowns.restype = C.c_long
-        lib.orc_precondition.argtypes = [vp, _dp, _dp, _dp]
-        lib.orc_precondition.restype = C.c_int
-        lib.orc_solve.argtypes = [vp, _dp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp]
-        lib.orc_solve.restype = C.c_int
-        lib.orc_ic0.argtypes = [C.c_int, C.c_int, C.c_int, vp, _dp, C.c_double, _lp, _lp, _dp,
-                                _lp, C.POINTER(C.c_long), C.POINTER(C.c_long)]
-        lib.orc_ic0.restype = C.c_int
-        lib.orc_ic0_solve.argtypes = [C.c_long, _lp, _lp, _dp, _dp, _dp]
-        lib.orc_ic0_ordered.argtypes = [C.c_int, C.c_int, C.c_int, vp, _dp, C.c_double, C.c_int, _lp, _lp, _dp,
-                                        _lp, C.POINTER(C.c_long), C.POINTER(C.c_long)]
-        lib.orc_ic0_ordered.restype = C.c_int
-        lib.orc_precondition_ordered.argtypes = [vp, _dp, _dp, _dp, C.c_int]
-        lib.orc_precondition_ordered.restype = C.c_int
-        lpp = C.POINTER(C.POINTER(C.c_long))
-        dpp = C.POINTER(C.POINTER(C.c_double))
-        lib.orc_ict.argtypes = [C.c_int, C.c_int, C.c_int, vp, _dp, C.c_double, C.c_double, lpp, lpp, dpp, lpp,
-                                C.POINTER(C.c_long), C.POINTER(C.c_long)]
-        lib.orc_ict.restype = C.c_int
-        lib.orc_free.argtypes = [vp]
-        lib.orc_free.restype = None
-        lib.orc_hmax.argtypes = [vp, _dp]
-        lib.orc_hmax.restype = C.c_double
-        lib.orc_set_droptol.argtypes = [vp, C.c_double]
-        lib.orc_set_droptol.restype = None
-        lib.orc_precondition_ict.argtypes = [vp, _dp, _dp, _dp, C.c_double]
-        lib.orc_precondition_ict.restype = C.c_int
-        lib.orc_voxel.argtypes = [C.c_int, C.c_int, _dp, _dp, vp, C.c_double, _dp]
-        lib.orc_voxel.restype = C.c_int
-        lib.orc_voxel_r.argtypes = [C.c_int, C.c_int, _dp, vp, _dp, _dp]
-        lib.orc_voxel_r.restype = C.c_int
-        _LIB = lib
-        return lib
+        if _LIB is None:
+            _LIB = _declare(C.CDLL(build_oracle()))
+        return _LIB
+
+
+def load_oracle_variant(path):
+    """Load another build of fm_oracle.c (e.g. a copy with a planted mistake, compiled by a
+    test) with the same signatures; pass it to Oracle(..., lib=...)."""
+    return _declare(C.CDLL(path))
+
+
+def _declare(lib):
+    vp = C.c_void_p
+    lib.orc_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                               _dp, vp, _dp, vp, C.c_double]
+    lib.orc_create.restype = C.c_int
+    lib.orc_destroy.argtypes = [vp]
+    for name in ("orc_phi", "orc_reg", "orc_cost"):
+        getattr(lib, name).argtypes = [vp, _dp]
+        getattr(lib, name).restype = C.c_double
+    for name in ("orc_grad", "orc_grad_phi", "orc_curv"):
+        getattr(lib, name).argtypes = [vp, _dp, _dp]
+        getattr(lib, name).restype = None
+    lib.orc_init.argtypes = [vp, _dp]
+    lib.orc_hess_diag.argtypes = [vp, _dp, _dp]
+    lib.orc_hess_diag.restype = None
+    lib.orc_dgrad_dy.argtypes = [vp, _dp, _dp, _dp]
+    lib.orc_dgrad_dy.restype = None
+    lib.orc_dgrad_dy_adj.argtypes = [vp, _dp, _dp, _dp]
+    lib.orc_dgrad_dy_adj.restype = None
+    lib.orc_set_gamma.argtypes = [vp, _dp]
+    lib.orc_set_gamma.restype = C.c_int
+    lib.orc_phi_vox.argtypes = [vp, _dp, _dp]
+    lib.orc_phi_vox.restype = None
+    lib.orc_rho.argtypes = [vp, _dp]
+    lib.orc_rho.restype = None
+    lib.orc_wf_sweep.argtypes = [vp, C.c_int, C.c_double, C.c_double, _dp]
+    lib.orc_wf_sweep.restype = None
+    lib.orc_pwls.argtypes = [vp, _dp, C.c_int, _dp]
+    lib.orc_pwls.restype = C.c_int
+    lib.orc_set_curvature.argtypes = [vp, C.c_int]
+    lib.orc_set_curvature.restype = None
+    lib.orc_num_unknowns.argtypes = [vp]
+    lib.orc_num_unknowns.restype = C.c_long
+    lib.orc_precondition.argtypes = [vp, _dp, _dp, _dp]
+    lib.orc_precondition.restype = C.c_int
+    lib.orc_solve.argtypes = [vp, _dp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp]
+    lib.orc_solve.restype = C.c_int
+    lib.orc_ic0.argtypes = [C.c_int, C.c_int, C.c_int, vp, _dp, C.c_double, _lp, _lp, _dp,
+                            _lp, C.POINTER(C.c_long), C.POINTER(C.c_long)]
+    lib.orc_ic0.restype = C.c_int
+    lib.orc_ic0_solve.argtypes = [C.c_long, _lp, _lp, _dp, _dp, _dp]
+    lib.orc_ic0_ordered.argtypes = [C.c_int, C.c_int, C.c_int, vp, _dp, C.c_double, C.c_int, _lp, _lp, _dp,
+                                    _lp, C.POINTER(C.c_long), C.POINTER(C.c_long)]
+    lib.orc_ic0_ordered.restype = C.c_int
+    lib.orc_precondition_ordered.argtypes = [vp, _dp, _dp, _dp, C.c_int]
+    lib.orc_precondition_ordered.restype = C.c_int
+    lpp = C.POINTER(C.POINTER(C.c_long))
+    dpp = C.POINTER(C.POINTER(C.c_double))
+    lib.orc_ict.argtypes = [C.c_int, C.c_int, C.c_int, vp, _dp, C.c_double, C.c_double, lpp, lpp, dpp, lpp,
+                            C.POINTER(C.c_long), C.POINTER(C.c_long)]
+    lib.orc_ict.restype = C.c_int
+    lib.orc_free.argtypes = [vp]
+    lib.orc_free.restype = None
+    lib.orc_hmax.argtypes = [vp, _dp]
+    lib.orc_hmax.restype = C.c_double
+    lib.orc_set_droptol.argtypes = [vp, C.c_double]
+    lib.orc_set_droptol.restype = None
+    lib.orc_precondition_ict.argtypes = [vp, _dp, _dp, _dp, C.c_double]
+    lib.orc_precondition_ict.restype = C.c_int
+    lib.orc_voxel.argtypes = [C.c_int, C.c_int, _dp, _dp, vp, C.c_double, _dp]
+    lib.orc_voxel.restype = C.c_int
+    lib.orc_voxel_r.argtypes = [C.c_int, C.c_int, _dp, vp, _dp, _dp]
+    lib.orc_voxel_r.restype = C.c_int
+    return lib
 
 
 def _c128(a):
@@ -126,8 +144,8 @@ class Oracle:
     float64 arrays of the grid's shape.
     """
 
-    def __init__(self, y, smap, te, mask, beta):
-        lib = _lib()
+    def __init__(self, y, smap, te, mask, beta, lib=None):
+        lib = lib or _lib()
         y = np.asarray(y)
         L, nc, nz, ny, nx = y.shape
         self.shape = (nz, ny, nx)
