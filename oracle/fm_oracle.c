@@ -36,11 +36,74 @@
  *          mu^0 = 0, mu^i = (g^i - g^{i-1})'p^i / ((g^{i-1})'p^{i-1}); monotonic line
  *          search alpha_{k+1} = alpha_k - f'(alpha_k) / (d^(k) + beta ||C z||^2),
  *          d^(k) = sum_j z_j^2 d_j(w + alpha_k z), alpha_0 = 0, N_ls fixed steps.
- * All reductions are sequential in voxel order.
+ * Reductions over voxels are taken in fixed chunks of ORC_CHUNK consecutive voxels: each
+ * chunk is summed sequentially in voxel order and the chunk sums are added in chunk order.
+ * With OpenMP (orc_set_threads) the chunks and the per-voxel loops are spread over
+ * threads; the fixed chunking makes every result bitwise independent of the thread count.
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_CHUNK 8192
+static int g_threads = 1;
+
+/* Number of host threads for the per-voxel loops and chunked sums (>= 1; 1 = serial).
+ * Returns the count in effect (1 when built without OpenMP). */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    g_threads = n < 1 ? 1 : n;
+#else
+    (void)n;
+    g_threads = 1;
+#endif
+    return g_threads;
+}
+
+int orc_get_threads(void) { return g_threads; }
+
+/* sum_{j in [0, n)} of a per-index term, chunked as stated in the header */
+typedef double (*orc_range_sum)(const void *arg, long j0, long j1);
+static double chunked_sum(long n, orc_range_sum f, const void *arg) {
+    long nch = (n + ORC_CHUNK - 1) / ORC_CHUNK;
+    double stack_part[64];
+    double *part = nch <= 64 ? stack_part : (double *)malloc(sizeof(double) * nch);
+    double acc = 0.0;
+    if (!part) return NAN;
+#pragma omp parallel for schedule(static) if (g_threads > 1) num_threads(g_threads)
+    for (long c = 0; c < nch; ++c) {
+        long j0 = c * ORC_CHUNK, j1 = j0 + ORC_CHUNK < n ? j0 + ORC_CHUNK : n;
+        part[c] = f(arg, j0, j1);
+    }
+    for (long c = 0; c < nch; ++c) acc += part[c];
+    if (part != stack_part) free(part);
+    return acc;
+}
+
+/* sum_j a_j b_j over [0, n) */
+typedef struct { const double *a, *b; } dot_arg;
+static double dot_range(const void *p, long j0, long j1) {
+    const dot_arg *d = (const dot_arg *)p;
+    double acc = 0.0;
+    for (long j = j0; j < j1; ++j) acc += d->a[j] * d->b[j];
+    return acc;
+}
+static double dot(long n, const double *a, const double *b) {
+    dot_arg d = {a, b};
+    return chunked_sum(n, dot_range, &d);
+}
+
+/* sum_j a_j over [0, n) */
+static double sum_range(const void *p, long j0, long j1) {
+    const double *a = (const double *)p;
+    double acc = 0.0;
+    for (long j = j0; j < j1; ++j) acc += a[j];
+    return acc;
+}
+static double sum(long n, const double *a) { return chunked_sum(n, sum_range, a); }
 
 #define ORC_OK 0
 #define ORC_ERR_ARG (-1)
@@ -179,6 +242,7 @@ int orc_create(orc_t **out, int nx, int ny, int nz, int nc, int L, const double 
     h->rang = (double *)malloc(sizeof(double) * (h->nm ? h->nm : 1) * h->T);
     if (!h->rabs || !h->rang) { orc_destroy(h); return ORC_ERR_OOM; }
     /* precompute r_cdmnj (Eq. 3) once, as the Algorithm box does */
+#pragma omp parallel for schedule(dynamic, 256) if (g_threads > 1) num_threads(g_threads)
     for (long j = 0; j < h->nv; ++j) {
         long k = h->slot[j];
         if (k < 0) continue;
@@ -192,16 +256,23 @@ int orc_create(orc_t **out, int nx, int ny, int nz, int nc, int L, const double 
 long orc_num_unknowns(const orc_t *h) { return h->nm; }
 
 /* Phi (Eq. 2) over the mask voxels */
-double orc_phi(const orc_t *h, const double *w) {
+typedef struct { const orc_t *h; const double *w; } hw_arg;
+static double phi_range(const void *p, long j0, long j1) {
+    const orc_t *h = ((const hw_arg *)p)->h;
+    const double *w = ((const hw_arg *)p)->w;
     double acc = 0.0;
-    for (long j = 0; j < h->nv; ++j) {
+    for (long j = j0; j < j1; ++j) {
         long k = h->slot[j];
         if (k < 0) continue;
-        double p;
-        voxel_terms(h->T, h->rabs + k * h->T, h->rang + k * h->T, h->dt, w[j], &p, NULL, NULL);
-        acc += p;
+        double ph;
+        voxel_terms(h->T, h->rabs + k * h->T, h->rang + k * h->T, h->dt, w[j], &ph, NULL, NULL);
+        acc += ph;
     }
     return acc;
+}
+double orc_phi(const orc_t *h, const double *w) {
+    hw_arg a = {h, w};
+    return chunked_sum(h->nv, phi_range, &a);
 }
 
 /* neighbour helpers: forward neighbours (+x, +y, +z) of voxel j, -1 if outside grid or mask */
@@ -223,17 +294,24 @@ static long bwd_nbr(const orc_t *h, long j, int axis) {
     return (k >= 0 && h->mask[k]) ? k : -1;
 }
 
-/* sum over edges (both ends in the mask) of (a_j - a_k)(b_j - b_k) */
-static double edge_dot(const orc_t *h, const double *a, const double *b) {
+/* sum over edges (both ends in the mask) of (a_j - a_k)(b_j - b_k), each edge counted at
+ * its lower voxel j */
+typedef struct { const orc_t *h; const double *a, *b; } edge_arg;
+static double edge_range(const void *p, long j0, long j1) {
+    const edge_arg *e = (const edge_arg *)p;
     double acc = 0.0;
-    for (long j = 0; j < h->nv; ++j) {
-        if (!h->mask[j]) continue;
+    for (long j = j0; j < j1; ++j) {
+        if (!e->h->mask[j]) continue;
         for (int ax = 0; ax < 3; ++ax) {
-            long k = fwd_nbr(h, j, ax);
-            if (k >= 0) acc += (a[j] - a[k]) * (b[j] - b[k]);
+            long k = fwd_nbr(e->h, j, ax);
+            if (k >= 0) acc += (e->a[j] - e->a[k]) * (e->b[j] - e->b[k]);
         }
     }
     return acc;
+}
+static double edge_dot(const orc_t *h, const double *a, const double *b) {
+    edge_arg e = {h, a, b};
+    return chunked_sum(h->nv, edge_range, &e);
 }
 
 /* beta/2 ||C w||^2 */
@@ -243,6 +321,7 @@ double orc_cost(const orc_t *h, const double *w) { return orc_phi(h, w) + orc_re
 
 /* grad Psi (Eq. 8); zero outside the mask */
 void orc_grad(const orc_t *h, const double *w, double *g) {
+#pragma omp parallel for schedule(dynamic, 256) if (g_threads > 1) num_threads(g_threads)
     for (long j = 0; j < h->nv; ++j) {
         long k = h->slot[j];
         if (k < 0) { g[j] = 0.0; continue; }
@@ -260,6 +339,7 @@ void orc_grad(const orc_t *h, const double *w, double *g) {
 
 /* gradient of the data term alone */
 void orc_grad_phi(const orc_t *h, const double *w, double *g) {
+#pragma omp parallel for schedule(dynamic, 256) if (g_threads > 1) num_threads(g_threads)
     for (long j = 0; j < h->nv; ++j) {
         long k = h->slot[j];
         if (k < 0) { g[j] = 0.0; continue; }
@@ -294,6 +374,7 @@ void orc_set_curvature(orc_t *h, int mode) { h->curv_mode = mode; }
 
 /* curvature d_j of Eq. 10 at w (or the combined variant); zero outside the mask */
 void orc_curv(const orc_t *h, const double *w, double *d) {
+#pragma omp parallel for schedule(dynamic, 256) if (g_threads > 1) num_threads(g_threads)
     for (long j = 0; j < h->nv; ++j) {
         long k = h->slot[j];
         if (k < 0) { d[j] = 0.0; continue; }
@@ -306,6 +387,7 @@ void orc_curv(const orc_t *h, const double *w, double *d) {
  * the diagonal of the true Hessian of the data term (used for implicit differentiation of the
  * converged field map, not by the solver).  Zero outside the mask. */
 void orc_hess_diag(const orc_t *h, const double *w, double *out) {
+#pragma omp parallel for schedule(dynamic, 256) if (g_threads > 1) num_threads(g_threads)
     for (long j = 0; j < h->nv; ++j) {
         long k = h->slot[j];
         if (k < 0) { out[j] = 0.0; continue; }
@@ -424,6 +506,7 @@ int orc_set_gamma(orc_t *h, const double *gam) {
 
 /* Phi_j(w_j) (Eq. 2) of every voxel (0 outside the mask). */
 void orc_phi_vox(const orc_t *h, const double *w, double *out) {
+#pragma omp parallel for schedule(dynamic, 256) if (g_threads > 1) num_threads(g_threads)
     for (long j = 0; j < h->nv; ++j) {
         long k = h->slot[j];
         double phi = 0.0;
@@ -447,6 +530,7 @@ void orc_rho(const orc_t *h, double *out) {
  * nsweep equally spaced values from wlo to whi (both included) and keep the first value
  * with the smallest cost.  Zero outside the mask. */
 void orc_wf_sweep(const orc_t *h, int nsweep, double wlo, double whi, double *out) {
+#pragma omp parallel for schedule(dynamic, 256) if (g_threads > 1) num_threads(g_threads)
     for (long j = 0; j < h->nv; ++j) {
         long k = h->slot[j];
         if (k < 0) { out[j] = 0.0; continue; }
@@ -843,8 +927,7 @@ int orc_solve(const orc_t *h, double *w, int init, int niter, int nls, int preco
                 p[j] = g[j] / hjj;
             }
         }
-        double gp = 0.0, gprevp = 0.0;
-        for (long j = 0; j < nv; ++j) { gp += g[j] * p[j]; gprevp += gprev[j] * p[j]; }
+        double gp = dot(nv, g, p), gprevp = dot(nv, gprev, p);
         double mu = 0.0;
         if (i > 0 && gp_prev != 0.0) mu = (gp - gprevp) / gp_prev;
         for (long j = 0; j < nv; ++j) z[j] = -p[j] + mu * z[j];
@@ -854,8 +937,8 @@ int orc_solve(const orc_t *h, double *w, int init, int niter, int nls, int preco
             for (long j = 0; j < nv; ++j) wk[j] = w[j] + alpha * z[j];
             orc_grad_phi(h, wk, gk);
             orc_curv(h, wk, d);
-            double fp = 0.0, D = 0.0;
-            for (long j = 0; j < nv; ++j) { fp += z[j] * gk[j]; D += z[j] * z[j] * d[j]; }
+            for (long j = 0; j < nv; ++j) wk[j] = z[j] * z[j] * d[j];
+            double fp = dot(nv, z, gk), D = sum(nv, wk);
             fp += h->beta * (a + alpha * cz2);
             double den = D + h->beta * cz2;
             if (den == 0.0) { alpha = 0.0; break; }

@@ -31,12 +31,25 @@ def source_path():
 
 def compile_oracle(src, out):
     """Compile a C source of the oracle (fm_oracle.c or a test's modified copy) into the shared
-    library out, with plain IEEE double semantics (no fused contractions)."""
+    library out, with plain IEEE double semantics (no fused contractions) and OpenMP when the
+    compiler has it (the results do not depend on it: see orc_set_threads)."""
     tmp = out + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
-                           "-fno-fast-math", "-o", tmp, src, "-lm"])
+    base = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
+    r = subprocess.run(base + ["-fopenmp", "-o", tmp, src, "-lm"], capture_output=True, text=True)
+    if r.returncode != 0:
+        subprocess.check_call(base + ["-o", tmp, src, "-lm"])
     os.replace(tmp, out)
     return out
+
+
+def set_threads(n):
+    """Host threads the oracle uses (1 = serial); returns the count in effect (1 without
+    OpenMP).  Results are bitwise the same for every count."""
+    return int(_lib().orc_set_threads(int(n)))
+
+
+def get_threads():
+    return int(_lib().orc_get_threads())
 
 
 def build_oracle(force=False):
@@ -64,6 +77,10 @@ def load_oracle_variant(path):
 
 def _declare(lib):
     vp = C.c_void_p
+    lib.orc_set_threads.argtypes = [C.c_int]
+    lib.orc_set_threads.restype = C.c_int
+    lib.orc_get_threads.argtypes = []
+    lib.orc_get_threads.restype = C.c_int
     lib.orc_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                _dp, vp, _dp, vp, C.c_double]
     lib.orc_create.restype = C.c_int

@@ -300,6 +300,13 @@ def full_config(seed=1002, **kw):
                        nblobs=6, step_hz=40.0, name="full_256x256x128_c8", **kw)
 
 
+def full8_small_config(seed=1007, **kw):
+    """64x64x32, 8 coils: the full workload's recipe (echoes 0/2/10 ms, +-250 Hz mixture +
+    40 Hz step, SNR 15 dB) at a size whose 100-iteration oracle solve takes minutes."""
+    return make_volume(64, 64, 32, ncoil=8, snr_db=15.0, seed=seed, fmax_hz=250.0,
+                       nblobs=6, step_hz=40.0, name="full8_64x64x32_c8", **kw)
+
+
 def diff_config(seed=1005, **kw):
     """128x128x64, 8 coils, echoes 0/2/10 ms (the differentiation workload's shape)."""
     return make_volume(128, 128, 64, ncoil=8, snr_db=20.0, seed=seed, fmax_hz=250.0,
