@@ -37,14 +37,30 @@ if ROOT not in sys.path:
 
 # ncu DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch, by (workload,
 # kernel), from one ncu capture of the full workload (its summary sits with the committed
-# profiles); an entry is removed when its kernel changes.
+# profiles), each with the hash of the kernel sources it was measured on: a figure whose
+# sources have changed since is reported as null.
+KERNEL_SOURCES = {"ls": ("k_data.cu",), "grad": ("k_data.cu",), "dir": ("k_data.cu",), "ic_fwd": ("k_ic.cu",),
+                  "ic_bwd": ("k_ic.cu",)}
 NCU_TRAFFIC_BYTES = {
-    ("full", "ls"): 1944912384 + 101888,
-    ("full", "grad"): 504670208 + 21847424,
-    ("full", "ic_fwd"): 78444544 + 34418048,
-    ("full", "ic_bwd"): 134260480 + 16525056,
-    ("full", "dir"): 64357504 + 1170560,
 }
+
+
+def kernel_src_hash(kernel):
+    """sha256 (16 hex digits) of the sources a kernel class is built from (its .cu and the
+    shared device header)."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2005_08661_gb300", "csrc")
+    for f in KERNEL_SOURCES.get(kernel, ()) + ("fm_internal.h",):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload, kernel):
+    e = NCU_TRAFFIC_BYTES.get((workload, kernel))
+    if e is None or e[1] != kernel_src_hash(kernel):
+        return None
+    return e[0]
 
 WORKLOADS = {
     "full": dict(desc="256x256x128 voxels, 8 coils, 3 echoes (0/2/10 ms), SNR 15 dB, beta=2^-3, "
@@ -69,7 +85,8 @@ WORKLOADS = {
                       "torch.autograd forward (100 NCG iterations) + backward (IC(0)-preconditioned adjoint "
                       "CG to 1e-6, dl/dbeta and dl/dy) of l = ||w^ - w_true||^2", niter=100),
 }
-CPU_SAMPLE = (32, 32, 16)  # oracle sample: centred sub-volume of the same acquisition
+CPU_SAMPLE = (64, 64, 32)  # oracle sample (all host cores): centred sub-volume of the same acquisition
+CPU_SAMPLE_1CORE = (32, 32, 16)  # the one-thread figure, on a smaller centred sub-volume
 
 
 def make_workload(name, seed_offset=0):
@@ -86,7 +103,7 @@ def make_workload(name, seed_offset=0):
 def sub_volume(vol, size):
     """Centred sub-block of a volume (same data, mask and coils) for oracle sampling."""
     from synth import Volume
-    sx, sy, sz = size
+    sx, sy, sz = min(size[0], vol.nx), min(size[1], vol.ny), min(size[2], vol.nz)
     x0, y0, z0 = (vol.nx - sx) // 2, (vol.ny - sy) // 2, (vol.nz - sz) // 2
     sl = (slice(z0, z0 + sz), slice(y0, y0 + sy), slice(x0, x0 + sx))
     return Volume(y=np.ascontiguousarray(vol.y[(slice(None), slice(None)) + sl]),
@@ -99,20 +116,14 @@ def sub_volume(vol, size):
 # ------------------------------------------------------------------ flop / byte model
 
 def data_eval_flops(nc, L, literal):
-    """Algorithmic FP32 flops of one voxel's data-term evaluation (gradient + curvature),
-    counting a fused multiply-add as 2.
-
-    Per echo pair: phase (2), half-angle sine/cosine (20), gradient/cost terms (6).  Literal
-    curvature per (pair, c, d): phase difference (1), wrap to [-pi, pi] (5), u^2 (1),
-    degree-5 polynomial in u^2 for sin(u)/u (10), amplitude multiply-accumulate (2) = 19;
-    plus 2 per (pair, d) for the rotated phase and 2 per (pair, c) for the outer sum."""
+    """Algorithmic flops of one voxel's data-term evaluation (gradient + curvature), by the
+    method's work count rather than the implementation's instructions: about 12 per echo-pair
+    rotation (the phase of the pair term and its cost and gradient contributions, Eq. 2 and 8)
+    and about 14 per wrapped-sinc curvature term (Eq. 10-11: phase, wrap into [-pi, pi],
+    sin(u)/u, weighted accumulation) -- N_c^2 of them per pair for the literal curvature, one
+    per pair for the coil-combined form."""
     P = L * (L - 1) // 2
-    per_pair = 28
-    if literal:
-        per_pair += nc * nc * 19 + 4 * nc
-    else:
-        per_pair += 19
-    return P * per_pair
+    return P * (12 + 14 * (nc * nc if literal else 1))
 
 
 def data_eval_bytes(nc, L, literal, ts=4):
@@ -126,7 +137,27 @@ def data_eval_bytes(nc, L, literal, ts=4):
 HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal (the measured copy peak is the roofline)
 
 
-def peak_numbers(sm_max_mhz, nsm):
+def fp32_probe(device):
+    """Measured FP32 FMA rate of the GPU (paper_2005_08661_gb300/probe/fp32_rate.cu):
+    (TFLOP/s, FMA lane-ops per SM per clock, SM MHz during the probe), or None."""
+    import ctypes as C
+    from paper_2005_08661_gb300 import build as fm_build
+    try:
+        lib = C.CDLL(fm_build.probe_path())
+        f = lib.fmprobe_fp32_rate
+        f.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        f.restype = C.c_int
+        t, r, m = C.c_double(), C.c_double(), C.c_double()
+        if f(int(device), C.byref(t), C.byref(r), C.byref(m)) != 0:
+            return None
+        return t.value, r.value, m.value
+    except OSError:
+        return None
+
+
+def peak_numbers(sm_mhz, nsm, probe=None):
+    """Roofline denominators: the measured HBM copy bandwidth, and the FP32 rate measured by the
+    FMA probe scaled to the SM clock of the timed region (else derived from 128 lanes per SM)."""
     peaks = {}
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -136,8 +167,14 @@ def peak_numbers(sm_max_mhz, nsm):
     else:
         peaks["hbm_gbs"] = 6800.0
         peaks["hbm_src"] = "of fallback"
-    # FP32 CUDA-core peak: 128 FP32 lanes per SM, one FMA (2 flops) per lane per clock
-    peaks["fp32_tflops"] = 2 * 128 * nsm * sm_max_mhz * 1e6 / 1e12
+    if probe is not None:
+        tflops, per_clk, mhz = probe
+        peaks["fp32_tflops"] = 2 * per_clk * nsm * sm_mhz * 1e6 / 1e12
+        peaks["fp32_src"] = (f"of measured: FMA probe {per_clk:.1f} FP32 FMA/clk/SM ({tflops:.1f} TFLOP/s at "
+                             f"{mhz:.0f} MHz), x {nsm} SMs x {sm_mhz:.0f} MHz of the timed region")
+    else:
+        peaks["fp32_tflops"] = 2 * 128 * nsm * sm_mhz * 1e6 / 1e12
+        peaks["fp32_src"] = f"derived: 2 flops x 128 FP32 lanes x {nsm} SMs x {sm_mhz:.0f} MHz"
     return peaks
 
 
@@ -212,30 +249,56 @@ def barrier(world):
 
 # ------------------------------------------------------------------ oracle (CPU baseline / reference arm)
 
-def oracle_sample(vol, iters, curvature="literal"):
-    """Time the FP64 oracle, single-threaded, on a centred sub-volume; returns (seconds, units).
-    curvature "combined" selects the oracle's coil-combined curvature (the labelled variant)."""
-    from oracle import Oracle, wf_gamma
-    sub = sub_volume(vol, CPU_SAMPLE)
-    if "fat_amps" in sub.meta:  # water-fat: the sweep + PWLS start, then the timed NCG iterations
-        amps, freqs = sub.meta["fat_amps"], sub.meta["fat_freqs_khz"]
-        o = Oracle.from_volume(sub)
-        o.set_gamma(wf_gamma(sub.te, amps, freqs)[1])
-        half = float(np.pi * abs(freqs[int(np.argmax(amps))]))
-        w0 = o.pwls(o.wf_sweep(100, -half, half), 10)
+def _oracle_child(p):
+    """Runs in a spawned process (no CUDA context, its own OpenMP runtime): times the FP64
+    oracle on one sub-volume, p["reps"] times; returns (seconds of each rep, threads used)."""
+    from oracle import Oracle, set_threads, wf_gamma
+    from synth import Volume
+    used = set_threads(p["threads"])
+    sub = Volume(y=p["y"], smap=p["smap"], mask=p["mask"], te=p["te"], omega_true=np.zeros(p["mask"].shape),
+                 beta=p["beta"], name="sample", meta=p["meta"])
+    out = []
+    for _ in range(p["reps"]):
+        if "fat_amps" in sub.meta:  # water-fat: the sweep + PWLS start, then the timed NCG iterations
+            amps, freqs = sub.meta["fat_amps"], sub.meta["fat_freqs_khz"]
+            o = Oracle.from_volume(sub)
+            o.set_gamma(wf_gamma(sub.te, amps, freqs)[1])
+            half = float(np.pi * abs(freqs[int(np.argmax(amps))]))
+            w0 = o.pwls(o.wf_sweep(100, -half, half), 10)
+            t0 = time.perf_counter()
+            o.solve(w0=w0, niter=p["iters"], nls=5)
+            out.append(time.perf_counter() - t0)
+            o.close()
+            continue
         t0 = time.perf_counter()
-        o.solve(w0=w0, niter=iters, nls=5)
-        dt = time.perf_counter() - t0
+        o = Oracle.from_volume(sub)
+        if p["curvature"] == "combined":
+            o.set_curvature("combined")
+        o.solve(niter=p["iters"], nls=5)
+        out.append(time.perf_counter() - t0)
         o.close()
-        return dt, sub.nvox * iters
-    t0 = time.perf_counter()
-    o = Oracle.from_volume(sub)
-    if curvature == "combined":
-        o.set_curvature("combined")
-    o.solve(niter=iters, nls=5)
-    dt = time.perf_counter() - t0
-    o.close()
-    return dt, sub.nvox * iters
+    return out, used
+
+
+def oracle_sample(vol, iters, curvature="literal", threads=None, size=CPU_SAMPLE, reps=1):
+    """Time the FP64 oracle (precompute + iters NCG-MLS iterations) on a centred sub-volume in a
+    spawned process with `threads` host threads (default: all); returns (seconds per rep,
+    voxel-iterations per rep, threads used, sub-volume)."""
+    import multiprocessing as mp
+    sub = sub_volume(vol, size)
+    meta = {k: v for k, v in sub.meta.items() if k.startswith("fat_")}
+    payload = dict(y=sub.y, smap=sub.smap, te=sub.te, mask=sub.mask, beta=sub.beta, meta=meta, iters=iters,
+                   threads=threads or os.cpu_count() or 1, curvature=curvature, reps=reps)
+    with mp.get_context("spawn").Pool(1) as pool:
+        dts, used = pool.apply(_oracle_child, (payload,))
+    return dts, sub.nvox * iters, used, sub
+
+
+def sample_desc(sub, iters, threads, curvature, ncoil):
+    return (f"FP64 C oracle, {threads} thread{'s' if threads > 1 else ''} (OpenMP, fixed-chunk sums), precompute + "
+            f"{iters} NCG-MLS-IC(0) iteration{'s' if iters > 1 else ''} (N_ls=5) on the centred "
+            f"{sub.nx}x{sub.ny}x{sub.nz} sub-volume of the workload ({ncoil} coils, {curvature} curvature), host "
+            f"{cpu_desc()}, nproc {os.cpu_count()}")
 
 
 def cpu_desc():
@@ -254,24 +317,19 @@ def run_reference(args, world, rank):
     if rank != 0:
         return 0
     vol = make_workload(args.workload)
-    sample = (f"FP64 C oracle, 1 thread, 1 NCG-MLS-IC(0) iteration (N_ls=5) per step on the centred "
-              f"{CPU_SAMPLE[0]}x{CPU_SAMPLE[1]}x{CPU_SAMPLE[2]} sub-volume of the workload ({vol.ncoil} coils, "
-              f"{args.curvature} curvature), host {cpu_desc()}, nproc {os.cpu_count()}")
-    for _ in range(args.warmup):
-        oracle_sample(vol, 1, args.curvature)
-    times, units = [], 0
-    for _ in range(args.steps):
-        dt, u = oracle_sample(vol, 1, args.curvature)
-        times.append(dt)
-        units = u
+    # one step = the oracle's precompute + 1 NCG-MLS iteration on the sample, all host cores
+    dts, units, used, sub = oracle_sample(vol, 1, args.curvature, reps=args.warmup + args.steps)
+    times = dts[args.warmup:]
     t = sum(times) / len(times)
     value = units / t
+    sample = sample_desc(sub, 1, used, args.curvature, vol.ncoil) + ", per step"
     line = {"metric": "voxel-NCG-iters/s", "value": value, "unit": "voxel-iter/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": WORKLOADS[args.workload]["desc"], "sample": sample},
-            "cpu_baseline": {"value": value, "unit": "voxel-iter/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "voxel-iter/s", "cores": used, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": "voxel-iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -351,72 +409,49 @@ def run_ours(args, world, rank, local):
     t_step = max_over_ranks(t_step, world, dev)
     value = world * nv * niter / t_step
 
-    # end to end: host buffers in, field map out, through the same calls
+    # end to end through the C ABI's host-buffer calls (fm_set_data_host, fm_solve_host): every
+    # step copies its images, coil maps and mask from page-locked host memory into the
+    # library's staging buffers (its copy stream) and the field map back to host memory; the
+    # upload of step k + 1 runs while step k is solved
     h2d = y_h.numel() * y_h.element_size() + m_h.numel() + (s_h.numel() * s_h.element_size() if s_h is not None else 0)
     d2h = w.numel() * w.element_size()
     e2e = None
-    if not args.no_e2e:
-        # every step copies its inputs from pinned host memory and reads the field map back;
-        # step k + 1's inputs are copied on a second stream into a second set of device
-        # buffers while step k computes
-        copy_stream = torch.cuda.Stream(dev)
-        bufs = [(y_d, s_d, m_d), (torch.empty_like(y_d), torch.empty_like(s_d) if s_d is not None else None,
-                                  torch.empty_like(m_d))]
-        ev_copied = [torch.cuda.Event(), torch.cuda.Event()]
-        ev_freed = [torch.cuda.Event(), torch.cuda.Event()]
-        copy_times = []  # (start, end) events of each step's host-to-device copy
-
-        def issue_copy(k):
-            yb, sb, mb = bufs[k % 2]
-            copy_stream.wait_event(ev_freed[k % 2])
-            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            with torch.cuda.stream(copy_stream):
-                c0.record(copy_stream)
-                yb.copy_(y_h, non_blocking=True)
-                if sb is not None:
-                    sb.copy_(s_h, non_blocking=True)
-                mb.copy_(m_h, non_blocking=True)
-                c1.record(copy_stream)
-            copy_times.append((c0, c1))
-            ev_copied[k % 2].record(copy_stream)
-
-        def compute(k):
-            stream.wait_event(ev_copied[k % 2])
-            solve_path(bufs[k % 2])
-            ev_freed[k % 2].record(stream)
-            with torch.cuda.stream(stream):
-                w_h.copy_(w, non_blocking=True)
+    if not args.no_e2e and not wf:
+        fm_io = FieldMap(vol.nx, vol.ny, vol.nz, ncoil=vol.ncoil, necho=vol.necho, precision=prec, device=local,
+                         stream=stream, curvature=args.curvature)
+        fm_io.set_profiling(True)
 
         def run_e2e(nsteps):
-            issue_copy(0)
-            for k in range(nsteps):
-                if k + 1 < nsteps:
-                    issue_copy(k + 1)
-                compute(k)
+            for _ in range(nsteps):
+                fm_io.set_data_host(y_h, s_h, vol.te, m_h, vol.beta)
+                fm_io.solve_host(w_h, True, niter)
 
         run_e2e(2)
-        torch.cuda.synchronize(dev)
+        fm_io.synchronize()
         barrier(world)
-        copy_times.clear()
         nst = max(1, args.steps)
         e0.record(stream)
-        copy_stream.wait_event(e0)
         run_e2e(nst)
         e1.record(stream)
+        fm_io.synchronize()
         torch.cuda.synchronize(dev)
         barrier(world)
         t_e2e = max_over_ranks(e0.elapsed_time(e1) / 1000.0 / nst, world, dev)
-        h2d_ms = sum(a.elapsed_time(b) for a, b in copy_times) / max(1, len(copy_times))
+        kio = fm_io.kernel_times()
+        h2d_ms, d2h_ms = kio["h2d"][0], kio["d2h"][0]
+        fm_io.close()
         e2e = {"value": world * nv * niter / t_e2e, "unit": "voxel-iter/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000 * t_e2e,
                "h2d_ms_per_step": h2d_ms, "h2d_gbs": h2d / (h2d_ms * 1e-3) / 1e9 if h2d_ms > 0 else None,
-               "pipelined": "step k+1's inputs copied on a second stream while step k computes"}
+               "d2h_ms_per_step": d2h_ms,
+               "path": "C ABI fm_set_data_host + fm_solve_host on page-locked host buffers; the library's copy "
+                       "stream uploads step k+1 while step k is solved"}
 
     # roofline of the kernel with the largest share of the outer iteration
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    sm_max = clk.get("sm_max_mhz") or 2070.0
-    peaks = peak_numbers(sm_max, nsm)
-    per_iter = {k: v[0] for k, v in kt.items() if v[1] > 0}
+    sm_run = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+    peaks = peak_numbers(sm_run, nsm, fp32_probe(local))
+    per_iter = {k: v[0] for k, v in kt.items() if v[1] > 0 and k in ("grad", "ic_fwd", "ic_bwd", "dir", "ls")}
     dom = max(per_iter, key=per_iter.get) if per_iter else None
     literal = vol.ncoil > 1 and args.curvature == "literal"
     def kernel_roofline(name, ms):
@@ -426,10 +461,16 @@ def run_ours(args, world, rank, local):
         if evals and literal:
             flops = evals * nmask * data_eval_flops(vol.ncoil, vol.necho, True)
             ach = flops / (ms * 1e-3) / 1e12
+            byts = evals * nmask * data_eval_bytes(vol.ncoil, vol.necho, literal, ts)
+            hbm = byts / (ms * 1e-3) / 1e9
             return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
-                    "frac": ach / peaks["fp32_tflops"], "peak_src": "derived: 2 flops x 128 FP32 lanes x "
-                    f"{nsm} SMs x {sm_max:.0f} MHz", "ms_per_launch": ms, "algorithmic_flops_per_launch": flops,
-                    "traffic": NCU_TRAFFIC_BYTES.get((args.workload, name))}
+                    "frac": ach / peaks["fp32_tflops"], "peak_src": peaks["fp32_src"], "ms_per_launch": ms,
+                    "algorithmic_flops_per_launch": flops,
+                    "flop_count": "per mask voxel and evaluation: 12 per echo-pair rotation + 14 per wrapped-sinc "
+                                  "term (N_c^2 per pair)",
+                    "hbm": {"achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                            "frac": hbm / peaks["hbm_gbs"], "algorithmic_bytes_per_launch": byts},
+                    "traffic": ncu_traffic(args.workload, name)}
         if evals:
             byts = evals * (nmask * data_eval_bytes(vol.ncoil, vol.necho, literal, ts) + nv)
         elif name == "ic_fwd":  # per grid voxel: bits, d and g in, pivots and v out
@@ -441,7 +482,7 @@ def run_ours(args, world, rank, local):
         ach = byts / (ms * 1e-3) / 1e9
         out = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                "frac": ach / peaks["hbm_gbs"], "peak_src": peaks["hbm_src"], "ms_per_launch": ms,
-               "algorithmic_bytes_per_launch": byts, "traffic": NCU_TRAFFIC_BYTES.get((args.workload, name))}
+               "algorithmic_bytes_per_launch": byts, "traffic": ncu_traffic(args.workload, name)}
         if name.startswith("ic"):
             out["note"] = "latency-bound wavefront: the HBM fraction is reported for reference only"
         return out
@@ -449,19 +490,23 @@ def run_ours(args, world, rank, local):
     roof = kernel_roofline(dom, per_iter[dom]) if dom is not None else None
     kernels = {}
     for k, v in kt.items():
-        if v[1] > 0:
+        if v[1] > 0 and k in ("grad", "ic_fwd", "ic_bwd", "dir", "ls"):
             r = kernel_roofline(k, v[0])
             kernels[k] = {"ms_per_launch": v[0], "share_of_iteration": v[0] / sum(per_iter.values()),
                           "bound": r["bound"], "achieved": r["achieved"], "unit": r["unit"], "frac": r["frac"]}
-            tb = NCU_TRAFFIC_BYTES.get((args.workload, k))
+            if "hbm" in r:
+                kernels[k]["hbm_frac_algorithmic"] = r["hbm"]["frac"]
+            tb = ncu_traffic(args.workload, k)
             if tb:  # ncu DRAM bytes of one launch over its CUDA-event time, against the HBM peak
                 kernels[k]["hbm_traffic_frac"] = tb / (v[0] * 1e-3) / 1e9 / peaks["hbm_gbs"]
                 kernels[k]["hbm_traffic_frac_nominal"] = tb / (v[0] * 1e-3) / 1e9 / HBM_NOMINAL_GBS
 
-    # time to the oracle's final cost on the small workload (stored by tests/golden/make_golden.py)
-    ttc = None
+    # time to the oracle's final cost on the small workload and on the eight-coil 64x64x32
+    # volume (oracle histories stored by tests/golden/make_golden.py)
+    ttc = ttc8 = None
     if rank == 0 and not args.no_ttc:
-        ttc = time_to_oracle_cost(prec, stream)
+        ttc = time_to_oracle_cost(prec, stream, "small")
+        ttc8 = time_to_oracle_cost(prec, stream, "full8")
 
     # the precision form against the plain FP64 GPU solve of the same workload (untimed)
     fp64cmp = None
@@ -492,12 +537,13 @@ def run_ours(args, world, rank, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, units = oracle_sample(vol, 4, args.curvature)
-        cpu = {"value": units / dt, "unit": "voxel-iter/s", "cores": 1, "kind": "oracle",
-               "sample": f"FP64 C oracle, 1 thread, 4 NCG-MLS-IC(0) iterations (N_ls=5) on the centred "
-                         f"{CPU_SAMPLE[0]}x{CPU_SAMPLE[1]}x{CPU_SAMPLE[2]} sub-volume of the workload "
-                         f"({vol.ncoil} coils, {args.curvature} curvature), {dt:.1f} s, host {cpu_desc()}, "
-                         f"nproc {os.cpu_count()}"}
+        iters = 8 if literal else 20
+        dts, units, used, sub = oracle_sample(vol, iters, args.curvature)
+        cpu = {"value": units / dts[0], "unit": "voxel-iter/s", "cores": used, "kind": "oracle",
+               "sample": sample_desc(sub, iters, used, args.curvature, vol.ncoil) + f", {dts[0]:.1f} s"}
+        dts1, units1, _, sub1 = oracle_sample(vol, 1, args.curvature, threads=1, size=CPU_SAMPLE_1CORE)
+        cpu["one_core"] = {"value": units1 / dts1[0], "unit": "voxel-iter/s", "cores": 1,
+                           "sample": sample_desc(sub1, 1, 1, args.curvature, vol.ncoil) + f", {dts1[0]:.1f} s"}
 
     # per step: mask count, chunk scan, setup; 5 kernels per outer iteration; the final update
     # (water-fat adds the sweep, the PWLS start and 2 kernels per PWLS iteration, the amplitudes)
@@ -513,7 +559,8 @@ def run_ours(args, world, rank, local):
                        "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (2.1 GB streamed per step)",
                        "masked_voxel_iters_per_s": world * nmask * niter / t_step},
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "kernels": kernels, "clocks": clk,
-            "cpu_baseline": cpu, "time_to_oracle_cost": ttc, "fp32_vs_fp64_gpu": fp64cmp}
+            "cpu_baseline": cpu, "time_to_oracle_cost": ttc, "time_to_oracle_cost_8coil": ttc8,
+            "fp32_vs_fp64_gpu": fp64cmp}
     if rank == 0:
         print(json.dumps(line), flush=True)
     fm.close()
@@ -796,23 +843,35 @@ def run_precond(args, world, rank, local):
     return 0
 
 
-def time_to_oracle_cost(prec, stream):
-    """FP32/FP64 solve of the 64x64x16 workload: seconds until the cost first falls to the
-    FP64 oracle's 50-iteration cost x (1 + 1e-6)."""
+TTC_CASES = {
+    "small": ("small_oracle_cost.json", WORKLOADS["small"]["desc"]),
+    "full8": ("full8_oracle_cost.json", "64x64x32 voxels, 8 coils, 3 echoes (0/2/10 ms), +-250 Hz + 40 Hz step, "
+                                        "SNR 15 dB, beta=2^-3 (the full workload's recipe), 100 NCG iterations, "
+                                        "N_ls=5, IC(0)"),
+}
+
+
+def time_to_oracle_cost(prec, stream, case="small"):
+    """Seconds (setup + solve, CUDA events) until the GPU solve's cost first falls to the FP64
+    oracle's final cost x (1 + 1e-6), on the 64x64x16 one-coil workload or the 64x64x32
+    eight-coil volume."""
     import torch
     from paper_2005_08661_gb300 import FieldMap
-    path = os.path.join(ROOT, "tests", "golden", "small_oracle_cost.json")
+    from synth import full8_small_config
+    fname, desc = TTC_CASES[case]
+    path = os.path.join(ROOT, "tests", "golden", fname)
     if not os.path.exists(path):
         return None
     gold = json.load(open(path))
     target = gold["final_cost"] * (1 + 1e-6)
-    vol = make_workload("small")
+    vol = make_workload("small") if case == "small" else full8_small_config()
     cd = torch.complex64 if prec == "fp32" else torch.complex128
     dev = torch.device("cuda", torch.cuda.current_device())
     y = torch.from_numpy(vol.y).to(dev).to(cd)
+    s = torch.from_numpy(vol.smap).to(dev).to(cd) if vol.smap is not None else None
     m = torch.from_numpy(vol.mask).to(dev)
-    fm = FieldMap(vol.nx, vol.ny, vol.nz, 1, 3, precision=prec, stream=stream)
-    fm.set_data(y, None, vol.te, m, vol.beta)
+    fm = FieldMap(vol.nx, vol.ny, vol.nz, vol.ncoil, vol.necho, precision=prec, stream=stream)
+    fm.set_data(y, s, vol.te, m, vol.beta)
     nmax = gold["niter"]
     _, cost = fm.solve(niter=nmax)
     hit = [i for i, c in enumerate(cost) if c <= target]
@@ -823,19 +882,20 @@ def time_to_oracle_cost(prec, stream):
     w = fm.empty()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(3):
-        fm.set_data(y, None, vol.te, m, vol.beta)
+        fm.set_data(y, s, vol.te, m, vol.beta)
         fm.solve_into(w, True, i_star)
     ts = []
     for _ in range(5):
         e0.record(stream)
-        fm.set_data(y, None, vol.te, m, vol.beta)
+        fm.set_data(y, s, vol.te, m, vol.beta)
         fm.solve_into(w, True, i_star)
         e1.record(stream)
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1) / 1000.0)
     fm.close()
-    return {"workload": WORKLOADS["small"]["desc"], "precision": prec, "iterations": i_star,
-            "seconds": statistics.median(ts), "oracle_cost": gold["final_cost"], "target_rel": 1e-6}
+    return {"workload": desc, "precision": prec, "iterations": i_star, "seconds": statistics.median(ts),
+            "oracle_cost": gold["final_cost"], "final_cost_rel": abs(cost[-1] - gold["final_cost"]) /
+            abs(gold["final_cost"]), "target_rel": 1e-6}
 
 
 def main():

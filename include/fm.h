@@ -58,8 +58,8 @@ extern "C" {
 #define FM_ERR_NONFINITE (-6) /* a global reduction (cost, dot, step) was not finite */
 #define FM_ERR_OOM (-7)       /* device or host allocation failed */
 #define FM_ERR_SIZE (-8)      /* problem larger than a fixed-size buffer of the call allows */
-#define FM_ERR_FILL (-9)      /* FM_PC_ICT: the drop tolerance keeps an entry outside the
-                                 held pattern (see FM_PC_ICT) */
+#define FM_ERR_FILL (-9)      /* FM_PC_ICT: the drop tolerance keeps fill at more grid offsets
+                                 than the factor can hold (see FM_PC_ICT) */
 
 #define FM_FP64 0
 #define FM_FP32 1
@@ -73,11 +73,15 @@ extern "C" {
                         NCG-MLS-IC): natural order, every off-diagonal factor entry (fill-in
                         included) smaller in magnitude than tau = droptol * H_max is set to
                         zero, H_max being the largest |H_jk| of each outer iteration's H.  The
-                        factor is held on IC(0)'s pattern plus the level-1 fill offsets
-                        (x+1, y-1, z), (x+1, y, z-1), (x, y+1, z-1); it is exact whenever the
-                        tolerance keeps nothing outside that pattern, and a factorisation that
-                        would is reported as FM_ERR_FILL at the next synchronising call.  The
-                        sweeps run level by level (x + 2y + 3z), slower than IC(0)'s. */
+                        factor is held on a set of grid offsets: IC(0)'s plus the level-1 fill
+                        offsets (x+1, y-1, z), (x+1, y, z-1), (x, y+1, z-1) at first; a check
+                        after every factorisation finds any entry the tolerance keeps outside
+                        the set, and the calls that factor (fm_ic_factor, fm_solve,
+                        fm_adjoint_solve, fm_batch_solve) then add those offsets and run again
+                        from the same start, so the result is the exact drop-tolerance factor
+                        (these calls synchronise).  FM_ERR_FILL remains only for a pattern of
+                        more than 64 offsets.  The sweeps run level by level (x + B y + C z,
+                        B = 2, C = 3 for the initial set), slower than IC(0)'s. */
 
 #define FM_CURV_LITERAL 0  /* d_j summed over every (c, d, m, n) term (Eq. 10) */
 #define FM_CURV_COMBINED 1 /* d_j from the coil-combined pair weights (labelled variant) */
@@ -165,6 +169,36 @@ FM_API int fm_cost_grad(fm_ctx *ctx, const void *omega, double *cost, void *grad
 FM_API int fm_ic_factor(fm_ctx *ctx, const void *omega, void *inv_pivot);
 
 /*
+ * fm_ic_factor from a given curvature instead of the field map: the factor of
+ * H = diag(curv) + beta C'C (Eq. 9, 12) with the mask and beta of fm_set_data.  curv: device
+ * [nz][ny][nx] of the voxel type (read at mask voxels only).  inv_pivot as for fm_ic_factor.
+ * Errors: as fm_ic_factor.
+ */
+FM_API int fm_ic_factor_curv(fm_ctx *ctx, const void *curv, void *inv_pivot);
+
+/*
+ * The drop-tolerance factor (FM_PC_ICT) as the context holds it: *n_offsets receives the
+ * number nh of held offsets; offsets (host int [3 nh], nullable) their (dx, dy, dz), each
+ * pointing from a voxel to an earlier one in natural order; planes (host double
+ * [nh + 1][nz][ny][nx], nullable; requires a factor) plane 0 = 1 / L_ii, plane 1 + h =
+ * L_{i, i + offset h} (0 where dropped, outside the grid or outside the mask).  The held
+ * pattern starts as IC(0)'s offsets plus the level-1 fill offsets and grows, inside the
+ * calls that factor, until the drop tolerance keeps nothing outside it (at most 64 offsets).
+ * Synchronises when planes is non-NULL.  Errors: FM_ERR_ARG, FM_ERR_STATE.
+ */
+FM_API int fm_ict_pattern(fm_ctx *ctx, int *n_offsets, int *offsets, double *planes);
+
+/*
+ * fm_ic_factor for the IC(0) preconditioner with the inverse pivots returned in double:
+ * inv_pivot (device double [nz][ny][nx]) receives 1/pi_j as the recurrence carries it --
+ * IEEE double in FM_FP64 mode; in FM_FP32 mode the sum hi + lo of the float pair the
+ * forward sweep keeps (about 46 significant bits; the sweeps themselves apply the float hi).
+ * The first FM_FP32 call allocates a float [nz][ny][nx] buffer kept by the context.
+ * Errors: as fm_ic_factor; FM_ERR_STATE for another preconditioner.
+ */
+FM_API int fm_ic_factor64(fm_ctx *ctx, const void *omega, double *inv_pivot);
+
+/*
  * p = (L L')^{-1} g with the factor of the last fm_ic_factor (Sec. III-B, the
  * "precondition" step of the Algorithm box): a forward then a back substitution.
  * g, p: device [nz][ny][nx], distinct.  Errors: FM_ERR_STATE if no factor exists.
@@ -179,10 +213,46 @@ FM_API int fm_ic_apply(fm_ctx *ctx, const void *g, void *p);
  * (g_{i-1}'p_{i-1}), z = -p + mu z, then nls steps alpha <- alpha - f'(alpha) /
  * (sum_j z_j^2 d_j(w + alpha z) + beta ||C z||^2) from alpha = 0, and w <- w + alpha z.
  * cost_hist (host double [niter + 1], nullable) receives Psi(w^0) .. Psi(w^niter);
- * a non-NULL cost_hist synchronises the stream.  Errors: FM_ERR_STATE, FM_ERR_ARG
- * (niter < 0), FM_ERR_NOT_PD, FM_ERR_TIMEOUT, FM_ERR_NONFINITE.
+ * a non-NULL cost_hist synchronises the stream and reports the solve's device errors.
+ * Without it the call returns once the solve is enqueued, and its device errors are
+ * reported by the next synchronising call (e.g. fm_synchronize).  Errors: FM_ERR_STATE,
+ * FM_ERR_ARG (niter < 0), FM_ERR_NOT_PD, FM_ERR_TIMEOUT, FM_ERR_NONFINITE.
  */
 FM_API int fm_solve(fm_ctx *ctx, void *omega, int init_from_data, int niter, double *cost_hist);
+
+/* ---------------------------------------------------------------------------------
+ * Host-buffer form of the problem statement (Sec. II): images, coil maps and mask in host
+ * memory in, field map in host memory out.  The library owns two staging sets of device
+ * inputs (allocated by the first fm_set_data_host: about (8 N_c (L + 1) + 1) bytes per
+ * voxel each in FM_FP32 mode, twice that in FM_FP64 mode) and copies into them on its own
+ * copy stream, so the upload of one acquisition runs while the previous one is solved.
+ * Page-locked host memory (cudaHostAlloc, cudaHostRegister) is needed for that overlap;
+ * pageable memory works, but its copies complete before the call returns.
+ * ------------------------------------------------------------------------------- */
+
+/*
+ * fm_set_data with host arrays: y (host, complex [necho][ncoil][nz][ny][nx] of the image
+ * type), smap (host, complex [ncoil][nz][ny][nx] or NULL as for fm_set_data), te (host
+ * double [necho]), mask (host uint8 [nz][ny][nx] or NULL), beta.  The copies run on the
+ * library's copy stream; the precompute runs on the context's stream after them and after
+ * everything enqueued there before (a solve in flight keeps its own data).  Returns once
+ * both are enqueued: y, smap and mask must stay unchanged until the next synchronising call
+ * on ctx.  Errors: as fm_set_data, and FM_ERR_OOM / FM_ERR_CUDA for the staging buffers.
+ */
+FM_API int fm_set_data_host(fm_ctx *ctx, const void *y, const void *smap, const double *te,
+                            const uint8_t *mask, double beta);
+
+/*
+ * fm_solve with a host field map: omega (host [nz][ny][nx] of the voxel type) is read as
+ * the start point when init_from_data == 0 and receives the result.  Enqueued on the
+ * context's stream (the result is in omega after the next synchronising call, e.g.
+ * fm_synchronize, or at return when cost_hist is non-NULL).  Errors: as fm_solve.
+ */
+FM_API int fm_solve_host(fm_ctx *ctx, void *omega, int init_from_data, int niter, double *cost_hist);
+
+/* Wait for all work of ctx (its stream and its copy stream) and report device errors of
+ * earlier asynchronous calls.  Errors: FM_ERR_CUDA and the device-side codes. */
+FM_API int fm_synchronize(fm_ctx *ctx);
 
 /*
  * Copy the step sizes alpha^(N_i) and Polak-Ribiere factors mu of the last fm_solve
@@ -353,7 +423,9 @@ FM_API int fm_set_spin_limit(fm_ctx *ctx, long long spin_limit);
 #define FM_K_IC_BWD 2 /* back substitution wavefront + g'p, g_prev'p */
 #define FM_K_DIR 3    /* Polak-Ribiere direction + first line-search step */
 #define FM_K_LS 4     /* persistent line search (steps 2..N_i) */
-#define FM_NKERNEL 5
+#define FM_K_H2D 5    /* fm_set_data_host: host-to-device copy of one acquisition's inputs */
+#define FM_K_D2H 6    /* fm_solve_host: device-to-host copy of the field map */
+#define FM_NKERNEL 7
 
 /*
  * Turn per-kernel timing on or off (off by default).  While on, fm_solve brackets

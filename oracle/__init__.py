@@ -11,8 +11,8 @@ solver beyond those pins (search-direction sign, Polak-Ribiere form, fixed inner
 step count) follows the readings stated in fm_oracle.c and is "parity unpinned"
 against the paper itself.
 """
-from .oracle import (Oracle, build_oracle, get_threads, ic0_factor, ic0_solve, ict_factor, lib_path, set_threads,
-                     voxel_r, voxel_terms, wf_gamma)
+from .oracle import (Oracle, build_oracle, curv_raw, get_threads, ic0_factor, ic0_solve, ict_factor, lib_path,
+                     set_threads, voxel_r, voxel_terms, wf_gamma)
 
 __all__ = ["Oracle", "build_oracle", "ic0_factor", "ic0_solve", "ict_factor", "voxel_terms", "voxel_r", "wf_gamma",
-           "lib_path", "set_threads", "get_threads"]
+           "lib_path", "set_threads", "get_threads", "curv_raw"]

@@ -977,6 +977,39 @@ int orc_voxel(int nc, int L, const double *te, const double *y_vox, const double
     return ORC_OK;
 }
 
+/* Curvature d_j of Eq. 10 at w for every voxel of a volume straight from its raw data,
+ * voxel by voxel (r of Eq. 3 formed per voxel, nothing kept): for volumes whose precomputed
+ * r (orc_create) would not fit in host memory.  y: [L][nc][nv] complex, s: [nc][nv] complex
+ * or NULL, mask: [nv] or NULL; out: [nv], 0 outside the mask. */
+int orc_curv_raw(int nx, int ny, int nz, int nc, int L, const double *y, const double *s, const double *te,
+                 const unsigned char *mask, const double *w, double *out) {
+    if (nx < 1 || ny < 1 || nz < 1 || nc < 1 || L < 2 || L > ORC_MAXL || !y || !te || !w || !out) return ORC_ERR_ARG;
+    if (!s && nc != 1) return ORC_ERR_ARG;
+    long nv = (long)nx * ny * nz, T = (long)nc * nc * L * L;
+    double *dt = (double *)malloc(sizeof(double) * T);
+    if (!dt) return ORC_ERR_OOM;
+    tuple_dt(nc, L, te, dt);
+    int st = ORC_OK;
+#pragma omp parallel if (g_threads > 1) num_threads(g_threads)
+    {
+        double *ra = (double *)malloc(sizeof(double) * T), *rg = (double *)malloc(sizeof(double) * T);
+        if (!ra || !rg) {
+#pragma omp atomic write
+            st = ORC_ERR_OOM;
+        }
+#pragma omp for schedule(dynamic, 256)
+        for (long j = 0; j < nv; ++j) {
+            if ((mask && !mask[j]) || !ra || !rg) { out[j] = 0.0; continue; }
+            pair_weights(nc, L, y + 2 * j, 2 * nv, s ? s + 2 * j : NULL, 2 * nv, NULL, ra, rg);
+            voxel_terms(T, ra, rg, dt, w[j], NULL, NULL, out + j);
+        }
+        free(ra);
+        free(rg);
+    }
+    free(dt);
+    return st;
+}
+
 /* raw r_cdmnj of Eq. 3 for one voxel (modulus, angle), T = nc*nc*L*L, order c,d,m,n */
 int orc_voxel_r(int nc, int L, const double *y_vox, const double *s_vox, double *rabs, double *rang) {
     if (nc < 1 || L < 2 || L > ORC_MAXL) return ORC_ERR_ARG;

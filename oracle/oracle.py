@@ -142,6 +142,8 @@ def _declare(lib):
     lib.orc_voxel.restype = C.c_int
     lib.orc_voxel_r.argtypes = [C.c_int, C.c_int, _dp, vp, _dp, _dp]
     lib.orc_voxel_r.restype = C.c_int
+    lib.orc_curv_raw.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _dp, vp, _dp, vp, _dp, _dp]
+    lib.orc_curv_raw.restype = C.c_int
     return lib
 
 
@@ -473,6 +475,24 @@ def voxel_terms(te, y_vox, s_vox, w):
     if st != ORC_OK:
         raise RuntimeError(f"orc_voxel failed: {st}")
     return out
+
+
+def curv_raw(y, smap, te, mask, w):
+    """Curvature d_j (Eq. 10) at w of every voxel of a volume, from the raw images y
+    [L][N_c][z][y][x], coil maps smap [N_c][z][y][x] (or None) and mask, without the
+    precomputed r that Oracle keeps (for volumes too large for it)."""
+    lib = _lib()
+    y = np.asarray(y)
+    L, nc, nz, ny, nx = y.shape
+    yc = _c128(y).reshape(-1)
+    sc = _c128(smap).reshape(-1) if smap is not None else None
+    m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+    out = np.zeros(nx * ny * nz, np.float64)
+    st = lib.orc_curv_raw(nx, ny, nz, nc, L, yc, _ptr(sc), np.ascontiguousarray(te, np.float64), _ptr(m),
+                          np.ascontiguousarray(w, np.float64).reshape(-1), out)
+    if st != ORC_OK:
+        raise RuntimeError(f"orc_curv_raw failed: {st}")
+    return out.reshape(nz, ny, nx)
 
 
 def voxel_r(y_vox, s_vox):

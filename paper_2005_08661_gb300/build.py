@@ -22,8 +22,15 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", 
          "--expt-relaxed-constexpr"]
 
 
+PROBE = os.path.join(HERE, "probe", "fp32_rate.cu")
+
+
 def lib_path():
     return os.path.join(BUILD, "libfm.so")
+
+
+def probe_path():
+    return os.path.join(BUILD, "libfmprobe.so")
 
 
 def _nvcc():
@@ -45,10 +52,10 @@ def _deps():
 
 def up_to_date():
     out = lib_path()
-    if not os.path.exists(out):
+    if not os.path.exists(out) or not os.path.exists(probe_path()):
         return False
-    t = os.path.getmtime(out)
-    return all(os.path.getmtime(f) <= t for f in _deps())
+    t = min(os.path.getmtime(out), os.path.getmtime(probe_path()))
+    return all(os.path.getmtime(f) <= t for f in _deps() + [PROBE])
 
 
 def build(force=False, verbose=False, extra_flags=()):
@@ -71,8 +78,18 @@ def build(force=False, verbose=False, extra_flags=()):
             print(r.stderr, file=sys.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    def build_probe():
+        tmp = probe_path() + f".tmp{os.getpid()}"
+        cmd = [nvcc, *ARCH, *FLAGS, "-shared", "-cudart", "static", PROBE, "-o", tmp]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on the FP32 rate probe:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, probe_path())
+
+    with cf.ThreadPoolExecutor(max_workers=len(SOURCES) + 1) as ex:
+        probe = ex.submit(build_probe)
         objs = list(ex.map(compile_one, SOURCES))
+        probe.result()
     tmp = lib_path() + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -51,7 +51,16 @@ struct fm_ctx {
     int nsm = 0, grid_data = 0, grid_ls = 0, grid_ic = 0, grid_icb = 0;  // grid_icb: backward IC sweep
     int base_data = 0, base_ls = 0, base_ic = 0, base_icb = 0;
     int grid_ict = 0, base_ict = 0, block_ict = 0;  // drop-tolerance IC sweeps (persistent, level barriers)
-    double* ict_L = nullptr;         // drop-tolerance IC factor planes [kIctPlanes][nv]  // grids chosen at creation (batch autotuning scales them)
+    int grid_ictg = 0, base_ictg = 0;                // the same for the table-driven sweeps
+    // drop-tolerance IC: the held pattern (dx, dy, dz per offset, plane order), its device
+    // tables, the factor planes [nh + 2][nv] and the candidate fill offsets of the check
+    std::vector<int> ict_off, ict_qoff;
+    int* ict_tab = nullptr;
+    unsigned* ict_qflags = nullptr;
+    IctTables ict_tb{};
+    int ict_nplanes = 0;
+    double* ict_L = nullptr;
+    void* ict_w0 = nullptr;  // a solve's start map, kept while a growing pattern reruns the solve
     int last_niter = 0;
     cudaGraphExec_t gexec = nullptr;
     cudaGraphExec_t cg_gexec = nullptr;  // adjoint CG iterations (tolerance and limit are arguments)
@@ -60,6 +69,15 @@ struct fm_ctx {
     bool profiling = false;
     cudaEvent_t ev[2][FM_NKERNEL][2] = {};
     bool ev_rec[2][FM_NKERNEL] = {};
+    // host-buffer entry points: two staging sets of device inputs, filled on a copy stream
+    // while the other set's acquisition is being solved, and the field map's device copy
+    cudaStream_t copy_stream = nullptr;
+    void *st_y[2] = {nullptr, nullptr}, *st_s[2] = {nullptr, nullptr};
+    uint8_t* st_m[2] = {nullptr, nullptr};
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_read[2] = {nullptr, nullptr};
+    int st_next = 0;
+    void* w_io = nullptr;
+    float* ip_lo = nullptr;  // fm_ic_factor64 in FP32 mode: low parts of the inverse pivots
     std::string err;
 };
 
@@ -109,21 +127,45 @@ void free_all(fm_ctx* c) {
                 if (e) cudaEventDestroy(e);
     void* bufs[] = {c->pairs, c->coils, c->w0, c->nb, c->vlist, c->chunk_off, c->w[0], c->w[1], c->z[0], c->z[1], c->g[0],
                     c->g[1], c->d, c->p, c->v, c->ip, c->scal, c->partials, c->face, c->tile_part, c->rho,
-                    c->hist_cost, c->hist_alpha, c->hist_mu, c->istate, c->icint, c->order, c->ict_L};
+                    c->hist_cost, c->hist_alpha, c->hist_mu, c->istate, c->icint, c->order, c->ict_L,
+                    c->st_y[0], c->st_y[1], c->st_s[0], c->st_s[1], c->st_m[0], c->st_m[1], c->w_io, c->ip_lo,
+                    c->ict_tab, c->ict_qflags, c->ict_w0};
     for (void* b : bufs)
         if (b) cudaFree(b);
+    for (int k = 0; k < 2; ++k) {
+        if (c->ev_copied[k]) cudaEventDestroy(c->ev_copied[k]);
+        if (c->ev_read[k]) cudaEventDestroy(c->ev_read[k]);
+    }
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
-// Clear the device error word and the grid barrier's arrival count.  A block that gives up
-// in grid_barrier (FM_ERR_TIMEOUT) leaves its arrival counted; if the count survived into the
-// next launch sequence, a later barrier would open before every block had arrived.  So
-// every launch sequence starts from a zero count, and an error read back clears it too
-// (stream-ordered after the launch that timed out has finished).
+// The grid barrier's arrival count.  A block that gives up in grid_barrier (FM_ERR_TIMEOUT)
+// leaves its arrival counted; if the count survived into the next launch sequence, a later
+// barrier would open before every block had arrived.  So every launch sequence starts from
+// a zero count (stream-ordered after the launch that timed out has finished), and an error
+// read back clears it together with the error word.  The error word itself is cleared only
+// when it is read: an error of an earlier asynchronous call is reported by the next call
+// that synchronises.
+cudaError_t reset_barrier(fm_ctx* c) {
+    return cudaMemsetAsync(c->istate + I_BAR_COUNT, 0, sizeof(int), c->stream);
+}
 cudaError_t reset_dev(fm_ctx* c) {
     cudaError_t e = cudaMemsetAsync(c->istate + I_ERR, 0, sizeof(int), c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->istate + I_BAR_COUNT, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = reset_barrier(c);
     return e;
+}
+
+// Records a profiling event: inside a stream capture as an external event node of the graph
+// (so replays time the kernels), outside one as a plain record.  A failed record only loses
+// a timing, so its error is cleared rather than left for the next launch check to find.
+void prof_record(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    cudaError_t r = cudaStreamIsCapturing(s, &st);
+    if (r == cudaSuccess)
+        r = st == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                                                 : cudaEventRecord(e, s);
+    if (r != cudaSuccess) cudaGetLastError();
 }
 
 // Read back the device error word and clear it.
@@ -198,7 +240,7 @@ cudaError_t run_grad(fm_ctx* c, const void* w_in, const void* zdir, void* w_out,
 // forward (pivots when d != null) + backward substitution: p = (L L')^{-1} g
 template <typename T>
 cudaError_t run_ic0(fm_ctx* c, const void* d, const void* g, void* p, const void* gdot, const void* gpdot,
-                    int slot) {
+                    int slot, float* ip_lo = nullptr) {
     const size_t nint = 4 + 2 * (size_t)c->ntiles;
     cudaError_t e = cudaMemsetAsync(c->icint, 0, nint * sizeof(int), c->stream);
     if (e != cudaSuccess) return e;
@@ -210,12 +252,13 @@ cudaError_t run_ic0(fm_ctx* c, const void* d, const void* g, void* p, const void
     f.g = g;
     f.v = c->v;
     f.ip_out = c->ip;
+    f.ip_lo_out = ip_lo;
     {
         fm_ctx* pc = slot >= 0 ? c : nullptr;
-        if (pc && pc->profiling) cudaEventRecordWithFlags(pc->ev[slot][FM_K_IC_FWD][0], c->stream, cudaEventRecordExternal);
+        if (pc && pc->profiling) prof_record(pc->ev[slot][FM_K_IC_FWD][0], c->stream);
         e = launch_ic_fwd<T>(f, c->grid_ic, c->stream);
         if (pc && pc->profiling) {
-            cudaEventRecordWithFlags(pc->ev[slot][FM_K_IC_FWD][1], c->stream, cudaEventRecordExternal);
+            prof_record(pc->ev[slot][FM_K_IC_FWD][1], c->stream);
             pc->ev_rec[slot][FM_K_IC_FWD] = true;
         }
     }
@@ -231,13 +274,149 @@ cudaError_t run_ic0(fm_ctx* c, const void* d, const void* g, void* p, const void
     b.gdot = gdot;
     b.gpdot = gpdot;
     b.tile_part = (gdot || gpdot) ? c->tile_part : nullptr;
-    if (slot >= 0 && c->profiling) cudaEventRecordWithFlags(c->ev[slot][FM_K_IC_BWD][0], c->stream, cudaEventRecordExternal);
+    if (slot >= 0 && c->profiling) prof_record(c->ev[slot][FM_K_IC_BWD][0], c->stream);
     e = launch_ic_bwd<T>(b, c->grid_icb, c->stream);
     if (slot >= 0 && c->profiling) {
-        cudaEventRecordWithFlags(c->ev[slot][FM_K_IC_BWD][1], c->stream, cudaEventRecordExternal);
+        prof_record(c->ev[slot][FM_K_IC_BWD][1], c->stream);
         c->ev_rec[slot][FM_K_IC_BWD] = true;
     }
     return e;
+}
+
+// ------------------------------------------------------------------ drop-tolerance IC pattern
+
+// lexicographic (dz, dy, dx) order of offsets = natural order of the voxels they point to
+bool lex_less(const int* a, const int* b) {
+    if (a[2] != b[2]) return a[2] < b[2];
+    if (a[1] != b[1]) return a[1] < b[1];
+    return a[0] < b[0];
+}
+
+int ceil_div_pos(long long num, long long den) {  // ceil(num / den), den > 0
+    return (int)(num >= 0 ? (num + den - 1) / den : -((-num) / den));
+}
+
+// Builds the device tables of the held pattern c->ict_off (see IctTables), the level
+// coefficients, the candidate fill offsets, and (re)allocates the factor planes.  Synchronous.
+int ict_build(fm_ctx* c) {
+    const int nh = (int)c->ict_off.size() / 3;
+    const int* off = c->ict_off.data();
+    std::vector<int> ord(nh), hs(nh), pp(nh + 1, 0), pr, qoff, qp(1, 0), qpr;
+    for (int h = 0; h < nh; ++h) ord[h] = h;
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) { return lex_less(off + 3 * a, off + 3 * b); });
+    for (int h = 0; h < nh; ++h) {
+        const int* o = off + 3 * h;
+        hs[h] = (std::abs(o[0]) + std::abs(o[1]) + std::abs(o[2])) == 1 ? 1 : 0;
+    }
+    auto held = [&](int dx, int dy, int dz) {
+        for (int h = 0; h < nh; ++h)
+            if (off[3 * h] == dx && off[3 * h + 1] == dy && off[3 * h + 2] == dz) return h;
+        return -1;
+    };
+    for (int h = 0; h < nh; ++h) {  // pairs (p1, p2) with o_p1 - o_p2 = o_h
+        for (int p2 = 0; p2 < nh; ++p2) {
+            const int p1 = held(off[3 * h] + off[3 * p2], off[3 * h + 1] + off[3 * p2 + 1], off[3 * h + 2] + off[3 * p2 + 2]);
+            if (p1 >= 0) { pr.push_back(p1); pr.push_back(p2); }
+        }
+        pp[h + 1] = (int)pr.size() / 2;
+    }
+    // candidate fill: q = o_p1 - o_p2 pointing to an earlier voxel, not held
+    std::vector<std::vector<int>> cand;  // per candidate: dx, dy, dz, then its pairs
+    for (int p1 = 0; p1 < nh; ++p1)
+        for (int p2 = 0; p2 < nh; ++p2) {
+            const int q[3] = {off[3 * p1] - off[3 * p2], off[3 * p1 + 1] - off[3 * p2 + 1], off[3 * p1 + 2] - off[3 * p2 + 2]};
+            const int zero[3] = {0, 0, 0};
+            if (!lex_less(q, zero) || held(q[0], q[1], q[2]) >= 0) continue;
+            size_t k = 0;
+            for (; k < cand.size(); ++k)
+                if (cand[k][0] == q[0] && cand[k][1] == q[1] && cand[k][2] == q[2]) break;
+            if (k == cand.size()) cand.push_back({q[0], q[1], q[2]});
+            cand[k].push_back(p1);
+            cand[k].push_back(p2);
+        }
+    if ((int)cand.size() > kIctMaxCand) return fail(c, FM_ERR_FILL, "drop-tolerance IC: too many candidate fill offsets");
+    for (auto& q : cand) {
+        qoff.insert(qoff.end(), q.begin(), q.begin() + 3);
+        qpr.insert(qpr.end(), q.begin() + 3, q.end());
+        qp.push_back((int)qpr.size() / 2);
+    }
+    // level t = x + B y + C z with t(o) <= -1 for every held offset
+    int B = 1, C = 1;
+    for (int h = 0; h < nh; ++h) {
+        const int* o = off + 3 * h;
+        if (o[2] == 0 && o[1] < 0) B = std::max(B, ceil_div_pos((long long)o[0] + 1, -o[1]));
+    }
+    for (int h = 0; h < nh; ++h) {
+        const int* o = off + 3 * h;
+        if (o[2] < 0) C = std::max(C, ceil_div_pos((long long)o[0] + (long long)B * o[1] + 1, -o[2]));
+    }
+    const int nq = (int)cand.size();
+    std::vector<int> tab;
+    auto put = [&](const std::vector<int>& v) { const size_t at = tab.size(); tab.insert(tab.end(), v.begin(), v.end()); return at; };
+    const size_t a_off = put(c->ict_off), a_ord = put(ord), a_hs = put(hs), a_pp = put(pp), a_pr = put(pr),
+                 a_qoff = put(qoff), a_qp = put(qp), a_qpr = put(qpr);
+    if (c->ict_tab) { cudaFree(c->ict_tab); c->ict_tab = nullptr; }
+    if (c->ict_qflags) { cudaFree(c->ict_qflags); c->ict_qflags = nullptr; }
+    const int nflag = std::max(1, (nq + 31) / 32);
+    if (dalloc(&c->ict_tab, std::max<size_t>(tab.size(), 1) * sizeof(int)) != cudaSuccess ||
+        dalloc(&c->ict_qflags, nflag * sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, FM_ERR_OOM, "drop-tolerance IC tables");
+    }
+    FM_CK(cudaMemcpy(c->ict_tab, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice), "upload tables");
+    FM_CK(cudaMemset(c->ict_qflags, 0, nflag * sizeof(unsigned)), "clear flags");
+    IctTables& t = c->ict_tb;
+    t.nh = nh;
+    t.nq = nq;
+    t.B = B;
+    t.C = C;
+    t.off = c->ict_tab + a_off;
+    t.ord = c->ict_tab + a_ord;
+    t.hs = c->ict_tab + a_hs;
+    t.pp = c->ict_tab + a_pp;
+    t.pr = c->ict_tab + a_pr;
+    t.qoff = c->ict_tab + a_qoff;
+    t.qp = c->ict_tab + a_qp;
+    t.qpr = c->ict_tab + a_qpr;
+    t.qflags = c->ict_qflags;
+    c->ict_qoff = qoff;
+    if (nh + 2 > c->ict_nplanes) {  // grow the factor planes (the old factor is discarded)
+        FM_CK(cudaStreamSynchronize(c->stream), "synchronise");
+        if (c->ict_L) cudaFree(c->ict_L);
+        c->ict_L = nullptr;
+        c->ict_nplanes = 0;
+        if (dalloc(&c->ict_L, (size_t)(nh + 2) * c->nv * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, FM_ERR_OOM, "drop-tolerance IC factor planes");
+        }
+        c->ict_nplanes = nh + 2;
+        c->have_factor = false;
+    }
+    FM_CK(cudaMemset(c->ict_L, 0, (size_t)c->ict_nplanes * c->nv * sizeof(double)), "clear factor");
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }  // the tables are kernel arguments
+    if (c->cg_gexec) { cudaGraphExecDestroy(c->cg_gexec); c->cg_gexec = nullptr; }
+    return FM_OK;
+}
+
+// After a factorisation reported FM_ERR_FILL: hold every flagged candidate offset too.  Returns
+// 1 when the pattern grew, 0 when nothing was flagged, or an error (FM_ERR_FILL beyond
+// kIctMaxOffsets held offsets).  Synchronous.
+int ict_grow(fm_ctx* c) {
+    if (c->o.precond != FM_PC_ICT || !c->ict_qflags) return 0;
+    const int nq = c->ict_tb.nq;
+    std::vector<unsigned> fl(std::max(1, (nq + 31) / 32), 0u);
+    FM_CK(cudaMemcpy(fl.data(), c->ict_qflags, fl.size() * sizeof(unsigned), cudaMemcpyDeviceToHost), "read flags");
+    int added = 0;
+    for (int q = 0; q < nq; ++q)
+        if (fl[q >> 5] & (1u << (q & 31))) {
+            c->ict_off.insert(c->ict_off.end(), c->ict_qoff.begin() + 3 * q, c->ict_qoff.begin() + 3 * q + 3);
+            ++added;
+        }
+    if (!added) return 0;
+    if ((int)c->ict_off.size() / 3 > kIctMaxOffsets)
+        return fail(c, FM_ERR_FILL, "drop-tolerance IC: the kept fill needs more than 64 offsets");
+    const int rc = ict_build(c);
+    return rc == FM_OK ? 1 : rc;
 }
 
 // The same with the drop-tolerance IC (k_ict.cu): tau from H_max, factor + forward sweep,
@@ -254,6 +433,7 @@ cudaError_t run_ict(fm_ctx* c, const void* d, const void* g, void* p, const void
     a.d = d;
     a.g = g;
     a.L = c->ict_L;
+    a.tb = c->ict_tb;
     a.ip_out = d ? c->ip : nullptr;
     a.p = p;
     a.gdot = gdot;
@@ -269,10 +449,12 @@ cudaError_t run_ict(fm_ctx* c, const void* d, const void* g, void* p, const void
         e = launch_ict_tau<T>(t, c->o.droptol, c->grid_data, c->stream);
         if (e != cudaSuccess) return e;
     }
-    if (prof) cudaEventRecordWithFlags(c->ev[slot][FM_K_IC_FWD][0], c->stream, cudaEventRecordExternal);
-    e = launch_ict_fwd<T>(a, c->grid_ict, c->block_ict, c->stream);
+    const bool base = c->ict_tb.nh == kIctBaseOffsets;  // the unrolled kernels hold exactly the base pattern
+    if (prof) prof_record(c->ev[slot][FM_K_IC_FWD][0], c->stream);
+    e = base ? launch_ict_fwd<T>(a, c->grid_ict, c->block_ict, c->stream)
+             : launch_ictg_fwd<T>(a, c->grid_ictg, c->block_ict, c->stream);
     if (prof) {
-        cudaEventRecordWithFlags(c->ev[slot][FM_K_IC_FWD][1], c->stream, cudaEventRecordExternal);
+        prof_record(c->ev[slot][FM_K_IC_FWD][1], c->stream);
         c->ev_rec[slot][FM_K_IC_FWD] = true;
     }
     if (e != cudaSuccess) return e;
@@ -280,10 +462,11 @@ cudaError_t run_ict(fm_ctx* c, const void* d, const void* g, void* p, const void
         e = launch_ict_check<T>(a, c->grid_data, c->stream);
         if (e != cudaSuccess) return e;
     }
-    if (prof) cudaEventRecordWithFlags(c->ev[slot][FM_K_IC_BWD][0], c->stream, cudaEventRecordExternal);
-    e = launch_ict_bwd<T>(a, c->grid_ict, c->block_ict, c->stream);
+    if (prof) prof_record(c->ev[slot][FM_K_IC_BWD][0], c->stream);
+    e = base ? launch_ict_bwd<T>(a, c->grid_ict, c->block_ict, c->stream)
+             : launch_ictg_bwd<T>(a, c->grid_ictg, c->block_ict, c->stream);
     if (prof) {
-        cudaEventRecordWithFlags(c->ev[slot][FM_K_IC_BWD][1], c->stream, cudaEventRecordExternal);
+        prof_record(c->ev[slot][FM_K_IC_BWD][1], c->stream);
         c->ev_rec[slot][FM_K_IC_BWD] = true;
     }
     return e;
@@ -302,11 +485,11 @@ struct Mark {
     fm_ctx* c;
     int cur, k;
     Mark(fm_ctx* c_, int cur_, int k_) : c(c_), cur(cur_), k(k_) {
-        if (c->profiling) cudaEventRecordWithFlags(c->ev[cur][k][0], c->stream, cudaEventRecordExternal);
+        if (c->profiling) prof_record(c->ev[cur][k][0], c->stream);
     }
     ~Mark() {
         if (c->profiling) {
-            cudaEventRecordWithFlags(c->ev[cur][k][1], c->stream, cudaEventRecordExternal);
+            prof_record(c->ev[cur][k][1], c->stream);
             c->ev_rec[cur][k] = true;
         }
     }
@@ -371,7 +554,7 @@ cudaError_t iteration(fm_ctx* c, int cur) {
 
 // Enqueue everything a solve needs before its first outer iteration.
 template <typename T>
-int solve_begin(fm_ctx* c, void* omega, int init, int niter) {
+int solve_begin(fm_ctx* c, void* omega, int init, int niter, bool host_io = false) {
     if (niter + 1 > c->hist_cap) {
         if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
         cudaFree(c->hist_cost); cudaFree(c->hist_alpha); cudaFree(c->hist_mu);
@@ -386,10 +569,13 @@ int solve_begin(fm_ctx* c, void* omega, int init, int niter) {
     }
     const size_t vb = (size_t)c->nv * c->ts;
     cudaStream_t s = c->stream;
-    FM_CK(reset_dev(c), "reset");
+    FM_CK(reset_barrier(c), "reset");
     // the kernels write mask voxels only: every entry outside the mask starts (and stays) 0
     if (init) {
         FM_CK(cudaMemcpyAsync(c->w[0], c->w0, vb, cudaMemcpyDeviceToDevice, s), "copy omega");
+    } else if (host_io) {  // through w[1], which is cleared next
+        FM_CK(cudaMemcpyAsync(c->w[1], omega, vb, cudaMemcpyHostToDevice, s), "copy omega in");
+        FM_CK(launch_masked_copy<T>(c->w[1], c->w[0], c->nb, c->nv, c->grid_data, s), "copy omega");
     } else {
         FM_CK(launch_masked_copy<T>(omega, c->w[0], c->nb, c->nv, c->grid_data, s), "copy omega");
     }
@@ -407,12 +593,17 @@ int solve_begin(fm_ctx* c, void* omega, int init, int niter) {
 
 // Enqueue the last update, the copy of the field map out and of the cost history.
 template <typename T>
-int solve_end(fm_ctx* c, void* omega, int niter, double* cost_hist) {
+int solve_end(fm_ctx* c, void* omega, int niter, double* cost_hist, bool host_io = false) {
     const size_t vb = (size_t)c->nv * c->ts;
     cudaStream_t s = c->stream;
     const int cur = niter & 1;
     FM_CK(run_grad<T>(c, c->w[cur], c->z[cur], c->w[cur ^ 1], c->g[cur], c->d, c->hist_cost), "final update");
-    FM_CK(cudaMemcpyAsync(omega, c->w[cur ^ 1], vb, cudaMemcpyDeviceToDevice, s), "copy omega out");
+    if (host_io) {
+        Mark m(c, 0, FM_K_D2H);
+        FM_CK(cudaMemcpyAsync(omega, c->w[cur ^ 1], vb, cudaMemcpyDeviceToHost, s), "copy omega out");
+    } else {
+        FM_CK(cudaMemcpyAsync(omega, c->w[cur ^ 1], vb, cudaMemcpyDeviceToDevice, s), "copy omega out");
+    }
     if (cost_hist)
         FM_CK(cudaMemcpyAsync(cost_hist, c->hist_cost, (niter + 1) * sizeof(double), cudaMemcpyDeviceToHost, s),
               "copy cost history");
@@ -420,9 +611,51 @@ int solve_end(fm_ctx* c, void* omega, int niter, double* cost_hist) {
     return FM_OK;
 }
 
+constexpr int kIctMaxRounds = 64;  // pattern growths one call may go through
+
+// Enqueues the whole solve; synchronises (and reports device errors) only when the cost
+// history is requested -- or with the drop-tolerance IC, which checks every solve: when a
+// factorisation keeps fill outside the held pattern, the pattern grows and the solve runs
+// again from the same start (a larger held pattern gives the identical factor, so the result
+// is the drop-tolerance solve itself).
 template <typename T>
-int solve_t(fm_ctx* c, void* omega, int init, int niter, double* cost_hist) {
-    int rc = solve_begin<T>(c, omega, init, niter);
+int solve_once(fm_ctx* c, const void* omega_in, bool in_host, void* omega_out, bool out_host, int init, int niter,
+               double* cost_hist);
+
+template <typename T>
+int solve_t(fm_ctx* c, void* omega, int init, int niter, double* cost_hist, bool host_io = false) {
+    if (c->o.precond != FM_PC_ICT) {
+        const int rc = solve_once<T>(c, omega, host_io, omega, host_io, init, niter, cost_hist);
+        if (rc != FM_OK) return rc;
+        return cost_hist ? check_dev(c) : FM_OK;
+    }
+    const void* in = omega;
+    bool in_host = host_io;
+    if (!init) {  // keep the start map: the output overwrites omega
+        const size_t vb = (size_t)c->nv * c->ts;
+        if (!c->ict_w0 && dalloc(&c->ict_w0, vb) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, FM_ERR_OOM, "allocate start map");
+        }
+        FM_CK(cudaMemcpyAsync(c->ict_w0, omega, vb, host_io ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                              c->stream), "keep start map");
+        in = c->ict_w0;
+        in_host = false;
+    }
+    for (int round = 0;; ++round) {
+        int rc = solve_once<T>(c, in, in_host, omega, host_io, init, niter, cost_hist);
+        if (rc != FM_OK) return rc;
+        rc = check_dev(c);
+        if (rc != FM_ERR_FILL || round >= kIctMaxRounds) return rc;
+        const int g = ict_grow(c);
+        if (g <= 0) return g < 0 ? g : rc;
+    }
+}
+
+template <typename T>
+int solve_once(fm_ctx* c, const void* omega_in, bool in_host, void* omega_out, bool out_host, int init, int niter,
+               double* cost_hist) {
+    int rc = solve_begin<T>(c, const_cast<void*>(omega_in), init, niter, in_host);
     if (rc != FM_OK) return rc;
     cudaStream_t s = c->stream;
     int i = 0;
@@ -442,9 +675,7 @@ int solve_t(fm_ctx* c, void* omega, int init, int niter, double* cost_hist) {
         for (; i + 2 <= niter; i += 2) FM_CK(cudaGraphLaunch(c->gexec, s), "launch graph");
     }
     for (; i < niter; ++i) FM_CK(iteration<T>(c, i & 1), "launch iteration");
-    rc = solve_end<T>(c, omega, niter, cost_hist);
-    if (rc != FM_OK) return rc;
-    return check_dev(c);
+    return solve_end<T>(c, omega_out, niter, cost_hist, out_host);
 }
 
 // ------------------------------------------------------------------ implicit differentiation
@@ -497,7 +728,7 @@ int adjoint_t(fm_ctx* c, const void* w_hat, const void* rhs, void* lambda, doubl
     cudaStream_t s = c->stream;
     const size_t vb = (size_t)c->nv * c->ts;
     const double tol2 = tol * tol;
-    FM_CK(reset_dev(c), "reset");
+    FM_CK(reset_barrier(c), "reset");
     // majoriser curvature d(w_hat) for the preconditioner (Eq. 9-12)
     FM_CK(run_grad<T>(c, w_hat, nullptr, c->w[1], c->g[1], c->d, nullptr), "curvature");
     void* zero[] = {c->w[0], c->g[0], c->z[0], c->z[1], c->g[1]};
@@ -564,7 +795,7 @@ int implicit_t(fm_ctx* c, const void* y, const void* smap, const void* w_hat, co
     a.y = y;
     a.smap = smap;
     a.dldy = dl_dy;
-    FM_CK(reset_dev(c), "reset");
+    FM_CK(reset_barrier(c), "reset");
     if (dl_dy) FM_CK(launch_dldy<T>(a, c->grid_data, c->stream), "image derivative kernel");
     if (dl_dbeta) {
         FM_CK(launch_lap_dot<T>(a, c->grid_data, c->stream), "beta derivative kernel");
@@ -608,7 +839,7 @@ template <typename T>
 int pwls_t(fm_ctx* c, const void* wt, int niter, void* w0) {
     cudaStream_t s = c->stream;
     const size_t vb = (size_t)c->nv * c->ts;
-    FM_CK(reset_dev(c), "reset");
+    FM_CK(reset_barrier(c), "reset");
     void* zero[] = {c->w[0], c->g[0], c->z[0], c->z[1], c->g[1]};
     for (void* b : zero) FM_CK(cudaMemsetAsync(b, 0, vb, s), "clear CG vectors");
     AdjArgs a = adj_args(c);
@@ -752,6 +983,12 @@ int fm_create(fm_ctx** out, int nx, int ny, int nz, int ncoil, int necho, const 
         c->grid_ict = (int)std::max(1LL, std::min<long long>((cols + c->block_ict - 1) / c->block_ict,
                                                              (long long)occ * c->nsm));
         c->base_ict = c->grid_ict;
+        const int occg = o.precision == FM_FP64 ? ictg_max_blocks_per_sm<double>(c->block_ict)
+                                                : ictg_max_blocks_per_sm<float>(c->block_ict);
+        if (occg < 1) return bail(FM_ERR_CUDA);
+        c->grid_ictg = (int)std::max(1LL, std::min<long long>((cols + c->block_ict - 1) / c->block_ict,
+                                                              (long long)occg * c->nsm));
+        c->base_ictg = c->grid_ictg;
     }
     const size_t vb = (size_t)c->nv * c->ts;
     const int P = necho * (necho - 1) / 2;
@@ -774,7 +1011,7 @@ int fm_create(fm_ctx** out, int nx, int ny, int nz, int ncoil, int necho, const 
     A(&c->istate, I_NISTATE * sizeof(int));
     A(&c->icint, (4 + 2 * (size_t)c->ntiles) * sizeof(int));
     A(&c->order, 2 * (size_t)c->ntiles * sizeof(int));  // forward order, then the back substitution's
-    if (o.precond == FM_PC_ICT) A(&c->ict_L, (size_t)kIctPlanes * c->nv * sizeof(double));
+
     if (!ok) { cudaGetLastError(); return bail(FM_ERR_OOM); }
 #ifndef FM_IC_WXY
 #define FM_IC_WXY 2
@@ -782,6 +1019,10 @@ int fm_create(fm_ctx** out, int nx, int ny, int nz, int ncoil, int necho, const 
 #ifndef FM_IC_WZ
 #define FM_IC_WZ 1
 #endif
+    if (o.precond == FM_PC_ICT) {  // IC(0)'s offsets and the level-1 fill offsets, in plane order
+        c->ict_off = {-1, 0, 0, 0, -1, 0, 0, 0, -1, 1, -1, 0, 1, 0, -1, 0, 1, -1};
+        if (ict_build(c) != FM_OK) return bail(FM_ERR_OOM);
+    }
     if (!set_ic_order(c, FM_IC_WXY, FM_IC_WZ) ||
         cudaMemset(c->scal, 0, S_NSCAL * sizeof(double)) != cudaSuccess ||
         cudaMemset(c->istate, 0, I_NISTATE * sizeof(int)) != cudaSuccess ||
@@ -811,6 +1052,7 @@ int fm_set_data(fm_ctx* c, const void* y, const void* smap, const double* te, co
         if (!std::isfinite(te[l])) return fail(c, FM_ERR_ARG, "echo times must be finite");
     if (te[1] == te[0]) return fail(c, FM_ERR_ARG, "t_2 == t_1 (Eq. 6 divides by t_2 - t_1)");
     DevGuard guard(c->device);
+    const double old_beta = c->beta;
     c->beta = beta;
     for (int l = 0; l < c->L; ++l) c->te[l] = te[l];
     // Eq. gamma: Gamma = 1/L, or gamma (gamma^H gamma)^{-1} gamma^H with gamma = [1, phi]
@@ -857,9 +1099,17 @@ int fm_set_data(fm_ctx* c, const void* y, const void* smap, const double* te, co
             pr.gph[pr.P] = c->wf ? std::arg(lgam[(size_t)m * c->L + n]) : 0.0;
             ++pr.P;
         }
+    // beta and the pair constants are kernel arguments of the captured graphs: keep the
+    // graphs only when they are unchanged (every buffer the graphs use belongs to the context)
+    bool same = c->have_data && beta == old_beta && pr.P == c->pr.P;
+    for (int q = 0; same && q < pr.P; ++q)
+        same = pr.m[q] == c->pr.m[q] && pr.n[q] == c->pr.n[q] && pr.dt[q] == c->pr.dt[q] &&
+               pr.gmag[q] == c->pr.gmag[q] && pr.gph[q] == c->pr.gph[q];
     c->pr = pr;
-    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }  // beta / dt are graph arguments
-    if (c->cg_gexec) { cudaGraphExecDestroy(c->cg_gexec); c->cg_gexec = nullptr; }
+    if (!same) {
+        if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+        if (c->cg_gexec) { cudaGraphExecDestroy(c->cg_gexec); c->cg_gexec = nullptr; }
+    }
     SetupArgs a{};
     a.geo = Geo{c->nx, c->ny, c->nz, c->nv};
     a.nc = c->nc;
@@ -891,7 +1141,7 @@ int fm_set_data(fm_ctx* c, const void* y, const void* smap, const double* te, co
     if (e != cudaSuccess) return cuda_fail(c, e, "setup kernel");
     // rows outside the new mask must read as empty in the drop-tolerance factor
     if (c->ict_L)
-        FM_CK(cudaMemsetAsync(c->ict_L, 0, (size_t)kIctPlanes * c->nv * sizeof(double), c->stream), "clear factor");
+        FM_CK(cudaMemsetAsync(c->ict_L, 0, (size_t)c->ict_nplanes * c->nv * sizeof(double), c->stream), "clear factor");
     c->have_data = true;
     c->have_factor = false;
     return FM_OK;
@@ -927,16 +1177,10 @@ int fm_cost_grad(fm_ctx* c, const void* omega, double* cost, void* grad, void* c
     return FM_OK;
 }
 
-int fm_ic_factor(fm_ctx* c, const void* omega, void* inv_pivot) {
-    if (!c) return FM_ERR_ARG;
-    if (!omega) return fail(c, FM_ERR_ARG, "omega is required");
-    if (!c->have_data) return fail(c, FM_ERR_STATE, "fm_set_data first");
-    DevGuard guard(c->device);
+// The preconditioner factor of H = diag(d) + beta C'C with d already in c->d (Eq. 9, 12).
+int ic_factor_from_d(fm_ctx* c, void* inv_pivot) {
     const bool f64 = c->o.precision == FM_FP64;
-    FM_CK(cudaMemsetAsync(c->istate + I_BAR_COUNT, 0, sizeof(int), c->stream), "reset barrier");
-    cudaError_t e = f64 ? run_grad<double>(c, omega, nullptr, c->w[0], c->g[0], c->d, nullptr)
-                        : run_grad<float>(c, omega, nullptr, c->w[0], c->g[0], c->d, nullptr);
-    if (e != cudaSuccess) return cuda_fail(c, e, "gradient kernel");
+    cudaError_t e;
     if (c->o.precond == FM_PC_RB) {  // red-black pivots of both colours
         DataArgs a = base_args(c);
         a.d = c->d;
@@ -950,8 +1194,83 @@ int fm_ic_factor(fm_ctx* c, const void* omega, void* inv_pivot) {
                 : run_ic<float>(c, c->d, c->g[0], c->p, nullptr, nullptr);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "IC(0) kernels");
+    if (c->o.precond == FM_PC_ICT) {  // grow the held pattern until the factor is exact (synchronous)
+        for (int round = 0;; ++round) {
+            const int rc = check_dev(c);
+            if (rc != FM_ERR_FILL || round >= kIctMaxRounds) {
+                if (rc != FM_OK) return rc;
+                break;
+            }
+            const int g = ict_grow(c);
+            if (g <= 0) return g < 0 ? g : rc;
+            e = f64 ? run_ic<double>(c, c->d, c->g[0], c->p, nullptr, nullptr)
+                    : run_ic<float>(c, c->d, c->g[0], c->p, nullptr, nullptr);
+            if (e != cudaSuccess) return cuda_fail(c, e, "IC kernels");
+        }
+    }
     if (inv_pivot)
         FM_CK(cudaMemcpyAsync(inv_pivot, c->ip, (size_t)c->nv * c->ts, cudaMemcpyDeviceToDevice, c->stream), "copy");
+    c->have_factor = true;
+    return FM_OK;
+}
+
+int fm_ic_factor(fm_ctx* c, const void* omega, void* inv_pivot) {
+    if (!c) return FM_ERR_ARG;
+    if (!omega) return fail(c, FM_ERR_ARG, "omega is required");
+    if (!c->have_data) return fail(c, FM_ERR_STATE, "fm_set_data first");
+    DevGuard guard(c->device);
+    FM_CK(reset_barrier(c), "reset barrier");
+    cudaError_t e = c->o.precision == FM_FP64 ? run_grad<double>(c, omega, nullptr, c->w[0], c->g[0], c->d, nullptr)
+                                              : run_grad<float>(c, omega, nullptr, c->w[0], c->g[0], c->d, nullptr);
+    if (e != cudaSuccess) return cuda_fail(c, e, "gradient kernel");
+    return ic_factor_from_d(c, inv_pivot);
+}
+
+int fm_ic_factor_curv(fm_ctx* c, const void* curv, void* inv_pivot) {
+    if (!c) return FM_ERR_ARG;
+    if (!curv) return fail(c, FM_ERR_ARG, "curv is required");
+    if (!c->have_data) return fail(c, FM_ERR_STATE, "fm_set_data first");
+    DevGuard guard(c->device);
+    FM_CK(reset_barrier(c), "reset barrier");
+    const size_t vb = (size_t)c->nv * c->ts;
+    // only mask voxels are read by the factor kernels
+    FM_CK(cudaMemcpyAsync(c->d, curv, vb, cudaMemcpyDeviceToDevice, c->stream), "copy curvature");
+    FM_CK(cudaMemsetAsync(c->g[0], 0, vb, c->stream), "clear");
+    return ic_factor_from_d(c, inv_pivot);
+}
+
+int fm_ict_pattern(fm_ctx* c, int* n_offsets, int* offsets, double* planes) {
+    if (!c || !n_offsets) return FM_ERR_ARG;
+    if (c->o.precond != FM_PC_ICT) return fail(c, FM_ERR_STATE, "fm_ict_pattern is for FM_PC_ICT");
+    DevGuard guard(c->device);
+    const int nh = c->ict_tb.nh;
+    *n_offsets = nh;
+    if (offsets) std::memcpy(offsets, c->ict_off.data(), 3 * (size_t)nh * sizeof(int));
+    if (planes) {
+        if (!c->have_factor) return fail(c, FM_ERR_STATE, "fm_ic_factor first");
+        FM_CK(cudaStreamSynchronize(c->stream), "synchronise");
+        FM_CK(cudaMemcpy(planes, c->ict_L, (size_t)(nh + 1) * c->nv * sizeof(double), cudaMemcpyDeviceToHost),
+              "copy factor");
+    }
+    return FM_OK;
+}
+
+int fm_ic_factor64(fm_ctx* c, const void* omega, double* inv_pivot) {
+    if (!c) return FM_ERR_ARG;
+    if (!omega || !inv_pivot) return fail(c, FM_ERR_ARG, "omega and inv_pivot are required");
+    if (!c->have_data) return fail(c, FM_ERR_STATE, "fm_set_data first");
+    if (c->o.precond != FM_PC_IC0) return fail(c, FM_ERR_STATE, "fm_ic_factor64 is for the IC(0) preconditioner");
+    if (c->o.precision == FM_FP64) return fm_ic_factor(c, omega, inv_pivot);
+    DevGuard guard(c->device);
+    if (!c->ip_lo && dalloc(&c->ip_lo, (size_t)c->nv * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, FM_ERR_OOM, "allocate pivot buffer");
+    }
+    FM_CK(reset_barrier(c), "reset barrier");
+    FM_CK(run_grad<float>(c, omega, nullptr, c->w[0], c->g[0], c->d, nullptr), "gradient kernel");
+    FM_CK(cudaMemsetAsync(c->ip_lo, 0, (size_t)c->nv * sizeof(float), c->stream), "clear");
+    FM_CK(run_ic0<float>(c, c->d, c->g[0], c->p, nullptr, nullptr, -1, c->ip_lo), "IC(0) kernels");
+    FM_CK(launch_inv_pivot64((const float*)c->ip, c->ip_lo, inv_pivot, c->nv, c->grid_data, c->stream), "combine");
     c->have_factor = true;
     return FM_OK;
 }
@@ -961,7 +1280,7 @@ int fm_ic_apply(fm_ctx* c, const void* g, void* p) {
     if (!g || !p || g == p) return fail(c, FM_ERR_ARG, "g and p must be distinct device arrays");
     if (!c->have_factor) return fail(c, FM_ERR_STATE, "fm_ic_factor first");
     DevGuard guard(c->device);
-    FM_CK(cudaMemsetAsync(c->istate + I_BAR_COUNT, 0, sizeof(int), c->stream), "reset barrier");
+    FM_CK(reset_barrier(c), "reset barrier");
     cudaError_t e;
     if (c->o.precond == FM_PC_RB) {
         DataArgs a = base_args(c);
@@ -992,6 +1311,69 @@ int fm_solve(fm_ctx* c, void* omega, int init_from_data, int niter, double* cost
                                      : solve_t<float>(c, omega, init_from_data, niter, cost_hist);
 }
 
+int fm_set_data_host(fm_ctx* c, const void* y, const void* smap, const double* te, const uint8_t* mask,
+                     double beta) {
+    if (!c) return FM_ERR_ARG;
+    if (!y || !te) return fail(c, FM_ERR_ARG, "y and te are required");
+    if (!smap && c->nc != 1) return fail(c, FM_ERR_ARG, "smap may be NULL only with one coil");
+    if (!(beta >= 0.0) || !std::isfinite(beta)) return fail(c, FM_ERR_ARG, "beta must be finite and >= 0");
+    for (int l = 0; l < c->L; ++l)
+        if (!std::isfinite(te[l])) return fail(c, FM_ERR_ARG, "echo times must be finite");
+    if (te[1] == te[0]) return fail(c, FM_ERR_ARG, "t_2 == t_1 (Eq. 6 divides by t_2 - t_1)");
+    DevGuard guard(c->device);
+    const size_t cb = 2 * c->ts;  // one complex value
+    const size_t yb = (size_t)c->L * c->nc * c->nv * cb, sb = (size_t)c->nc * c->nv * cb, mb = (size_t)c->nv;
+    if (!c->copy_stream) {
+        FM_CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking), "create copy stream");
+        for (int k = 0; k < 2; ++k) {
+            FM_CK(cudaEventCreateWithFlags(&c->ev_copied[k], cudaEventDisableTiming), "create event");
+            FM_CK(cudaEventCreateWithFlags(&c->ev_read[k], cudaEventDisableTiming), "create event");
+        }
+    }
+    const int k = c->st_next;
+    if (!c->st_y[k]) {
+        bool ok = dalloc(&c->st_y[k], yb) == cudaSuccess && dalloc(&c->st_s[k], sb) == cudaSuccess &&
+                  dalloc(&c->st_m[k], mb) == cudaSuccess;
+        if (!ok) { cudaGetLastError(); return fail(c, FM_ERR_OOM, "allocate staging buffers"); }
+    }
+    c->st_next ^= 1;
+    cudaStream_t cs = c->copy_stream;
+    // the precompute that last read this staging set must be done before it is overwritten
+    FM_CK(cudaStreamWaitEvent(cs, c->ev_read[k], 0), "order copy");
+    const bool prof = c->profiling && c->ev[k][FM_K_H2D][0];
+    if (prof) FM_CK(cudaEventRecord(c->ev[k][FM_K_H2D][0], cs), "record");
+    FM_CK(cudaMemcpyAsync(c->st_y[k], y, yb, cudaMemcpyHostToDevice, cs), "copy y");
+    if (smap) FM_CK(cudaMemcpyAsync(c->st_s[k], smap, sb, cudaMemcpyHostToDevice, cs), "copy smap");
+    if (mask) FM_CK(cudaMemcpyAsync(c->st_m[k], mask, mb, cudaMemcpyHostToDevice, cs), "copy mask");
+    if (prof) {
+        FM_CK(cudaEventRecord(c->ev[k][FM_K_H2D][1], cs), "record");
+        c->ev_rec[k][FM_K_H2D] = true;
+    }
+    FM_CK(cudaEventRecord(c->ev_copied[k], cs), "record copy");
+    FM_CK(cudaStreamWaitEvent(c->stream, c->ev_copied[k], 0), "order precompute");
+    const int rc = fm_set_data(c, c->st_y[k], smap ? c->st_s[k] : nullptr, te, mask ? c->st_m[k] : nullptr, beta);
+    FM_CK(cudaEventRecord(c->ev_read[k], c->stream), "record precompute");
+    return rc;
+}
+
+int fm_solve_host(fm_ctx* c, void* omega, int init_from_data, int niter, double* cost_hist) {
+    if (!c) return FM_ERR_ARG;
+    if (!omega) return fail(c, FM_ERR_ARG, "omega is required");
+    if (niter < 0) return fail(c, FM_ERR_ARG, "niter must be >= 0");
+    if (!c->have_data) return fail(c, FM_ERR_STATE, "fm_set_data first");
+    DevGuard guard(c->device);
+    c->have_factor = false;
+    return c->o.precision == FM_FP64 ? solve_t<double>(c, omega, init_from_data, niter, cost_hist, true)
+                                     : solve_t<float>(c, omega, init_from_data, niter, cost_hist, true);
+}
+
+int fm_synchronize(fm_ctx* c) {
+    if (!c) return FM_ERR_ARG;
+    DevGuard guard(c->device);
+    if (c->copy_stream) FM_CK(cudaStreamSynchronize(c->copy_stream), "synchronise copies");
+    return check_dev(c);
+}
+
 int fm_true_curv(fm_ctx* c, const void* omega, void* h) {
     if (!c) return FM_ERR_ARG;
     if (!omega || !h) return fail(c, FM_ERR_ARG, "omega and h are required");
@@ -1015,8 +1397,14 @@ int fm_adjoint_solve(fm_ctx* c, const void* omega_hat, const void* rhs, void* la
     if (maxiter < 0) return fail(c, FM_ERR_ARG, "maxiter must be >= 0");
     if (!c->have_data) return fail(c, FM_ERR_STATE, "fm_set_data first");
     DevGuard guard(c->device);
-    return c->o.precision == FM_FP64 ? adjoint_t<double>(c, omega_hat, rhs, lambda, tol, maxiter, iters, relres)
-                                     : adjoint_t<float>(c, omega_hat, rhs, lambda, tol, maxiter, iters, relres);
+    for (int round = 0;; ++round) {  // with the drop-tolerance IC: grow its pattern and solve again
+        const int rc = c->o.precision == FM_FP64
+                           ? adjoint_t<double>(c, omega_hat, rhs, lambda, tol, maxiter, iters, relres)
+                           : adjoint_t<float>(c, omega_hat, rhs, lambda, tol, maxiter, iters, relres);
+        if (rc != FM_ERR_FILL || round >= kIctMaxRounds) return rc;
+        const int g = ict_grow(c);
+        if (g <= 0) return g < 0 ? g : rc;
+    }
 }
 
 int fm_implicit_grad(fm_ctx* c, const void* y, const void* smap, const void* omega_hat, const void* lambda,
@@ -1212,6 +1600,7 @@ void batch_apply_fraction(fm_batch* b) {
         c->grid_ic = std::max(1, (int)std::lround(c->base_ic * b->fraction));
         c->grid_icb = std::max(1, (int)std::lround(c->base_icb * b->fraction));
         if (c->base_ict) c->grid_ict = std::max(1, (int)std::lround(c->base_ict * b->fraction));
+        if (c->base_ictg) c->grid_ictg = std::max(1, (int)std::lround(c->base_ictg * b->fraction));
         if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
     }
     if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
@@ -1236,12 +1625,13 @@ cudaError_t batch_join(fm_batch* b) {
 }
 
 template <typename T>
-int batch_solve_t(fm_batch* b, void* const* omega, int init, int niter, double* const* cost_hist) {
+int batch_solve_t(fm_batch* b, void* const* omega_in, void* const* omega, int init, int niter,
+                  double* const* cost_hist) {
     const size_t n = b->v.size();
     auto fail_b = [&](int code, const std::string& m) { b->err = m; return code; };
     if (batch_fork(b) != cudaSuccess) return fail_b(FM_ERR_CUDA, "fork");
     for (size_t k = 0; k < n; ++k) {
-        const int rc = solve_begin<T>(b->v[k], omega[k], init, niter);
+        const int rc = solve_begin<T>(b->v[k], omega_in[k], init, niter);
         if (rc != FM_OK) return fail_b(rc, "volume " + std::to_string(k) + ": " + b->v[k]->err);
     }
     int i = 0;
@@ -1295,9 +1685,14 @@ int batch_solve_t(fm_batch* b, void* const* omega, int init, int niter, double* 
     return first;
 }
 
+int batch_solve_io(fm_batch* b, void* const* omega_in, void* const* omega, int init, int niter,
+                   double* const* cost_hist) {
+    return b->precision == FM_FP64 ? batch_solve_t<double>(b, omega_in, omega, init, niter, cost_hist)
+                                   : batch_solve_t<float>(b, omega_in, omega, init, niter, cost_hist);
+}
+
 int batch_solve(fm_batch* b, void* const* omega, int init, int niter, double* const* cost_hist) {
-    return b->precision == FM_FP64 ? batch_solve_t<double>(b, omega, init, niter, cost_hist)
-                                   : batch_solve_t<float>(b, omega, init, niter, cost_hist);
+    return batch_solve_io(b, omega, omega, init, niter, cost_hist);
 }
 
 }  // namespace
@@ -1361,7 +1756,32 @@ int fm_batch_solve(fm_batch* b, void* const* omega, int init_from_data, int nite
         if (!b->v[k]->have_data) return FM_ERR_STATE;
     }
     DevGuard guard(b->device);
-    return batch_solve(b, omega, init_from_data, niter, cost_hist);
+    // the drop-tolerance IC: a volume whose factor keeps fill outside its held pattern grows the
+    // pattern and the batch runs again from the same starts
+    std::vector<void*> w0;
+    std::vector<void*> in(omega, omega + b->v.size());
+    if (!init_from_data && b->v[0]->o.precond == FM_PC_ICT) {
+        for (size_t k = 0; k < b->v.size(); ++k) {
+            fm_ctx* c = b->v[k];
+            const size_t vb = (size_t)c->nv * c->ts;
+            if (!c->ict_w0 && dalloc(&c->ict_w0, vb) != cudaSuccess) { cudaGetLastError(); return FM_ERR_OOM; }
+            if (cudaMemcpyAsync(c->ict_w0, omega[k], vb, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+                return FM_ERR_CUDA;
+            in[k] = c->ict_w0;
+        }
+    }
+    for (int round = 0;; ++round) {
+        int rc = batch_solve_io(b, in.data(), omega, init_from_data, niter, cost_hist);
+        if (rc != FM_ERR_FILL || round >= kIctMaxRounds) return rc;
+        int grew = 0;
+        for (fm_ctx* c : b->v) {
+            const int g = ict_grow(c);
+            if (g < 0) return g;
+            grew += g;
+        }
+        if (!grew) return rc;
+        if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    }
 }
 
 int fm_batch_set_fraction(fm_batch* b, double fraction) {

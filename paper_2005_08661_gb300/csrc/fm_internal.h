@@ -268,6 +268,7 @@ struct IcArgs {
     const void* g;         // T [nv] right-hand side
     void* v;               // T [nv] forward result
     void* ip_out;          // T [nv] inverse pivots (compute mode)
+    float* ip_lo_out;      // FP32 mode, nullable: low float of each inverse pivot (1/pi = hi + lo)
     void* face;            // per-tile face buffer (pivots, v, p)
     // backward
     const void* vin;       // T [nv]
@@ -281,11 +282,29 @@ struct IcArgs {
     long long spin_limit;
 };
 
-// IC with a drop tolerance (k_ict.cu) on the pattern of IC(0) plus the level-1 fill offsets.
-// Factor planes, each [nv] double: 1 / L_ii, then L_{i,i+o} for the offsets o = (-1,0,0),
-// (0,-1,0), (0,0,-1), (1,-1,0), (1,0,-1), (0,1,-1), then the substitution vector.
-constexpr int kIctPlanes = 8;
-constexpr int kIctThreads = 1024;  // most threads per block of the level sweeps (one per (y, z) column)
+// IC with a drop tolerance (k_ict.cu).  The factor is held on a set of nh grid offsets o
+// (each pointing to an earlier voxel in natural order): factor planes, each [nv] double:
+// plane 0 = 1 / L_ii, plane 1 + h = L_{i,i+o_h}, plane 1 + nh = the substitution vector.
+// The first six offsets are always IC(0)'s (-1,0,0), (0,-1,0), (0,0,-1) and the level-1 fill
+// offsets (1,-1,0), (1,0,-1), (0,1,-1); with exactly those the sweeps take the unrolled
+// kernels, with more (fill the tolerance keeps beyond level 1) the table-driven ones.
+constexpr int kIctBaseOffsets = 6;
+constexpr int kIctPlanes = kIctBaseOffsets + 2;
+constexpr int kIctMaxOffsets = 64;  // largest held pattern; beyond it the call reports FM_ERR_FILL
+constexpr int kIctMaxCand = 4096;   // largest set of candidate fill offsets the check examines
+constexpr int kIctThreads = 1024;   // most threads per block of the level sweeps (one per (y, z) column)
+
+// Tables of a held pattern (device, int): off[3 nh] (dx, dy, dz by plane), ord[nh] (planes in
+// increasing column order), hs[nh] (1: a stencil offset, H_{i,i+o} = -beta), the correction
+// pairs of each held offset in CSR form pp[nh + 1] / pr[2 np] (plane pairs (p1, p2) with
+// o_p1 - o_p2 = o_h), and the candidate fill offsets outside the pattern with their pairs,
+// qoff[3 nq], qp[nq + 1], qpr[2 nqp].
+struct IctTables {
+    int nh, nq;
+    int B, C;             // level of voxel (x, y, z): x + B y + C z
+    const int *off, *ord, *hs, *pp, *pr, *qoff, *qp, *qpr;
+    unsigned* qflags;     // [ceil(nq / 32)] bit q set: candidate q reached the tolerance somewhere
+};
 struct IctArgs {
     Geo geo;
     double beta;
@@ -293,7 +312,8 @@ struct IctArgs {
     const int* vlist;
     const void* d;         // T [nv]: factor (forward sweep), or null: apply the stored factor
     const void* g;         // T [nv] right-hand side
-    double* L;             // [kIctPlanes][nv]
+    double* L;             // [nh + 2][nv] factor planes
+    IctTables tb;          // held pattern (table-driven kernels and the fill check)
     void* ip_out;          // T [nv] or null: 1/L_ii^2 (the pivots' inverses), factor mode
     void* p;               // T [nv] result (back substitution)
     const void* gdot;      // T [nv] or null: g for g'p
@@ -354,6 +374,7 @@ template <typename T> cudaError_t launch_rb_black(const DataArgs& a, int grid, c
 template <typename T> cudaError_t launch_rb_red(const DataArgs& a, int grid, cudaStream_t s);
 template <typename T> cudaError_t launch_ic_fwd(const IcArgs& a, int grid, cudaStream_t s);
 template <typename T> cudaError_t launch_ic_bwd(const IcArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_inv_pivot64(const float* hi, const float* lo, double* out, long long nv, int grid, cudaStream_t s);
 template <typename T> cudaError_t launch_true_curv(const AdjArgs& a, int grid, cudaStream_t s);
 template <typename T> cudaError_t launch_cg_init(const AdjArgs& a, int grid, cudaStream_t s);
 template <typename T> cudaError_t launch_cg_dir(const AdjArgs& a, int grid, cudaStream_t s);
@@ -368,7 +389,10 @@ template <typename T> cudaError_t launch_ict_tau(const DataArgs& a, double dropt
 template <typename T> cudaError_t launch_ict_fwd(const IctArgs& a, int grid, int block, cudaStream_t s);
 template <typename T> cudaError_t launch_ict_bwd(const IctArgs& a, int grid, int block, cudaStream_t s);
 template <typename T> cudaError_t launch_ict_check(const IctArgs& a, int grid, cudaStream_t s);
+template <typename T> cudaError_t launch_ictg_fwd(const IctArgs& a, int grid, int block, cudaStream_t s);
+template <typename T> cudaError_t launch_ictg_bwd(const IctArgs& a, int grid, int block, cudaStream_t s);
 template <typename T> int ict_max_blocks_per_sm(int block);
+template <typename T> int ictg_max_blocks_per_sm(int block);
 template <typename T> int ic_tz();
 template <typename T> size_t ic_face_bytes_per_tile();
 template <typename T> int ic_max_blocks_per_sm(bool bwd);  // resident IC sweep blocks per SM

@@ -584,6 +584,7 @@ __global__ void __launch_bounds__(kThreadsIC) k_ic_fwd(IcArgs a, int mode, PivSc
                     const int i = (wz * 32 + ly2) * 32 + lane;
                     v[j] = sg[i];
                     if (mode == 0 && ipo) ipo[j] = sd[i];
+                    if (Ops::kLo && mode == 0 && a.ip_lo_out) a.ip_lo_out[j] = (float)sl[i];
                 }
             }
         }
@@ -780,6 +781,17 @@ cudaError_t launch_ic_bwd(const IcArgs& a, int grid, cudaStream_t s) {
     cudaError_t e = prep<T>();
     if (e != cudaSuccess) return e;
     k_ic_bwd<T><<<grid, 32 * kTZ, BwdSmem<T>::bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+// 1/pi = hi + lo as one double (FP32 mode's pivot pair, for inspection)
+__global__ void k_inv_pivot64(const float* hi, const float* lo, double* out, long long nv) {
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nv; j += (long long)gridDim.x * blockDim.x)
+        out[j] = (double)hi[j] + (double)lo[j];
+}
+
+cudaError_t launch_inv_pivot64(const float* hi, const float* lo, double* out, long long nv, int grid, cudaStream_t s) {
+    k_inv_pivot64<<<grid, kThreads, 0, s>>>(hi, lo, out, nv);
     return cudaGetLastError();
 }
 

@@ -25,20 +25,30 @@
 // barrier between levels; the back substitution sweeps them in reverse.  A level's work is
 // FP64 arithmetic on the active columns, so the blocks are sized to spread the columns over
 // every SM (a volume with few columns runs one-warp blocks), and the barrier is the bounded
-// grid barrier -- or a block barrier when one block holds every column.  The factor
-// stores 1 / L_ii, so every entry costs a multiply, and each row issues all of its loads
-// from the earlier rows before the dependency chain starts.
+// grid barrier of a cooperative launch -- or a block barrier when one block holds every
+// column.  The factor stores 1 / L_ii, so every entry costs a multiply, and each row issues
+// all of its loads from the earlier rows before the dependency chain starts.
 //
-// Exactness.  This is the exact drop-tolerance factor as long as no entry outside P
-// survives.  With the factor on P in hand, k_ict_check forms every would-be entry just
-// outside P -- at the six offsets q = p1 - p2 (p1, p2 in P, q outside P, pointing to an
-// earlier voxel): (-1,1,-1): (c,d); (-1,2,-1): (f,d); (0,2,-1): (f,b); (1,1,-1): (e,b),
-// (f,a); (2,-1,0): (d,a); (2,0,-1): (e,a) -- and reports FM_ERR_FILL if one reaches tau.  If
-// none does, no entry outside P ever appears (by induction over the columns); otherwise the
-// first column where one does sees exactly this value, since all earlier columns agree.
+// Deeper fill.  When the tolerance keeps entries beyond level 1, the pattern P grows: the host
+// holds any set of offsets (up to kIctMaxOffsets), builds the correction pairs of each offset
+// by the same offset arithmetic (pairs (p1, p2) with o_p1 - o_p2 = o) and a level function
+// t = x + B y + C z under which every held offset points to a lower level, and the
+// table-driven kernels k_ictg_fwd / k_ictg_bwd sweep it.
+//
+// Exactness.  The held factor is the exact drop-tolerance factor as long as no entry outside
+// the held pattern survives.  With the factor in hand, k_ict_check forms every would-be entry
+// just outside it -- at each offset q = o_p1 - o_p2 (p1, p2 held, q not held, pointing to an
+// earlier voxel) -- and flags the offsets where one reaches tau.  If none does, no entry
+// outside the pattern ever appears (by induction over the columns); otherwise the first
+// column where one does sees exactly this value, since all earlier columns agree.  Holding a
+// flagged offset where the exact factor turns out to drop every entry changes nothing (the
+// entries are computed and dropped exactly as the definition does), so the host adds every
+// flagged offset and factors again until nothing is flagged.  For the base pattern the
+// candidates are (-1,1,-1): (c,d); (-1,2,-1): (f,d); (0,2,-1): (f,b); (1,1,-1): (e,b), (f,a);
+// (2,-1,0): (d,a); (2,0,-1): (e,a).
 //
 // A pivot <= 0 is reported (FM_ERR_NOT_PD) by the back sweep, after the check, so that
-// FM_ERR_FILL wins when fill outside P is the cause.
+// FM_ERR_FILL wins when fill outside the held pattern is the cause.
 //
 // Arithmetic is double in both precision modes (the voxel type only for d, g and p): the
 // sweeps are latency-bound, not bound by the FP64 pipe.
@@ -264,14 +274,162 @@ __global__ void __launch_bounds__(kIctThreads) k_ict_bwd(IctArgs a) {
     }
 }
 
-// ------------------------------------------------------------------ fill beyond P
+// ------------------------------------------------------------------ table-driven sweeps
+
+// Voxel at offset (dx, dy, dz) from (x, y, z), or -1 when it lies outside the grid or the mask.
+__device__ __forceinline__ long long ict_nbr(const IctArgs& a, int x, int y, int z, int dx, int dy, int dz) {
+    const int xj = x + dx, yj = y + dy, zj = z + dz;
+    if ((unsigned)xj >= (unsigned)a.geo.nx || (unsigned)yj >= (unsigned)a.geo.ny || (unsigned)zj >= (unsigned)a.geo.nz)
+        return -1;
+    const long long j = xj + (long long)a.geo.nx * (yj + (long long)a.geo.ny * zj);
+    return (a.nb[j] & NB_IN) ? j : -1;
+}
+
+// The same factorisation and substitutions as k_ict_fwd / k_ict_bwd for any held pattern
+// (a.tb): row i's entries in increasing column order, L_{i,j} = (H_ij - sum over the pairs
+// (p1, p2) of o of L_{i,i+o_p1} L_{j,j+o_p2}) / L_jj, dropped below tau, then L_ii and y_i.
+// Level t = x + B y + C z, with B and C chosen by the host so that every held offset points
+// to a strictly lower level.
+template <typename T>
+__global__ void __launch_bounds__(kIctThreads) k_ictg_fwd(IctArgs a) {
+    const int nx = a.geo.nx, ny = a.geo.ny, nz = a.geo.nz;
+    const long long nxy = (long long)nx * ny, nv = a.geo.nv;
+    const IctTables tb = a.tb;
+    const int nh = tb.nh, PY = 1 + nh;
+    double* Lp = a.L;
+    auto P = [&](int k, long long j) -> double* { return Lp + (size_t)k * nv + j; };
+    const T* d = (const T*)a.d;
+    const T* g = (const T*)a.g;
+    T* ipo = (T*)a.ip_out;
+    const bool factor = d != nullptr;
+    const double beta = a.beta;
+    const double tau = factor ? a.scal[S_ICT_TAU] : 0.0;
+    const int npair = ny * nz;
+    const int tmax = (nx - 1) + tb.B * (ny - 1) + tb.C * (nz - 1);
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+    bool bad = false;
+    double lrow[kIctMaxOffsets];
+    for (int t = 0; t <= tmax; ++t) {
+        for (int pr = gtid; pr < npair; pr += nthr) {
+            const int y = pr % ny, z = pr / ny, x = t - tb.B * y - tb.C * z;
+            if (x < 0 || x >= nx) continue;
+            const long long i = x + (long long)nx * y + nxy * z;
+            const uint8_t b = a.nb[i];
+            if (!(b & NB_IN)) continue;
+            double rii;
+            if (factor) {
+                for (int k = 0; k < nh; ++k) {
+                    const int h = tb.ord[k];
+                    const long long j = ict_nbr(a, x, y, z, tb.off[3 * h], tb.off[3 * h + 1], tb.off[3 * h + 2]);
+                    if (j < 0) {
+                        lrow[h] = 0.0;
+                        continue;
+                    }
+                    double sj = tb.hs[h] ? -beta : 0.0;
+                    for (int q = tb.pp[h]; q < tb.pp[h + 1]; ++q) {
+                        const double l1 = lrow[tb.pr[2 * q]];
+                        if (l1 != 0.0) sj -= l1 * ld_level(P(1 + tb.pr[2 * q + 1], j));
+                    }
+                    const double v = sj * ld_level(P(0, j));
+                    lrow[h] = fabs(v) >= tau ? v : 0.0;
+                }
+                double sq = 0.0;
+                for (int h = 0; h < nh; ++h) sq += lrow[h] * lrow[h];
+                const double sdiag = (double)d[i] + beta * (double)__popc((unsigned)(b >> 1) & 0x3fu) - sq;
+                if (!(sdiag > 0.0)) bad = true;
+                rii = sdiag > 0.0 ? rsqrt_nr(sdiag) : 1.0;  // the error is reported; keep the arithmetic finite
+                *P(0, i) = rii;
+                for (int h = 0; h < nh; ++h) *P(1 + h, i) = lrow[h];
+                if (ipo) ipo[i] = (T)(rii * rii);
+            } else {
+                rii = *P(0, i);
+                for (int h = 0; h < nh; ++h) lrow[h] = *P(1 + h, i);
+            }
+            double acc = (double)g[i];
+            for (int h = 0; h < nh; ++h) {
+                if (lrow[h] == 0.0) continue;
+                const long long j = ict_nbr(a, x, y, z, tb.off[3 * h], tb.off[3 * h + 1], tb.off[3 * h + 2]);
+                acc -= lrow[h] * ld_level(P(PY, j));
+            }
+            *P(PY, i) = acc * rii;
+        }
+        if (t < tmax && !level_sync(a)) return;
+    }
+    if (bad) atomicExch(a.istate + I_ICT_BAD, 1);
+}
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_ict_check(IctArgs a) {
+__global__ void __launch_bounds__(kIctThreads) k_ictg_bwd(IctArgs a) {
+    __shared__ double sbuf[2 * 32];
     const int nx = a.geo.nx, ny = a.geo.ny, nz = a.geo.nz;
+    const long long nxy = (long long)nx * ny, nv = a.geo.nv;
+    const IctTables tb = a.tb;
+    const int nh = tb.nh, PY = 1 + nh;
+    double* Lp = a.L;
+    auto P = [&](int k, long long j) -> double* { return Lp + (size_t)k * nv + j; };
+    T* p = (T*)a.p;
+    const T* gd = (const T*)a.gdot;
+    const T* gpd = (const T*)a.gpdot;
+    const int npair = ny * nz;
+    const int tmax = (nx - 1) + tb.B * (ny - 1) + tb.C * (nz - 1);
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+    double acc2[2] = {0.0, 0.0};
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.istate[I_ICT_BAD]) {
+        set_err(a.istate, FM_ERR_NOT_PD);
+        a.istate[I_ICT_BAD] = 0;
+    }
+    for (int t = tmax; t >= 0; --t) {
+        for (int pr = gtid; pr < npair; pr += nthr) {
+            const int y = pr % ny, z = pr / ny, x = t - tb.B * y - tb.C * z;
+            if (x < 0 || x >= nx) continue;
+            const long long i = x + (long long)nx * y + nxy * z;
+            if (!(a.nb[i] & NB_IN)) {
+                p[i] = T(0);
+                continue;
+            }
+            // the later rows r = i - o_h that hold an entry in column i: L_{r,i} = plane h of row r
+            double sacc = *P(PY, i);
+            for (int h = 0; h < nh; ++h) {
+                const long long r = ict_nbr(a, x, y, z, -tb.off[3 * h], -tb.off[3 * h + 1], -tb.off[3 * h + 2]);
+                if (r < 0) continue;
+                const double l = ld_level(P(1 + h, r));
+                if (l != 0.0) sacc -= l * ld_level(P(PY, r));
+            }
+            const double xi = sacc * *P(0, i);
+            *P(PY, i) = xi;  // y_i becomes x_i: every row that still needs y_i is this one
+            p[i] = (T)xi;
+            if (gd) acc2[0] += (double)gd[i] * (double)(T)xi;
+            if (gpd) acc2[1] += (double)gpd[i] * (double)(T)xi;
+        }
+        if (t > 0 && !level_sync(a)) return;
+    }
+    if (gd || gpd) {
+        double out[2];
+        if (last_block_reduce<2>(acc2, a.partials, (unsigned*)(a.istate + I_DONE0), out, sbuf)) {
+            if (threadIdx.x == 0) {
+                a.scal[S_GP] = out[0];
+                a.scal[S_GPREVP] = out[1];
+                if (!isfinite(out[0]) || !isfinite(out[1])) set_err(a.istate, FM_ERR_NONFINITE);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ fill beyond the held pattern
+
+// Every would-be entry just outside the held pattern: at each candidate offset q (q = o_p1 -
+// o_p2 for held p1, p2, pointing to an earlier voxel, not held), -(sum over its pairs of
+// L_{i,i+o_p1} L_{j,j+o_p2}) / L_jj with j = i + q.  One that reaches tau sets its bit in
+// tb.qflags and reports FM_ERR_FILL; the host then holds those offsets too and factors again.
+// With nothing flagged no entry outside the pattern ever appears (by induction over the
+// columns), so the held factor is the exact drop-tolerance factor.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_ict_check(IctArgs a) {
+    const int nx = a.geo.nx, ny = a.geo.ny;
     const long long nxy = (long long)nx * ny, nv = a.geo.nv;
     const double* Lp = a.L;
     auto P = [&](int k, long long j) -> double { return Lp[(size_t)k * nv + j]; };
+    const IctTables tb = a.tb;
     const double tau = a.scal[S_ICT_TAU];
     const long long nm = a.istate[I_NMASK];
     bool fill = false;
@@ -279,32 +437,34 @@ __global__ void __launch_bounds__(kThreads) k_ict_check(IctArgs a) {
          k += (long long)gridDim.x * blockDim.x) {
         const long long i = a.vlist[k];
         const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / nxy);
-        const double lc = P(PL_C, i), ld = P(PL_D1, i), le = P(PL_E, i), lf = P(PL_F, i);
-        // would-be entry at j = i + (qx, qy, qz): -(sum of the listed products) / L_jj
-        auto test = [&](int qx, int qy, int qz, double s) {
-            if (s == 0.0) return;
-            const int xj = x + qx, yj = y + qy, zj = z + qz;
-            if (xj < 0 || xj >= nx || yj < 0 || yj >= ny || zj < 0 || zj >= nz) return;
-            const long long j = xj + (long long)nx * yj + nxy * zj;
-            if (!(a.nb[j] & NB_IN)) return;
-            fill |= fabs(s * P(PL_R, j)) >= tau;
-        };
-        auto at = [&](int qx, int qy, int qz, int plane) -> double {
-            const int xj = x + qx, yj = y + qy, zj = z + qz;
-            if (xj < 0 || xj >= nx || yj < 0 || yj >= ny || zj < 0 || zj >= nz) return 0.0;
-            return P(plane, xj + (long long)nx * yj + nxy * zj);
-        };
-        if (lc != 0.0) test(-1, 1, -1, lc * at(-1, 1, -1, PL_D1));
-        if (lf != 0.0) test(-1, 2, -1, lf * at(-1, 2, -1, PL_D1));
-        if (lf != 0.0) test(0, 2, -1, lf * at(0, 2, -1, PL_B));
-        if (le != 0.0 || lf != 0.0) test(1, 1, -1, le * at(1, 1, -1, PL_B) + lf * at(1, 1, -1, PL_A));
-        if (ld != 0.0) test(2, -1, 0, ld * at(2, -1, 0, PL_A));
-        if (le != 0.0) test(2, 0, -1, le * at(2, 0, -1, PL_A));
+        for (int q = 0; q < tb.nq; ++q) {
+            double sq = 0.0;
+            long long j = -2;
+            for (int e = tb.qp[q]; e < tb.qp[q + 1]; ++e) {
+                const double l1 = P(1 + tb.qpr[2 * e], i);
+                if (l1 == 0.0) continue;
+                if (j == -2) j = ict_nbr(a, x, y, z, tb.qoff[3 * q], tb.qoff[3 * q + 1], tb.qoff[3 * q + 2]);
+                if (j < 0) break;
+                sq += l1 * P(1 + tb.qpr[2 * e + 1], j);
+            }
+            if (j >= 0 && sq != 0.0 && fabs(sq * P(0, j)) >= tau) {
+                atomicOr(tb.qflags + (q >> 5), 1u << (q & 31));
+                fill = true;
+            }
+        }
     }
     if (fill) set_err(a.istate, FM_ERR_FILL);
 }
 
 // ------------------------------------------------------------------ launches
+
+template <typename T>
+int ictg_max_blocks_per_sm(int block) {
+    int f = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&f, k_ictg_fwd<T>, block, 0) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ictg_bwd<T>, block, 0) != cudaSuccess) return 0;
+    return f < b ? f : b;
+}
 
 template <typename T>
 int ict_max_blocks_per_sm(int block) {
@@ -335,6 +495,18 @@ cudaError_t launch_ict_bwd(const IctArgs& a, int grid, int block, cudaStream_t s
     return cudaLaunchCooperativeKernel((const void*)k_ict_bwd<T>, dim3(grid), dim3(block), args, 0, s);
 }
 template <typename T>
+cudaError_t launch_ictg_fwd(const IctArgs& a, int grid, int block, cudaStream_t s) {
+    IctArgs copy = a;
+    void* args[] = {&copy};
+    return cudaLaunchCooperativeKernel((const void*)k_ictg_fwd<T>, dim3(grid), dim3(block), args, 0, s);
+}
+template <typename T>
+cudaError_t launch_ictg_bwd(const IctArgs& a, int grid, int block, cudaStream_t s) {
+    IctArgs copy = a;
+    void* args[] = {&copy};
+    return cudaLaunchCooperativeKernel((const void*)k_ictg_bwd<T>, dim3(grid), dim3(block), args, 0, s);
+}
+template <typename T>
 cudaError_t launch_ict_check(const IctArgs& a, int grid, cudaStream_t s) {
     k_ict_check<T><<<grid, kThreads, 0, s>>>(a);
     return cudaGetLastError();
@@ -345,7 +517,10 @@ cudaError_t launch_ict_check(const IctArgs& a, int grid, cudaStream_t s) {
     template cudaError_t launch_ict_fwd<T>(const IctArgs&, int, int, cudaStream_t);     \
     template cudaError_t launch_ict_bwd<T>(const IctArgs&, int, int, cudaStream_t);     \
     template cudaError_t launch_ict_check<T>(const IctArgs&, int, cudaStream_t);        \
-    template int ict_max_blocks_per_sm<T>(int);
+    template cudaError_t launch_ictg_fwd<T>(const IctArgs&, int, int, cudaStream_t);    \
+    template cudaError_t launch_ictg_bwd<T>(const IctArgs&, int, int, cudaStream_t);    \
+    template int ict_max_blocks_per_sm<T>(int);                                         \
+    template int ictg_max_blocks_per_sm<T>(int);
 FM_ICT_INST(float)
 FM_ICT_INST(double)
 

@@ -46,8 +46,9 @@ EXPORTS = ["fm_default_opts", "fm_create", "fm_set_data", "fm_init_omega", "fm_c
            "fm_batch_solve", "fm_batch_autotune", "fm_batch_set_fraction", "fm_batch_ctx", "fm_batch_destroy",
            "fm_batch_schedule",
            "fm_true_curv", "fm_adjoint_solve", "fm_implicit_grad", "fm_set_fat_model", "fm_wf_sweep",
-           "fm_pwls_init", "fm_wf_amplitudes", "fm_wf_sweep_range", "fm_set_spin_limit"]
-KERNELS = ["grad", "ic_fwd", "ic_bwd", "dir", "ls"]
+           "fm_pwls_init", "fm_wf_amplitudes", "fm_wf_sweep_range", "fm_set_spin_limit", "fm_set_data_host",
+           "fm_solve_host", "fm_synchronize", "fm_ic_factor64", "fm_ic_factor_curv", "fm_ict_pattern"]
+KERNELS = ["grad", "ic_fwd", "ic_bwd", "dir", "ls", "h2d", "d2h"]
 
 
 def lib_path():
@@ -92,6 +93,17 @@ def load_library(path=None):
         lib.fm_wf_sweep.argtypes = [vp, i, d, d, vp]
         lib.fm_pwls_init.argtypes = [vp, vp, i, vp]
         lib.fm_wf_amplitudes.argtypes = [vp, vp, vp, vp, vp, vp]
+        lib.fm_ic_factor64.argtypes = [vp, vp, vp]
+        lib.fm_ic_factor64.restype = C.c_int
+        lib.fm_ic_factor_curv.argtypes = [vp, vp, vp]
+        lib.fm_ic_factor_curv.restype = C.c_int
+        lib.fm_ict_pattern.argtypes = [vp, C.POINTER(i), vp, vp]
+        lib.fm_ict_pattern.restype = C.c_int
+        lib.fm_set_data_host.argtypes = [vp, vp, vp, C.POINTER(d), vp, d]
+        lib.fm_solve_host.argtypes = [vp, vp, i, i, C.POINTER(d)]
+        lib.fm_synchronize.argtypes = [vp]
+        for fn in ("fm_set_data_host", "fm_solve_host", "fm_synchronize"):
+            getattr(lib, fn).restype = C.c_int
         lib.fm_wf_sweep_range.argtypes = [vp, C.POINTER(d), C.POINTER(d)]
         lib.fm_set_spin_limit.argtypes = [vp, C.c_longlong]
         for fn in ("fm_true_curv", "fm_adjoint_solve", "fm_implicit_grad", "fm_set_fat_model", "fm_wf_sweep",
@@ -198,6 +210,39 @@ class FieldMap:
                     "fm_set_data")
         self.data = (y, smap, tuple(float(v) for v in te), mask, float(beta))
 
+    def set_data_host(self, y, smap, te, mask=None, beta=2.0 ** -3):
+        """fm_set_data_host: y, smap and mask are CPU tensors (page-locked for an upload that
+        overlaps earlier work); they must stay unchanged until the next synchronize()."""
+        t = self._torch
+        nz, ny, nx = self.shape
+        if not (not y.is_cuda and y.dtype == self.cdtype and y.is_contiguous()
+                and tuple(y.shape) == (self.necho, self.ncoil, nz, ny, nx)):
+            raise TypeError(f"y must be a contiguous {self.cdtype} CPU tensor of shape "
+                            f"{(self.necho, self.ncoil, nz, ny, nx)}")
+        if smap is not None and not (not smap.is_cuda and smap.dtype == self.cdtype and smap.is_contiguous()
+                                     and tuple(smap.shape) == (self.ncoil, nz, ny, nx)):
+            raise TypeError("smap must be a contiguous CPU tensor of y's dtype with shape (ncoil, nz, ny, nx)")
+        if mask is not None and not (not mask.is_cuda and mask.dtype == t.uint8 and mask.is_contiguous()
+                                     and tuple(mask.shape) == self.shape):
+            raise TypeError("mask must be a contiguous uint8 CPU tensor of the volume's shape")
+        te_arr = (C.c_double * self.necho)(*[float(v) for v in te])
+        self._check(self.lib.fm_set_data_host(self._h, _dptr(y), _dptr(smap), te_arr, _dptr(mask), float(beta)),
+                    "fm_set_data_host")
+        self.data = None  # the device arrays of fm_set_data are not kept for host input
+
+    def solve_host(self, omega, init=True, niter=50, hist=None):
+        """fm_solve_host into the CPU tensor omega (read as the start when init is False);
+        hist: a ctypes double array of niter + 1 entries or None (then asynchronous)."""
+        if not (not omega.is_cuda and omega.dtype == self.rdtype and omega.is_contiguous()
+                and omega.numel() == int(np.prod(self.shape))):
+            raise TypeError(f"omega must be a contiguous {self.rdtype} CPU tensor of the volume's size")
+        self._check(self.lib.fm_solve_host(self._h, _dptr(omega), 0 if not init else 1, int(niter), hist),
+                    "fm_solve_host")
+        return omega
+
+    def synchronize(self):
+        self._check(self.lib.fm_synchronize(self._h), "fm_synchronize")
+
     def init_omega(self):
         out = self.empty()
         self._check(self.lib.fm_init_omega(self._h, _dptr(out)), "fm_init_omega")
@@ -216,6 +261,33 @@ class FieldMap:
         self._vec(omega, "omega")
         ip = self.empty() if want_pivots else None
         self._check(self.lib.fm_ic_factor(self._h, _dptr(omega), _dptr(ip)), "fm_ic_factor")
+        return ip
+
+    def ic_factor_curv(self, curv, want_pivots=True):
+        """fm_ic_factor_curv: the preconditioner factor of diag(curv) + beta C'C."""
+        self._vec(curv, "curv")
+        ip = self.empty() if want_pivots else None
+        self._check(self.lib.fm_ic_factor_curv(self._h, _dptr(curv), _dptr(ip)), "fm_ic_factor_curv")
+        return ip
+
+    def ict_pattern(self, planes=True):
+        """The drop-tolerance factor as held: (offsets [nh][3] of (dx, dy, dz), planes
+        [nh + 1][nz][ny][nx] float64 (1/L_ii, then L_{i,i+o} per offset) or None)."""
+        n = C.c_int(0)
+        self._check(self.lib.fm_ict_pattern(self._h, C.byref(n), None, None), "fm_ict_pattern")
+        off = np.zeros((n.value, 3), np.int32)
+        pl = np.zeros((n.value + 1,) + self.shape, np.float64) if planes else None
+        self._check(self.lib.fm_ict_pattern(self._h, C.byref(n), off.ctypes.data_as(C.c_void_p),
+                                            pl.ctypes.data_as(C.c_void_p) if pl is not None else None),
+                    "fm_ict_pattern")
+        return off, pl
+
+    def ic_factor64(self, omega):
+        """fm_ic_factor64: IC(0) factor at omega; returns the inverse pivots as a float64 tensor
+        (FP32 mode: the hi + lo pair the forward sweep carries)."""
+        self._vec(omega, "omega")
+        ip = self._torch.empty(self.shape, dtype=self._torch.float64, device=self.device)
+        self._check(self.lib.fm_ic_factor64(self._h, _dptr(omega), _dptr(ip)), "fm_ic_factor64")
         return ip
 
     def ic_apply(self, g, out=None):

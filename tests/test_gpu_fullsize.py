@@ -8,11 +8,13 @@ voxel's 3x3x3 neighbourhood, which holds every input the voxel's gradient needs 
 data and its six stencil neighbours).  The cost history must be finite and, up to FP32
 rounding of the cost, non-increasing (monotonic line search, Sec. III-C).
 """
+import os
+
 import numpy as np
 import pytest
 
 from gpu_util import dev_inputs, open_fm, to_dev, to_np
-from oracle import Oracle
+from oracle import Oracle, curv_raw, ic0_factor, ic0_solve, set_threads
 from synth import full_config
 
 pytestmark = pytest.mark.gpu
@@ -77,13 +79,15 @@ def test_full_size_fp32_solve_sampled_parity(full):
     fm.close()
 
 
+def _full_w(vol, seed=3):
+    """A seeded field map near the truth (inputs of both sides come from synth)."""
+    rng = np.random.default_rng(seed)
+    return (vol.omega_true + 0.02 * rng.standard_normal(vol.mask.shape)) * vol.mask
+
+
 def test_full_size_fp64_cost_grad_sampled_parity(full):
     vol = full
-    fm32 = open_fm(vol, "fp32")
-    w0 = to_np(fm32.init_omega())
-    fm32.close()
-    rng = np.random.default_rng(3)
-    w = (w0 + 0.02 * rng.standard_normal(w0.shape)) * vol.mask
+    w = _full_w(vol)
     fm = open_fm(vol, "fp64")
     _, g, d = fm.cost_grad(to_dev(w, "fp64"))
     g_np, d_np = to_np(g), to_np(d)
@@ -93,3 +97,81 @@ def test_full_size_fp64_cost_grad_sampled_parity(full):
         assert abs(g_np[z, y, x] - g_ref) <= TOL["fp64"]["g"] * gmax, (z, y, x)
         assert abs(d_np[z, y, x] - d_ref) <= TOL["fp64"]["d"] * max(abs(d_ref), 1e-3 * d_np.max()), (z, y, x)
     fm.close()
+
+
+@pytest.fixture(scope="module")
+def full_ic_ref(full):
+    """The oracle's generic IC(0) of H = diag(d(w)) + beta C'C on every mask voxel of the full
+    grid (2.1 M unknowns), with d of Eq. 10 formed voxel by voxel from the raw data."""
+    vol = full
+    w = _full_w(vol)
+    set_threads(os.cpu_count() or 1)
+    try:
+        d = curv_raw(vol.y, vol.smap, vol.te, vol.mask, w)
+    finally:
+        set_threads(1)
+    colptr, rowidx, val, umap = ic0_factor(vol.mask.shape, vol.mask, d, vol.beta)
+    inv_piv = np.zeros(vol.mask.size)
+    inv_piv[umap] = 1.0 / val[colptr[:-1]] ** 2  # pi_j = L_jj^2
+    rng = np.random.default_rng(17)
+    g = rng.standard_normal(vol.mask.shape) * vol.mask
+    p = np.zeros(vol.mask.size)
+    p[umap] = ic0_solve(colptr, rowidx, val, g.reshape(-1)[umap])
+    return w, inv_piv.reshape(vol.mask.shape), g, p.reshape(vol.mask.shape)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_size_ic0_factor_and_apply_match_the_oracle(full, full_ic_ref, prec):
+    """The bench's IC(0) path at full size -- 2.1 M unknowns, 8 x 8 x 16 tiles (30 tile
+    levels), the forward sweep on one block per SM with streamed faces and the back
+    substitution on two blocks per SM -- against the oracle's generic factor and triangular
+    solves, element by element on every grid voxel."""
+    vol = full
+    w, ip_ref, g, p_ref = full_ic_ref
+    fm = open_fm(vol, prec)
+    ip = to_np(fm.ic_factor(to_dev(w, prec)))
+    p = to_np(fm.ic_apply(to_dev(g, prec)))
+    fm.close()
+    tol_ip, tol_p = (1e-10, 1e-10) if prec == "fp64" else (3e-5, 2e-4)
+    np.testing.assert_allclose(ip, ip_ref, rtol=tol_ip, atol=0)
+    np.testing.assert_allclose(p, p_ref, rtol=0, atol=tol_p * np.abs(p_ref).max())
+
+
+def test_full_size_fp32_pivot_pair_carries_the_recurrence_to_double_accuracy(full):
+    """FP32 mode keeps each inverse pivot as a float pair hi + lo.  On the float curvature the
+    factor actually used (fm_cost_grad's d at the same w, the same kernel and inputs), the
+    pivots from fm_ic_factor64 must satisfy the IC(0) recurrence of Eq. 12,
+    pi_j = d_j + beta n_j - beta^2 sum_{k lower in-mask neighbour} 1/pi_k, to about 1e-12
+    relative at every voxel -- a float-only recurrence leaves residuals near 1e-7."""
+    vol = full
+    w = to_dev(_full_w(vol), "fp32")
+    fm = open_fm(vol, "fp32")
+    _, _, d = fm.cost_grad(w, want_cost=False, want_grad=False)
+    ip64 = fm.ic_factor64(w).cpu().numpy()
+    ip_hi = to_np(fm.ic_factor(w))
+    fm.close()
+    d = to_np(d)
+    m = vol.mask.astype(bool)
+    inv = np.where(m, ip64, 0.0)
+    n = np.zeros(m.shape)
+    lower = np.zeros(m.shape)
+    for ax in range(3):
+        lo_nb = np.zeros(m.shape, bool)
+        sl_dst = [slice(None)] * 3
+        sl_src = [slice(None)] * 3
+        sl_dst[ax] = slice(1, None)
+        sl_src[ax] = slice(None, -1)
+        lo_nb[tuple(sl_dst)] = m[tuple(sl_src)]
+        hi_nb = np.zeros(m.shape, bool)
+        hi_nb[tuple(sl_src)] = m[tuple(sl_dst)]
+        n += lo_nb & m
+        n += hi_nb & m
+        sh = np.zeros(m.shape)
+        sh[tuple(sl_dst)] = inv[tuple(sl_src)]
+        lower += np.where(lo_nb & m, sh, 0.0)
+    pi = 1.0 / ip64[m]
+    rhs = (d + vol.beta * n - vol.beta ** 2 * lower)[m]
+    rel = np.abs(pi - rhs) / np.abs(pi)
+    assert rel.max() < 1e-12, rel.max()
+    # and the float hi alone is the float-rounded pair
+    np.testing.assert_allclose(ip_hi[m], ip64[m], rtol=1e-6, atol=0)

@@ -1,13 +1,18 @@
 """IC with a drop tolerance on the GPU (FM_PC_ICT; Sec. III-B's L_t and the paper's
-NCG-MLS-IC).  The kernels hold IC(0)'s pattern plus the level-1 fill offsets and report
-FM_ERR_FILL exactly when the drop tolerance keeps an entry outside it.  Checked here against
-the oracle's generic left-looking threshold IC:
+NCG-MLS-IC).  The factor is held on a set of grid offsets -- IC(0)'s plus the level-1 fill
+offsets at first -- and grows, inside the calls that factor, until the drop tolerance keeps
+nothing outside it; FM_ERR_FILL remains only beyond 64 offsets.  Checked here against the
+oracle's generic left-looking threshold IC:
 
+* Table 1's toy problem (20 x 16 x 8, d ~ U(0, 0.1), beta = 0.1, tolerance 1e-3 H_max),
+  whose factor keeps fill at dozens of offsets: every entry, the pivots and the apply;
+* volumes whose factor keeps fill beyond level 1 (previously reported as FM_ERR_FILL): the
+  factor entry by entry, and the FP64 solve per iteration;
 * the factor's inverse pivots and the apply, on volumes whose factor keeps level-1 fill
   (echoes 0/1/2.3 ms, tolerance 1e-2 H_max) and on volumes that keep none (echoes 0/2/10 ms,
   the paper's 1e-3 H_max), with grids spanning several columns' worth of levels and ragged
   edges;
-* FM_ERR_FILL exactly where the oracle's factor has an entry outside the held pattern;
+* FM_ERR_FILL only where the kept fill needs more than 64 offsets (complete Cholesky);
 * the solve's per-iteration cost against the oracle's solve with the same preconditioner,
   alone and inside a batch;
 * the implicit-differentiation CG with this preconditioner reaches IC(0)'s solution;
@@ -83,24 +88,109 @@ def test_ict_factor_and_apply_match_oracle(prec, case):
     fm.close()
 
 
-@pytest.mark.parametrize("case", KEEPS_MORE + [(45, 33, 17, 2, (0.0, 2.0, 10.0), 0.0),
-                                               (45, 33, 17, 2, (0.0, 2.0, 10.0), 1e-9)])
-def test_fill_outside_the_held_pattern_is_reported(case):
-    from paper_2005_08661_gb300 import FmError, FM_ERR_FILL
+def _entries_match(fm, shape, colptr, rowidx, val, umap, tol):
+    """The GPU factor as held (fm_ict_pattern) against the oracle's compressed columns, entry by
+    entry: every oracle entry L_ij at its offset's plane, the diagonal as 1 / L_ii, and no
+    other nonzero on the GPU side."""
+    nz, ny, nx = shape
+    off, planes = fm.ict_pattern()
+    where = {tuple(int(t) for t in o): h for h, o in enumerate(off)}
+    vec = lambda a: np.stack([a % nx, (a // nx) % ny, a // (nx * ny)], 1)
+    cols = np.repeat(np.arange(colptr.size - 1), np.diff(colptr))
+    vi, vj = umap[rowidx], umap[cols]
+    diag = vi == vj
+    scale = np.abs(val).max()
+    np.testing.assert_allclose(planes[0].reshape(-1)[vi[diag]], 1.0 / val[diag], rtol=tol, atol=0)
+    o = vec(vj[~diag]) - vec(vi[~diag])
+    h = np.array([where[tuple(int(t) for t in v)] for v in o])  # KeyError: an entry outside the held pattern
+    got = planes[1:].reshape(len(off), -1)[h, vi[~diag]]
+    assert np.max(np.abs(got - val[~diag])) <= tol * scale
+    assert int(np.count_nonzero(planes[1:])) == int((~diag).sum())
+    return len(off)
+
+
+def test_table1_toy_problem_factors_entry_by_entry():
+    """Table 1's example: 20 x 16 x 8 grid, every voxel an unknown, d uniform on (0, 0.1), beta =
+    0.1, drop tolerance 1e-3 H_max (reading 21).  Its factor keeps fill at dozens of offsets
+    (far beyond level 1); the GPU's grown pattern must give the oracle's factor exactly."""
+    from paper_2005_08661_gb300 import FieldMap
+    import torch
+    shape = (8, 16, 20)
+    d = np.random.default_rng(2020).uniform(0.0, 0.1, shape)
+    beta = 0.1
+    te = (0.0, 2.0, 10.0)
+    y0 = np.zeros((3, 1) + shape, np.complex128)
+    o = Oracle(y0, None, te, None, beta)
+    tau = 1e-3 * o.hmax(d)
+    colptr, rowidx, val, umap = ict_factor(shape, None, d, beta, tau)
+    g = np.random.default_rng(3).standard_normal(shape)
+    p_ref = o.precondition_ict(d, g, tau)
+    fm = FieldMap(20, 16, 8, ncoil=1, necho=3, precision="fp64", precond="ict", droptol=1e-3)
+    fm.set_data(torch.zeros((3, 1) + shape, dtype=torch.complex128, device="cuda"), None, te,
+                torch.ones(shape, dtype=torch.uint8, device="cuda"), beta)
+    fm.ic_factor_curv(to_dev(d, "fp64"))
+    nh = _entries_match(fm, shape, colptr, rowidx, val, umap, 1e-11)
+    assert nh > 30  # the toy keeps fill at many offsets
+    p = to_np(fm.ic_apply(to_dev(g, "fp64")))
+    assert np.max(np.abs(p - p_ref)) <= 1e-11 * np.max(np.abs(p_ref))
+    fm.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", KEEPS_MORE)
+def test_deeper_fill_factor_matches_the_oracle(prec, case):
+    """Volumes whose factor keeps fill beyond level 1 (few coils, echoes 0/1/2.3 ms): the
+    pattern grows to hold it and the factor, the pivots and the apply match the oracle."""
     *dims, te, droptol = case
     vol = _vol(*dims, te)
     o = Oracle.from_volume(vol)
     w = o.init()
     d = o.curv(w)
-    offs = _offsets(o.shape, vol.mask, d, vol.beta, droptol * o.hmax(d))
+    tau = droptol * o.hmax(d)
+    offs = _offsets(o.shape, vol.mask, d, vol.beta, tau)
     assert any(v not in HELD for v in offs)
+    colptr, rowidx, val, umap = ict_factor(o.shape, vol.mask, d, vol.beta, tau)
+    g = np.random.default_rng(5).standard_normal(vol.mask.shape) * vol.mask
+    p_ref = o.precondition_ict(d, g, tau)
+    fm = open_fm(vol, prec, precond="ict", droptol=droptol)
+    wd = to_dev(w, prec)
+    fm.ic_factor(wd)
+    p = to_np(fm.ic_apply(to_dev(g, prec)))
+    if prec == "fp64":
+        _entries_match(fm, o.shape, colptr, rowidx, val, umap, 1e-11)
+    tol = 1e-11 if prec == "fp64" else 2e-4
+    assert np.max(np.abs(p - p_ref)) <= tol * np.max(np.abs(p_ref))
+    fm.close()
+
+
+def test_fp64_deeper_fill_solve_matches_oracle_per_iteration():
+    """The solve grows the pattern as its iterates need and reruns from the same start: the
+    per-iteration cost is the oracle's drop-tolerance solve's."""
+    *dims, te, droptol = KEEPS_MORE[0]
+    vol = _vol(*dims, te)
+    o = Oracle.from_volume(vol)
+    o.set_droptol(droptol)
+    ref = o.solve(niter=12, nls=5, precond=4)
+    fm = open_fm(vol, "fp64", precond="ict", droptol=droptol)
+    w, cost = fm.solve(niter=12)
+    np.testing.assert_allclose(cost, ref["cost"], rtol=1e-10)
+    np.testing.assert_allclose(to_np(w), ref["w"], rtol=0, atol=1e-9)
+    fm.close()
+
+
+@pytest.mark.parametrize("droptol", [0.0, 1e-9])
+def test_fill_beyond_the_largest_pattern_is_reported(droptol):
+    """A tolerance of 0 is the complete Cholesky factor, whose fill spans the whole band: more
+    offsets than the factor holds, so FM_ERR_FILL; the context stays usable."""
+    from paper_2005_08661_gb300 import FmError, FM_ERR_FILL
+    vol = _vol(45, 33, 17, 2, (0.0, 2.0, 10.0))
+    o = Oracle.from_volume(vol)
+    w = o.init()
     fm = open_fm(vol, "fp64", precond="ict", droptol=droptol)
     wd = to_dev(w, "fp64")
-    fm.ic_factor(wd)
     with pytest.raises(FmError) as e:
-        fm.cost_grad(wd)
+        fm.ic_factor(wd)
     assert e.value.status == FM_ERR_FILL
-    # the error word is cleared and the context stays usable
     fm.cost_grad(wd)
     fm.close()
 

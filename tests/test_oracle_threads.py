@@ -24,3 +24,19 @@ def test_results_do_not_depend_on_the_thread_count():
     for other in out[1:]:
         for a, b in zip(out[0], other):
             assert np.array_equal(np.asarray(a), np.asarray(b))
+
+
+def test_curvature_from_raw_data_is_the_precomputed_oracles():
+    """curv_raw (Eq. 10 formed voxel by voxel from y and s, for volumes whose precomputed r
+    would not fit in memory) is the same computation as Oracle.curv, bitwise."""
+    from oracle import curv_raw
+    vol = make_volume(30, 26, 9, ncoil=4, snr_db=15.0, seed=22, fmax_hz=150.0, nblobs=3)
+    rng = np.random.default_rng(1)
+    w = (vol.omega_true + 0.03 * rng.standard_normal(vol.mask.shape)) * vol.mask
+    ref = Oracle.from_volume(vol).curv(w)
+    try:
+        set_threads(4)
+        d = curv_raw(vol.y, vol.smap, vol.te, vol.mask, w)
+    finally:
+        set_threads(1)
+    assert np.array_equal(d, ref)
