@@ -421,8 +421,8 @@ FM_API int fm_set_spin_limit(fm_ctx *ctx, long long spin_limit);
 #define FM_K_GRAD 0   /* data term + stencil gradient pass (fused update of the previous step) */
 #define FM_K_IC_FWD 1 /* IC(0) pivots + forward substitution wavefront */
 #define FM_K_IC_BWD 2 /* back substitution wavefront + g'p, g_prev'p */
-#define FM_K_DIR 3    /* Polak-Ribiere direction + first line-search step */
-#define FM_K_LS 4     /* persistent line search (steps 2..N_i) */
+#define FM_K_DIR 3    /* (no longer launched on its own: the direction is FM_K_LS's first phase) */
+#define FM_K_LS 4     /* persistent kernel: Polak-Ribiere direction, then the line search */
 #define FM_K_H2D 5    /* fm_set_data_host: host-to-device copy of one acquisition's inputs */
 #define FM_K_D2H 6    /* fm_solve_host: device-to-host copy of the field map */
 #define FM_NKERNEL 7

@@ -541,12 +541,7 @@ cudaError_t iteration(fm_ctx* c, int cur) {
     a.mu_hist = c->hist_mu;
     a.alpha_hist = c->hist_alpha;
     {
-        Mark m(c, cur, FM_K_DIR);
-        e = launch_dir<T>(a, c->grid_data, c->stream);
-    }
-    if (e != cudaSuccess) return e;
-    if (c->o.nls > 1) {
-        Mark m(c, cur, FM_K_LS);
+        Mark m(c, cur, FM_K_LS);  // direction + line search
         e = launch_ls<T>(a, c->grid_ls, c->stream);
     }
     return e;

@@ -161,7 +161,9 @@ __device__ __forceinline__ int atom_add_acq_rel(int* p, int v) {
     return old;
 }
 
-__device__ __forceinline__ bool grid_barrier(int* istate, long long limit) {
+// nblocks: the blocks that take part (every block of the grid by default; blocks beyond it
+// must have left the kernel before the first barrier).
+__device__ __forceinline__ bool grid_barrier(int* istate, long long limit, int nblocks = -1) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -170,7 +172,7 @@ __device__ __forceinline__ bool grid_barrier(int* istate, long long limit) {
         const int g0 = ld_acquire(gen);
         const int arrived = atom_add_acq_rel(count, 1);
         int ok = 1;
-        if (arrived == (int)gridDim.x - 1) {
+        if (arrived == (nblocks > 0 ? nblocks : (int)gridDim.x) - 1) {
             atomicExch(count, 0);
             st_release(gen, g0 + 1);
         } else {
@@ -366,7 +368,6 @@ template <typename T> cudaError_t launch_setup(const SetupArgs& a, cudaStream_t 
 template <typename T> cudaError_t launch_masked_copy(const void* in, void* out, const uint8_t* nb, long long nv,
                                                      int grid, cudaStream_t s);
 template <typename T> cudaError_t launch_grad(const DataArgs& a, int grid, cudaStream_t s);
-template <typename T> cudaError_t launch_dir(const DataArgs& a, int grid, cudaStream_t s);
 template <typename T> cudaError_t launch_ls(const DataArgs& a, int grid, cudaStream_t s);
 template <typename T> cudaError_t launch_pdiag(const DataArgs& a, int mode, int grid, cudaStream_t s);
 template <typename T> int ls_max_blocks_per_sm(const DataArgs& a);

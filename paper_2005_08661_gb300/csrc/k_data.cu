@@ -232,84 +232,119 @@ __global__ void __launch_bounds__(kThreads) k_grad(DataArgs a) {
     }
 }
 
-// ------------------------------------------------------------------ direction pass
+// ------------------------------------------------------------------ line search
 
-// mu (Polak-Ribiere with the preconditioned gradients), z = -p + mu z, and the sums the
-// first line-search step needs: ||C z||^2, (C z)'(C w), z'g, sum z^2 d (Sec. III-C).
-// The first step alpha_1 = -z'g / (sum z^2 d + beta ||C z||^2) is taken here.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_dir(DataArgs a) {
+// The search direction and the monotonic line search (Algorithm box, Sec. III-C, Eq. 16) as
+// one persistent cooperative kernel.
+//
+// Direction: mu (Polak-Ribiere with the preconditioned gradients; 0 at the first iteration),
+// z = -p + mu z, and the sums the line search needs: ||C z||^2, (C z)'(C w), z'g and
+// sum z^2 d (each thread sums its voxels in the voxel type, blocks and the grid in FP64, in a
+// fixed order, so every block computes the same totals after one grid barrier).  The first
+// step alpha_1 = -z'g / (sum z^2 d + beta ||C z||^2) reuses the gradient pass's g and d.
+//
+// Steps k = 1 .. nls-1: each re-evaluates the data term at w + alpha_k z, reduces
+// sum z_j dPhi_j and sum z_j^2 d_j the same way, and updates alpha without leaving the device.
+// Every thread visits the same voxels in both phases (one grid-stride mapping), so it reads
+// back only the z values it wrote itself.
+//
+// The grid is sized for the whole voxel grid, but a small mask does not need all of it: only
+// the first nb blocks take part -- one mask voxel per thread at most (fewer threads with
+// several voxels each measured slower: each voxel is a chain of dependent gathers) -- and the
+// rest leave before the first grid barrier, which then counts the nb participants only.
+template <typename T, int NC>
+__global__ void __launch_bounds__(kThreads) k_ls(DataArgs a) {
     __shared__ double sbuf[4 * 32];
+    __shared__ double s_tot[4];
+    const T* w = (const T*)a.w_out;
+    const T* z = (const T*)a.z_new;
+    const int it = a.istate[I_ITER];
+    const long long nm = a.istate[I_NMASK];
+    const int nb = (int)max(1LL, min((long long)gridDim.x, (nm + kThreads - 1) / kThreads));
+    if ((int)blockIdx.x >= nb) return;
     const int nx = a.geo.nx;
     const long long nxy = (long long)nx * a.geo.ny;
-    const int it = a.istate[I_ITER];
     double mu = 0.0;
     if (it > 0) {
         const double den = a.scal[S_GP_PREV];
         mu = den != 0.0 ? (a.scal[S_GP] - a.scal[S_GPREVP]) / den : 0.0;
     }
-    const T muT = (T)mu;
-    const T* p = (const T*)a.p;
-    const T* zo = (const T*)a.z_old;
-    T* zn = (T*)a.z_new;
-    const T* w = (const T*)a.w_out;
-    const T* g = (const T*)a.g;
-    const T* d = (const T*)a.d;
-    auto zval = [&](long long k) -> T { return -p[k] + muT * zo[k]; };
-    const long long nm = a.istate[I_NMASK];
-    // each thread sums its few voxels in the voxel type; blocks and the grid sum in FP64
-    T s_cz2 = 0, s_czw = 0, s_zg = 0, s_zzd = 0;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nm;
-         k += (long long)gridDim.x * blockDim.x) {
-        const long long j = a.vlist[k];
-        const uint8_t b = a.nb[j];
-        const T zj = zval(j), wj = w[j];
-        zn[j] = zj;
-        if (b & NB_XP) { const T e = zj - zval(j + 1), f = wj - w[j + 1]; s_cz2 += e * e; s_czw += e * f; }
-        if (b & NB_YP) { const T e = zj - zval(j + nx), f = wj - w[j + nx]; s_cz2 += e * e; s_czw += e * f; }
-        if (b & NB_ZP) { const T e = zj - zval(j + nxy), f = wj - w[j + nxy]; s_cz2 += e * e; s_czw += e * f; }
-        s_zg += zj * g[j];
-        s_zzd += zj * zj * d[j];
+    {
+        const T muT = (T)mu;
+        const T* p = (const T*)a.p;
+        const T* zo = (const T*)a.z_old;
+        T* zn = (T*)a.z_new;
+        const T* g = (const T*)a.g;
+        const T* d = (const T*)a.d;
+        auto zval = [&](long long k) -> T { return -p[k] + muT * zo[k]; };
+        T s_cz2 = 0, s_czw = 0, s_zg = 0, s_zzd = 0;
+        // one voxel's direction entry and its terms of the four sums (the +x, +y, +z edges)
+        auto dir_voxel = [&](long long j, uint8_t b, T pj, T zoj, T wj, T gj, T dj) {
+            const T zj = -pj + muT * zoj;
+            zn[j] = zj;
+            if (b & NB_XP) { const T e = zj - zval(j + 1), f = wj - w[j + 1]; s_cz2 += e * e; s_czw += e * f; }
+            if (b & NB_YP) { const T e = zj - zval(j + nx), f = wj - w[j + nx]; s_cz2 += e * e; s_czw += e * f; }
+            if (b & NB_ZP) { const T e = zj - zval(j + nxy), f = wj - w[j + nxy]; s_cz2 += e * e; s_czw += e * f; }
+            s_zg += zj * gj;
+            s_zzd += zj * zj * dj;
+        };
+        // four voxels per pass with their own loads issued first (the gathers of a voxel
+        // depend on its list entry), then the rest one by one, in the same voxel order
+        constexpr int U = 4;
+        const long long stride = (long long)nb * blockDim.x;
+        long long k0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+        for (; k0 + (U - 1) * stride < nm; k0 += U * stride) {
+            long long jj[U];
+            uint8_t bb[U];
+            T pp[U], zz[U], ww[U], gg[U], dd[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) jj[u] = a.vlist[k0 + u * stride];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                bb[u] = a.nb[jj[u]];
+                pp[u] = p[jj[u]];
+                zz[u] = zo[jj[u]];
+                ww[u] = w[jj[u]];
+                gg[u] = g[jj[u]];
+                dd[u] = d[jj[u]];
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) dir_voxel(jj[u], bb[u], pp[u], zz[u], ww[u], gg[u], dd[u]);
+        }
+        for (long long k = k0; k < nm; k += stride) {
+            const long long j = a.vlist[k];
+            dir_voxel(j, a.nb[j], p[j], zo[j], w[j], g[j], d[j]);
+        }
+        double v[4] = {(double)s_cz2, (double)s_czw, (double)s_zg, (double)s_zzd};
+        block_sum<4>(v, sbuf);
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) a.partials[(size_t)q * nb + blockIdx.x] = v[q];
+        if (!grid_barrier(a.istate, a.spin_limit, nb)) return;
+        double tot[4];
+        sum_partials<4>(a.partials, nb, tot, sbuf);
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) s_tot[q] = tot[q];
+        __syncthreads();
     }
-    double v[4] = {(double)s_cz2, (double)s_czw, (double)s_zg, (double)s_zzd}, out[4];
-    if (last_block_reduce<4>(v, a.partials, (unsigned*)(a.istate + I_DONE0), out, sbuf)) {
-        if (threadIdx.x == 0) {
-            a.scal[S_CZ2] = out[0];
-            a.scal[S_CZW] = out[1];
-            a.scal[S_ZG] = out[2];
-            a.scal[S_ZZD] = out[3];
+    const double cz2 = s_tot[0], czw = s_tot[1];
+    double alpha;
+    {
+        const double den = s_tot[3] + a.beta * cz2;
+        alpha = den != 0.0 ? -s_tot[2] / den : 0.0;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            a.scal[S_CZ2] = cz2;
+            a.scal[S_CZW] = czw;
+            a.scal[S_ZG] = s_tot[2];
+            a.scal[S_ZZD] = s_tot[3];
             a.scal[S_MU] = mu;
-            a.scal[S_GP_PREV] = a.scal[S_GP];
-            const double den = out[3] + a.beta * out[0];
-            const double alpha = den != 0.0 ? -out[2] / den : 0.0;
-            a.scal[S_ALPHA] = alpha;
+            a.scal[S_GP_PREV] = a.scal[S_GP];  // every block read the old value before the barrier
             if (a.mu_hist) a.mu_hist[it] = mu;
             if (!isfinite(alpha) || !isfinite(mu) || !isfinite(den)) set_err(a.istate, FM_ERR_NONFINITE);
-            if (a.nls <= 1) {
-                if (a.alpha_hist) a.alpha_hist[it] = alpha;
-                a.istate[I_ITER] = it + 1;
-            }
         }
+        __syncthreads();  // s_tot is reused by the steps below
     }
-}
-
-// ------------------------------------------------------------------ line search
-
-// Steps k = 1 .. nls-1 of the monotonic line search (Eq. 16) as one persistent cooperative
-// kernel: each step re-evaluates the data term at w + alpha_k z, reduces
-// sum z_j dPhi_j and sum z_j^2 d_j in double (fixed order, every block computes the same
-// total), and updates alpha without leaving the device.
-template <typename T, int NC>
-__global__ void __launch_bounds__(kThreads) k_ls(DataArgs a) {
-    __shared__ double sbuf[2 * 32];
-    __shared__ double s_tot[2];
-    const T* w = (const T*)a.w_out;
-    const T* z = (const T*)a.z_new;
-    const double cz2 = a.scal[S_CZ2], czw = a.scal[S_CZW];
-    const int it = a.istate[I_ITER];
-    double alpha = a.scal[S_ALPHA];
-    const int nb = gridDim.x;
-    const long long nm = a.istate[I_NMASK];
     for (int step = 1; step < a.nls; ++step) {
         const T aT = (T)alpha;
         // each thread sums its few voxels in the voxel type, then the block and the grid in FP64
@@ -320,7 +355,7 @@ __global__ void __launch_bounds__(kThreads) k_ls(DataArgs a) {
             // one.  The voxels are visited in the same order as below, and a voxel with z = 0
             // adds exactly 0 whether or not it is evaluated, so the sums are unchanged.
             constexpr int U = 4;
-            const long long stride = (long long)gridDim.x * blockDim.x;
+            const long long stride = (long long)nb * blockDim.x;
             long long k0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
             for (; k0 + (U - 1) * stride < nm; k0 += U * stride) {
                 long long jj[U];
@@ -351,7 +386,7 @@ __global__ void __launch_bounds__(kThreads) k_ls(DataArgs a) {
             }
         } else {
             for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nm;
-                 k += (long long)gridDim.x * blockDim.x) {
+                 k += (long long)nb * blockDim.x) {
                 const long long j = a.vlist[k];
                 const T zj = z[j];
                 if (zj == T(0)) continue;
@@ -368,7 +403,7 @@ __global__ void __launch_bounds__(kThreads) k_ls(DataArgs a) {
             part[blockIdx.x] = v[0];
             part[nb + blockIdx.x] = v[1];
         }
-        if (!grid_barrier(a.istate, a.spin_limit)) return;
+        if (!grid_barrier(a.istate, a.spin_limit, nb)) return;
         double tot[2];
         sum_partials<2>(part, nb, tot, sbuf);
         if (threadIdx.x == 0) { s_tot[0] = tot[0]; s_tot[1] = tot[1]; }
@@ -443,12 +478,6 @@ cudaError_t launch_grad(const DataArgs& a, int grid, cudaStream_t s) {
     }
 }
 
-template <typename T>
-cudaError_t launch_dir(const DataArgs& a, int grid, cudaStream_t s) {
-    k_dir<T><<<grid, kThreads, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
 template <typename T, int NC>
 static cudaError_t ls_nc(const DataArgs& a, int grid, cudaStream_t s) {
     DataArgs copy = a;
@@ -495,7 +524,6 @@ cudaError_t launch_pdiag(const DataArgs& a, int mode, int grid, cudaStream_t s) 
 
 #define FM_INST(T)                                                                  \
     template cudaError_t launch_grad<T>(const DataArgs&, int, cudaStream_t);        \
-    template cudaError_t launch_dir<T>(const DataArgs&, int, cudaStream_t);         \
     template cudaError_t launch_ls<T>(const DataArgs&, int, cudaStream_t);          \
     template cudaError_t launch_pdiag<T>(const DataArgs&, int, int, cudaStream_t);  \
     template int ls_max_blocks_per_sm<T>(const DataArgs&);
