@@ -39,9 +39,12 @@ if ROOT not in sys.path:
 # kernel), from one ncu capture of the full workload (its summary sits with the committed
 # profiles), each with the hash of the kernel sources it was measured on: a figure whose
 # sources have changed since is reported as null.
-KERNEL_SOURCES = {"ls": ("k_data.cu",), "grad": ("k_data.cu",), "dir": ("k_data.cu",), "ic_fwd": ("k_ic.cu",),
-                  "ic_bwd": ("k_ic.cu",)}
-NCU_TRAFFIC_BYTES = {
+KERNEL_SOURCES = {"ls": ("k_data.cu",), "grad": ("k_data.cu",), "ic_fwd": ("k_ic.cu",), "ic_bwd": ("k_ic.cu",)}
+NCU_TRAFFIC_BYTES = {  # (bytes per launch, kernel_src_hash of the sources measured)
+    ("full", "ls"): (2006743552 + 10684800, "c45a72b6fcfbd267"),
+    ("full", "grad"): (504713472 + 21894826, "c45a72b6fcfbd267"),
+    ("full", "ic_fwd"): (78387584 + 34291456, "6b17fa9865553fe0"),
+    ("full", "ic_bwd"): (134262016 + 16783360, "6b17fa9865553fe0"),
 }
 
 
@@ -451,17 +454,18 @@ def run_ours(args, world, rank, local):
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_run = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
     peaks = peak_numbers(sm_run, nsm, fp32_probe(local))
-    per_iter = {k: v[0] for k, v in kt.items() if v[1] > 0 and k in ("grad", "ic_fwd", "ic_bwd", "dir", "ls")}
+    per_iter = {k: v[0] for k, v in kt.items() if v[1] > 0 and k in ("grad", "ic_fwd", "ic_bwd", "ls")}
     dom = max(per_iter, key=per_iter.get) if per_iter else None
     literal = vol.ncoil > 1 and args.curvature == "literal"
     def kernel_roofline(name, ms):
         """Algorithmic work of one launch of kernel class `name` against its bound."""
         evals = {"grad": 1, "ls": 4}.get(name, 0)
         ts = 4 if prec == "fp32" else 8
+        dir_bytes = nmask * (4 + 1 + 6 * ts) if name == "ls" else 0  # the line search's direction phase
         if evals and literal:
             flops = evals * nmask * data_eval_flops(vol.ncoil, vol.necho, True)
             ach = flops / (ms * 1e-3) / 1e12
-            byts = evals * nmask * data_eval_bytes(vol.ncoil, vol.necho, literal, ts)
+            byts = evals * nmask * data_eval_bytes(vol.ncoil, vol.necho, literal, ts) + dir_bytes
             hbm = byts / (ms * 1e-3) / 1e9
             return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
                     "frac": ach / peaks["fp32_tflops"], "peak_src": peaks["fp32_src"], "ms_per_launch": ms,
@@ -472,13 +476,13 @@ def run_ours(args, world, rank, local):
                             "frac": hbm / peaks["hbm_gbs"], "algorithmic_bytes_per_launch": byts},
                     "traffic": ncu_traffic(args.workload, name)}
         if evals:
-            byts = evals * (nmask * data_eval_bytes(vol.ncoil, vol.necho, literal, ts) + nv)
+            byts = evals * (nmask * data_eval_bytes(vol.ncoil, vol.necho, literal, ts) + nv) + dir_bytes
         elif name == "ic_fwd":  # per grid voxel: bits, d and g in, pivots and v out
             byts = nv * (1 + 2 * ts + 2 * ts)
         elif name == "ic_bwd":  # per grid voxel: bits, v, pivots, g, g_prev in, p out
             byts = nv * (1 + 2 * ts + 3 * ts)
-        else:  # direction pass over the mask list: index, bits, p, z, w, g, d in, z out
-            byts = nmask * (4 + 1 + 6 * ts)
+        else:
+            return None
         ach = byts / (ms * 1e-3) / 1e9
         out = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                "frac": ach / peaks["hbm_gbs"], "peak_src": peaks["hbm_src"], "ms_per_launch": ms,
@@ -490,7 +494,7 @@ def run_ours(args, world, rank, local):
     roof = kernel_roofline(dom, per_iter[dom]) if dom is not None else None
     kernels = {}
     for k, v in kt.items():
-        if v[1] > 0 and k in ("grad", "ic_fwd", "ic_bwd", "dir", "ls"):
+        if v[1] > 0 and k in ("grad", "ic_fwd", "ic_bwd", "ls"):
             r = kernel_roofline(k, v[0])
             kernels[k] = {"ms_per_launch": v[0], "share_of_iteration": v[0] / sum(per_iter.values()),
                           "bound": r["bound"], "achieved": r["achieved"], "unit": r["unit"], "frac": r["frac"]}
@@ -507,6 +511,13 @@ def run_ours(args, world, rank, local):
     if rank == 0 and not args.no_ttc:
         ttc = time_to_oracle_cost(prec, stream, "small")
         ttc8 = time_to_oracle_cost(prec, stream, "full8")
+
+    # the batched form (32 uneven volumes), measured after the main figures
+    batch = None
+    if rank == 0 and world == 1 and not args.no_batch and args.workload == "full":
+        fm_keep = fm
+        batch = batch_summary(local, prec, 3, 2)
+        fm = fm_keep
 
     # the precision form against the plain FP64 GPU solve of the same workload (untimed)
     fp64cmp = None
@@ -545,9 +556,10 @@ def run_ours(args, world, rank, local):
         cpu["one_core"] = {"value": units1 / dts1[0], "unit": "voxel-iter/s", "cores": 1,
                            "sample": sample_desc(sub1, 1, 1, args.curvature, vol.ncoil) + f", {dts1[0]:.1f} s"}
 
-    # per step: mask count, chunk scan, setup; 5 kernels per outer iteration; the final update
-    # (water-fat adds the sweep, the PWLS start and 2 kernels per PWLS iteration, the amplitudes)
-    launches = args.steps * (3 + 5 * niter + 1 + ((1 + 1 + 2 * 10 + 1) if wf else 0))
+    # per step: mask count, chunk scan, setup; 4 kernels per outer iteration (gradient pass, IC
+    # forward and back sweeps, direction + line search); the final update (water-fat adds the
+    # sweep, the PWLS start and 2 kernels per PWLS iteration, the amplitudes)
+    launches = args.steps * (3 + 4 * niter + 1 + ((1 + 1 + 2 * 10 + 1) if wf else 0))
     line = {"metric": "voxel-NCG-iters/s", "value": value, "unit": "voxel-iter/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
@@ -560,14 +572,28 @@ def run_ours(args, world, rank, local):
                        "masked_voxel_iters_per_s": world * nmask * niter / t_step},
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "kernels": kernels, "clocks": clk,
             "cpu_baseline": cpu, "time_to_oracle_cost": ttc, "time_to_oracle_cost_8coil": ttc8,
-            "fp32_vs_fp64_gpu": fp64cmp}
+            "fp32_vs_fp64_gpu": fp64cmp, "batch": batch}
     if rank == 0:
         print(json.dumps(line), flush=True)
     fm.close()
     return 0
 
 
-def run_batch(args, world, rank, local):
+def batch_summary(local, precision, steps, warmup, rank=0):
+    """The batched form's numbers for the main line: the 32-volume aggregate (one graph launch
+    per two iterations of every volume) against the same volumes solved one after another."""
+    class A:
+        pass
+    a = A()
+    a.niter, a.precision, a.steps, a.warmup = 0, precision, steps, warmup
+    line = run_batch(a, 1, rank, local, quiet=True)
+    return {"workload": WORKLOADS["batch"]["desc"], "value": line["value"], "unit": "voxel-iter/s",
+            "ms_per_step": line["ms_per_step"], "sequential": line["sequential"],
+            "speedup_vs_sequential": line["speedup_vs_sequential"], "steps": steps, "warmup": warmup,
+            "grid_fraction": line["config"]["grid_fraction"]}
+
+
+def run_batch(args, world, rank, local, quiet=False):
     """Config-4 form: aggregate voxel-NCG-iters/s of 32 uneven volumes solved together,
     against the same 32 volumes solved one after another with fm_solve."""
     import torch
@@ -631,7 +657,7 @@ def run_batch(args, world, rank, local):
 
     # the batched FP32 maps against plain FP64 GPU solves of a sample of the volumes (untimed)
     cmp = None
-    if rank == 0 and args.precision == "fp32":
+    if rank == 0 and args.precision == "fp32" and not quiet:
         step_batch()
         torch.cuda.synchronize(dev)
         order = sorted(range(len(vols)), key=lambda k: vols[k].nvox)
@@ -661,12 +687,12 @@ def run_batch(args, world, rank, local):
             "sequential": {"value": world * nvox * niter / t_s, "ms_per_step": 1000 * t_s,
                            "what": "the same 32 volumes, fm_set_data + fm_solve one after another"},
             "speedup_vs_sequential": t_s / t_b, "fp32_vs_fp64_gpu": cmp, "clocks": clk}
-    if rank == 0:
+    if rank == 0 and not quiet:
         print(json.dumps(line), flush=True)
     for f in singles:
         f.close()
     b.close()
-    return 0
+    return line if quiet else 0
 
 
 def run_diff(args, world, rank, local):
@@ -914,6 +940,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttc", action="store_true")
     ap.add_argument("--no-fp64-check", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if world > 1:
