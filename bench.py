@@ -340,7 +340,7 @@ def run_reference(args, world, rank):
 
 # ------------------------------------------------------------------ main arm
 
-def run_ours(args, world, rank, local):
+def run_ours(args, world, rank, local, quiet=False):
     import torch
     from paper_2005_08661_gb300 import FieldMap, build as fm_build
     fm_build.build()
@@ -512,11 +512,13 @@ def run_ours(args, world, rank, local):
         ttc = time_to_oracle_cost(prec, stream, "small")
         ttc8 = time_to_oracle_cost(prec, stream, "full8")
 
-    # the batched form (32 uneven volumes), measured after the main figures
-    batch = None
-    if rank == 0 and world == 1 and not args.no_batch and args.workload == "full":
+    # the batched, water-fat, differentiation and preconditioner forms, measured after the main
+    # figures (short runs; each form's own workload line comes from --workload)
+    batch = forms = None
+    if rank == 0 and world == 1 and not args.no_forms and args.workload == "full":
         fm_keep = fm
         batch = batch_summary(local, prec, 3, 2)
+        forms = forms_summary(local, prec)
         fm = fm_keep
 
     # the precision form against the plain FP64 GPU solve of the same workload (untimed)
@@ -572,11 +574,11 @@ def run_ours(args, world, rank, local):
                        "masked_voxel_iters_per_s": world * nmask * niter / t_step},
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "kernels": kernels, "clocks": clk,
             "cpu_baseline": cpu, "time_to_oracle_cost": ttc, "time_to_oracle_cost_8coil": ttc8,
-            "fp32_vs_fp64_gpu": fp64cmp, "batch": batch}
-    if rank == 0:
+            "fp32_vs_fp64_gpu": fp64cmp, "batch": batch, "forms": forms}
+    if rank == 0 and not quiet:
         print(json.dumps(line), flush=True)
     fm.close()
-    return 0
+    return line if quiet else 0
 
 
 def batch_summary(local, precision, steps, warmup, rank=0):
@@ -590,7 +592,34 @@ def batch_summary(local, precision, steps, warmup, rank=0):
     return {"workload": WORKLOADS["batch"]["desc"], "value": line["value"], "unit": "voxel-iter/s",
             "ms_per_step": line["ms_per_step"], "sequential": line["sequential"],
             "speedup_vs_sequential": line["speedup_vs_sequential"], "steps": steps, "warmup": warmup,
-            "grid_fraction": line["config"]["grid_fraction"]}
+            "grid_fraction": line["config"]["grid_fraction"],
+            "ic_bwd_blocks_per_sm": line["config"]["ic_bwd_blocks_per_sm"]}
+
+
+def forms_summary(local, precision):
+    """Short runs of the water-fat, differentiation and preconditioner-comparison workloads for
+    the main line (each is its own line with --workload wf|diff|precond)."""
+    class A:
+        pass
+    out = {}
+    for name, fn in (("wf", run_ours), ("diff", run_diff), ("precond", run_precond)):
+        a = A()
+        a.workload, a.precision, a.curvature, a.niter = name, precision, "literal", 0
+        a.steps, a.warmup = (1, 1) if name == "precond" else (3, 2)
+        a.no_e2e = a.no_cpu_baseline = a.no_ttc = a.no_forms = True
+        a.no_fp64_check = name != "wf"
+        try:
+            line = fn(a, 1, 0, local, quiet=True)
+        except Exception as e:  # a form that fails is reported, not hidden
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+            continue
+        keep = {"workload": WORKLOADS[name]["desc"], "value": line["value"], "unit": line["unit"],
+                "ms_per_step": line.get("ms_per_step")}
+        for k in ("fp32_vs_fp64_gpu", "fp32_error_vs_fp64_gpu", "backward", "preconditioners"):
+            if k in line:
+                keep[k] = line[k]
+        out[name] = keep
+    return out
 
 
 def run_batch(args, world, rank, local, quiet=False):
@@ -622,6 +651,7 @@ def run_batch(args, world, rank, local, quiet=False):
         b.set_data(k, dev_in[k][0], dev_in[k][1], v.te, dev_in[k][2], v.beta)
     frac, _ = b.autotune(niter_probe=4)
     _, order_w = b.schedule()
+    bwd_blocks = b.bwd_blocks_per_sm()
     ws = [b.empty(k) for k in range(len(vols))]
     ptrs = (C.c_void_p * len(vols))(*[w.data_ptr() for w in ws])
 
@@ -683,6 +713,7 @@ def run_batch(args, world, rank, local, quiet=False):
             "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": WORKLOADS["batch"]["desc"], "volumes": len(vols), "voxels": nvox, "niter": niter,
                        "grid_fraction": frac, "ic_tile_order_weights": list(order_w),
+                       "ic_bwd_blocks_per_sm": bwd_blocks,
                        "parallelism": f"replicas{world}"},
             "sequential": {"value": world * nvox * niter / t_s, "ms_per_step": 1000 * t_s,
                            "what": "the same 32 volumes, fm_set_data + fm_solve one after another"},
@@ -695,7 +726,7 @@ def run_batch(args, world, rank, local, quiet=False):
     return line if quiet else 0
 
 
-def run_diff(args, world, rank, local):
+def run_diff(args, world, rank, local, quiet=False):
     """Differentiation form: forward solve + implicit-gradient backward through
     torch.autograd, FP32 timed, with the FP64 GPU path as the accuracy reference."""
     import torch
@@ -775,11 +806,13 @@ def run_diff(args, world, rank, local):
                          "adjoint_cg_iterations": r64["adj"]["iterations"], "adjoint_relres": r64["adj"]["relres"]},
             "fp32_error_vs_fp64_gpu": err, "clocks": r32["clk"]}
     if rank == 0:
+        if quiet:
+            return line
         print(json.dumps(line), flush=True)
-    return 0
+    return line if quiet else 0
 
 
-def run_precond(args, world, rank, local):
+def run_precond(args, world, rank, local, quiet=False):
     """Time for each preconditioner to bring the RMSD to the converged map below 0.5 Hz
     (the paper's phantom comparison), with the converged map from a long FP64 IC(0) solve."""
     import torch
@@ -853,7 +886,7 @@ def run_precond(args, world, rank, local):
     for pc in ("ic0", "ict", "rb", "diag", "none"):
         try:
             rows[pc] = precond_row(pc)
-        except FmError as e:  # FM_ERR_FILL: the tolerance keeps fill beyond the held pattern
+        except FmError as e:  # FM_ERR_FILL: the kept fill needs more offsets than the factor holds
             rows[pc] = {"iterations": None, "ms": None, "error": str(e)}
     base = rows["ic0"]["ms"]
     for r in rows.values():
@@ -865,8 +898,10 @@ def run_precond(args, world, rank, local):
                        "reference": "converged map: 400 FP64 IC(0) iterations", "parallelism": f"replicas{world}"},
             "preconditioners": rows}
     if rank == 0:
+        if quiet:
+            return line
         print(json.dumps(line), flush=True)
-    return 0
+    return line if quiet else 0
 
 
 TTC_CASES = {
@@ -940,7 +975,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttc", action="store_true")
     ap.add_argument("--no-fp64-check", action="store_true")
-    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="leave out the short runs of the batched, water-fat, differentiation and preconditioner "
+                         "forms that the default line reports beside the main figures")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if world > 1:

@@ -391,11 +391,12 @@ FM_API int fm_batch_solve(fm_batch *b, void *const *omega, int init_from_data, i
 
 /* Choose, by timing short solves of niter_probe iterations, the launch schedule of the
  * volumes running side by side: the fraction of its own full-GPU grid each volume's kernels
- * use (candidates 1, 1/2, 1/4, 1/8) and the order in which the IC(0) forward wavefront
- * claims its tiles (weights (X + Y) : Z of 2 : 1, 1 : 1, 3 : 2; any positive weights keep the
- * dependency order).  best_ms (host, nullable) receives the winning probe time.  Requires
- * fm_batch_set_data on every volume.  The schedule stays in effect until changed
- * (fm_batch_schedule reports it). */
+ * use (candidates 1, 1/2, 1/4, 1/8), the order in which the IC(0) forward wavefront claims
+ * its tiles (weights (X + Y) : Z of 2 : 1, 1 : 1, 3 : 2; any positive weights keep the
+ * dependency order), and then, at the best of those, the back-substitution wavefront's blocks
+ * per SM (1, 2 or 3, as its occupancy allows).  best_ms (host, nullable) receives the winning
+ * probe time.  Requires fm_batch_set_data on every volume.  The schedule stays in effect
+ * until changed (fm_batch_schedule and fm_batch_bwd_blocks report it). */
 FM_API int fm_batch_autotune(fm_batch *b, int niter_probe, double *best_fraction, double *best_ms);
 
 /* Set the grid fraction directly (0 < fraction <= 1). */
@@ -403,6 +404,9 @@ FM_API int fm_batch_set_fraction(fm_batch *b, double fraction);
 
 /* The schedule in effect: grid fraction and the forward tile order weights (host, nullable). */
 FM_API int fm_batch_schedule(const fm_batch *b, double *fraction, int *order_wxy, int *order_wz);
+
+/* The back-substitution wavefront's blocks per SM in effect (before the grid fraction). */
+FM_API int fm_batch_bwd_blocks(const fm_batch *b, int *blocks_per_sm);
 
 /* Context of volume k (for fm_cost_grad, fm_get_history, ...; owned by the batch). */
 FM_API fm_ctx *fm_batch_ctx(fm_batch *b, int k);

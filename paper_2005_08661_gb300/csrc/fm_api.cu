@@ -50,6 +50,7 @@ struct fm_ctx {
     int ic_wxy = 2, ic_wz = 1;  // forward tile claim order weights
     int nsm = 0, grid_data = 0, grid_ls = 0, grid_ic = 0, grid_icb = 0;  // grid_icb: backward IC sweep
     int base_data = 0, base_ls = 0, base_ic = 0, base_icb = 0;
+    int occ_icb = 0;  // resident back-substitution blocks per SM the kernel allows
     int grid_ict = 0, base_ict = 0, block_ict = 0;  // drop-tolerance IC sweeps (persistent, level barriers)
     int grid_ictg = 0, base_ictg = 0;                // the same for the table-driven sweeps
     // drop-tolerance IC: the held pattern (dx, dy, dz per offset, plane order), its device
@@ -961,6 +962,7 @@ int fm_create(fm_ctx** out, int nx, int ny, int nz, int ncoil, int necho, const 
         if (occ_f < 1 || occ_b < 1) return bail(FM_ERR_CUDA);
         c->grid_ic = std::max(1, std::min(c->ntiles, occ_f * c->nsm));
         c->grid_icb = std::max(1, std::min(c->ntiles, std::min(occ_b, 2) * c->nsm));
+        c->occ_icb = occ_b;
     }
     c->base_data = c->grid_data;
     c->base_ls = c->grid_ls;
@@ -1574,6 +1576,7 @@ struct fm_batch {
     cudaGraphExec_t gexec = nullptr;
     std::vector<int> gen;  // history generations the captured graph was built with
     double fraction = 1.0;
+    int icb_per_sm = 2;  // back-substitution blocks per SM (before the fraction)
     std::string err;
 };
 
@@ -1593,7 +1596,8 @@ void batch_apply_fraction(fm_batch* b) {
         c->grid_data = std::max(1, (int)std::lround(c->base_data * b->fraction));
         c->grid_ls = std::max(1, (int)std::lround(c->base_ls * b->fraction));
         c->grid_ic = std::max(1, (int)std::lround(c->base_ic * b->fraction));
-        c->grid_icb = std::max(1, (int)std::lround(c->base_icb * b->fraction));
+        const int icb = std::max(1, std::min(c->ntiles, std::min(c->occ_icb, b->icb_per_sm) * c->nsm));
+        c->grid_icb = std::max(1, (int)std::lround(icb * b->fraction));
         if (c->base_ict) c->grid_ict = std::max(1, (int)std::lround(c->base_ict * b->fraction));
         if (c->base_ictg) c->grid_ictg = std::max(1, (int)std::lround(c->base_ictg * b->fraction));
         if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
@@ -1799,30 +1803,40 @@ int fm_batch_autotune(fm_batch* b, int niter_probe, double* best_fraction, doubl
     ok = ok && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
     const double cand[4] = {1.0, 0.5, 0.25, 0.125};
     const int wcand[3][2] = {{2, 1}, {1, 1}, {3, 2}};  // forward tile claim order weights (X + Y, Z)
+    const int bcand[3] = {1, 2, 3};                    // back-substitution blocks per SM
     double bestf = b->fraction, bestt = 1e300;
-    int bestw = 0;
+    int bestw = 0, bestb = b->icb_per_sm;
     int rc = ok ? FM_OK : FM_ERR_OOM;
+    auto probe = [&](double f, int wq, int bq) {
+        b->fraction = f;
+        b->icb_per_sm = bcand[bq];
+        batch_apply_fraction(b);
+        rc = batch_solve(b, w.data(), 1, niter_probe, nullptr);  // warm-up and capture
+        if (rc != FM_OK) return;
+        cudaEventRecord(e0, b->origin);
+        rc = batch_solve(b, w.data(), 1, niter_probe, nullptr);
+        cudaEventRecord(e1, b->origin);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rc == FM_OK && ms < bestt) {
+            bestt = ms;
+            bestf = f;
+            bestw = wq;
+            bestb = bcand[bq];
+        }
+    };
+    // grid fraction x forward claim order at two back-substitution blocks per SM, then the
+    // back substitution's blocks per SM at the best of those
     for (int wq = 0; wq < 3 && rc == FM_OK; ++wq) {
         for (fm_ctx* c : b->v)
             if (!set_ic_order(c, wcand[wq][0], wcand[wq][1])) rc = FM_ERR_CUDA;
-        for (int q = 0; q < 4 && rc == FM_OK; ++q) {
-            b->fraction = cand[q];
-            batch_apply_fraction(b);
-            rc = batch_solve(b, w.data(), 1, niter_probe, nullptr);  // warm-up and capture
-            if (rc != FM_OK) break;
-            cudaEventRecord(e0, b->origin);
-            rc = batch_solve(b, w.data(), 1, niter_probe, nullptr);
-            cudaEventRecord(e1, b->origin);
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (rc == FM_OK && ms < bestt) {
-                bestt = ms;
-                bestf = cand[q];
-                bestw = wq;
-            }
-        }
+        for (int q = 0; q < 4 && rc == FM_OK; ++q) probe(cand[q], wq, 1);
     }
+    for (fm_ctx* c : b->v)
+        if (rc == FM_OK && !set_ic_order(c, wcand[bestw][0], wcand[bestw][1])) rc = FM_ERR_CUDA;
+    for (int bq = 0; bq < 3 && rc == FM_OK; ++bq)
+        if (bcand[bq] != 2) probe(bestf, bestw, bq);
     for (void* p : w)
         if (p) cudaFree(p);
     if (e0) cudaEventDestroy(e0);
@@ -1830,6 +1844,7 @@ int fm_batch_autotune(fm_batch* b, int niter_probe, double* best_fraction, doubl
     for (fm_ctx* c : b->v)
         if (!set_ic_order(c, wcand[bestw][0], wcand[bestw][1]) && rc == FM_OK) rc = FM_ERR_CUDA;
     b->fraction = bestf;
+    b->icb_per_sm = bestb;
     batch_apply_fraction(b);
     if (best_fraction) *best_fraction = bestf;
     if (best_ms) *best_ms = bestt;
@@ -1841,6 +1856,12 @@ int fm_batch_schedule(const fm_batch* b, double* fraction, int* order_wxy, int* 
     if (fraction) *fraction = b->fraction;
     if (order_wxy) *order_wxy = b->v[0]->ic_wxy;
     if (order_wz) *order_wz = b->v[0]->ic_wz;
+    return FM_OK;
+}
+
+int fm_batch_bwd_blocks(const fm_batch* b, int* blocks_per_sm) {
+    if (!b || !blocks_per_sm) return FM_ERR_ARG;
+    *blocks_per_sm = b->icb_per_sm;
     return FM_OK;
 }
 

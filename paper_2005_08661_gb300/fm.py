@@ -7,6 +7,7 @@ built (``paper_2005_08661_gb300.build.build()``); there is no fallback.
 from __future__ import annotations
 
 import ctypes as C
+import functools
 import os
 import threading
 
@@ -47,7 +48,8 @@ EXPORTS = ["fm_default_opts", "fm_create", "fm_set_data", "fm_init_omega", "fm_c
            "fm_batch_schedule",
            "fm_true_curv", "fm_adjoint_solve", "fm_implicit_grad", "fm_set_fat_model", "fm_wf_sweep",
            "fm_pwls_init", "fm_wf_amplitudes", "fm_wf_sweep_range", "fm_set_spin_limit", "fm_set_data_host",
-           "fm_solve_host", "fm_synchronize", "fm_ic_factor64", "fm_ic_factor_curv", "fm_ict_pattern"]
+           "fm_solve_host", "fm_synchronize", "fm_ic_factor64", "fm_ic_factor_curv", "fm_ict_pattern",
+           "fm_batch_bwd_blocks"]
 KERNELS = ["grad", "ic_fwd", "ic_bwd", "dir", "ls", "h2d", "d2h"]
 
 
@@ -115,6 +117,8 @@ def load_library(path=None):
         lib.fm_batch_autotune.argtypes = [vp, i, C.POINTER(d), C.POINTER(d)]
         lib.fm_batch_set_fraction.argtypes = [vp, d]
         lib.fm_batch_schedule.argtypes = [vp, C.POINTER(d), C.POINTER(i), C.POINTER(i)]
+        lib.fm_batch_bwd_blocks.argtypes = [vp, C.POINTER(i)]
+        lib.fm_batch_bwd_blocks.restype = C.c_int
         lib.fm_batch_ctx.argtypes = [vp, i]
         lib.fm_batch_ctx.restype = vp
         lib.fm_batch_destroy.argtypes = [vp]
@@ -132,6 +136,26 @@ def load_library(path=None):
 
 def _dptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _ordered(fn):
+    """Orders a call that runs on the handle's stream with torch's current stream: the
+    handle's stream first waits for the work already queued on the current stream (which
+    made the input tensors), and the current stream then waits for the call's kernels, so
+    a returned tensor may be used (or freed) on the current stream at once.  Nothing is
+    added when the two streams are the same."""
+    @functools.wraps(fn)
+    def wrapper(self, *args, **kwargs):
+        cur = self._torch.cuda.current_stream(self.device)
+        same = cur == self.stream
+        if not same:
+            self.stream.wait_stream(cur)
+        try:
+            return fn(self, *args, **kwargs)
+        finally:
+            if not same:
+                cur.wait_stream(self.stream)
+    return wrapper
 
 
 class FieldMap:
@@ -192,6 +216,7 @@ class FieldMap:
         return self._torch.empty(self.shape, dtype=self.rdtype, device=self.device)
 
     # ---------------------------------------------------------------- API
+    @_ordered
     def set_data(self, y, smap, te, mask=None, beta=2.0 ** -3):
         t = self._torch
         nz, ny, nx = self.shape
@@ -243,11 +268,13 @@ class FieldMap:
     def synchronize(self):
         self._check(self.lib.fm_synchronize(self._h), "fm_synchronize")
 
+    @_ordered
     def init_omega(self):
         out = self.empty()
         self._check(self.lib.fm_init_omega(self._h, _dptr(out)), "fm_init_omega")
         return out
 
+    @_ordered
     def cost_grad(self, omega, want_cost=True, want_grad=True, want_curv=True):
         self._vec(omega, "omega")
         g = self.empty() if want_grad else None
@@ -257,12 +284,14 @@ class FieldMap:
                                           _dptr(g), _dptr(d)), "fm_cost_grad")
         return (cost.value if want_cost else None), g, d
 
+    @_ordered
     def ic_factor(self, omega, want_pivots=True):
         self._vec(omega, "omega")
         ip = self.empty() if want_pivots else None
         self._check(self.lib.fm_ic_factor(self._h, _dptr(omega), _dptr(ip)), "fm_ic_factor")
         return ip
 
+    @_ordered
     def ic_factor_curv(self, curv, want_pivots=True):
         """fm_ic_factor_curv: the preconditioner factor of diag(curv) + beta C'C."""
         self._vec(curv, "curv")
@@ -282,6 +311,7 @@ class FieldMap:
                     "fm_ict_pattern")
         return off, pl
 
+    @_ordered
     def ic_factor64(self, omega):
         """fm_ic_factor64: IC(0) factor at omega; returns the inverse pivots as a float64 tensor
         (FP32 mode: the hi + lo pair the forward sweep carries)."""
@@ -290,6 +320,7 @@ class FieldMap:
         self._check(self.lib.fm_ic_factor64(self._h, _dptr(omega), _dptr(ip)), "fm_ic_factor64")
         return ip
 
+    @_ordered
     def ic_apply(self, g, out=None):
         self._vec(g, "g")
         p = self.empty() if out is None else self._vec(out, "out")
@@ -316,6 +347,7 @@ class FieldMap:
         self._check(self.lib.fm_wf_sweep_range(self._h, C.byref(lo), C.byref(hi)), "fm_wf_sweep_range")
         return lo.value, hi.value
 
+    @_ordered
     def wf_sweep(self, nsweep=100, w_lo=None, w_hi=None, out=None):
         """Voxel-wise sweep initialisation; the default range is the library's
         (fm_wf_sweep_range)."""
@@ -325,6 +357,7 @@ class FieldMap:
         self._check(self.lib.fm_wf_sweep(self._h, int(nsweep), float(w_lo), float(w_hi), _dptr(out)), "fm_wf_sweep")
         return out
 
+    @_ordered
     def pwls_init(self, omega_tilde, niter=10, out=None):
         """PWLS initialisation (niter CG iterations) from the sweep's map."""
         self._vec(omega_tilde, "omega_tilde")
@@ -336,6 +369,7 @@ class FieldMap:
         """Sweep then PWLS: the water-fat initial map."""
         return self.pwls_init(self.wf_sweep(nsweep), niter)
 
+    @_ordered
     def wf_amplitudes(self, omega, y=None, smap=None, out=None):
         """(water, fat) complex maps at omega by the closed form of the water-fat model."""
         self._vec(omega, "omega")
@@ -353,6 +387,7 @@ class FieldMap:
                     "fm_wf_amplitudes")
         return w, f
 
+    @_ordered
     def true_curv(self, omega):
         """Exact second derivative of the data term at omega (0 outside the mask)."""
         self._vec(omega, "omega")
@@ -360,6 +395,7 @@ class FieldMap:
         self._check(self.lib.fm_true_curv(self._h, _dptr(omega), _dptr(h)), "fm_true_curv")
         return h
 
+    @_ordered
     def adjoint_solve(self, omega_hat, rhs, tol=None, maxiter=1000):
         """lambda = H_true^{-1} rhs by IC(0)-preconditioned CG.  Returns (lambda, iterations,
         relative residual).  tol defaults to 1e-6 (fp32) or 1e-12 (fp64)."""
@@ -373,6 +409,7 @@ class FieldMap:
                                               int(maxiter), C.byref(it), C.byref(rr)), "fm_adjoint_solve")
         return lam, it.value, rr.value
 
+    @_ordered
     def implicit_grad(self, omega_hat, lam, y=None, smap=None, want_dy=True, want_dbeta=True):
         """(dl/dy, dl/dbeta) of a loss whose adjoint is lam; y and smap default to the
         arrays of the last set_data."""
@@ -386,6 +423,7 @@ class FieldMap:
                                               _dptr(dy), C.byref(db) if want_dbeta else None), "fm_implicit_grad")
         return dy, (db.value if want_dbeta else None)
 
+    @_ordered
     def solve(self, omega=None, niter=50, want_history=True):
         """Run niter NCG-MLS iterations; omega=None starts from Eq. 6.  Returns (omega, costs)."""
         init = omega is None
@@ -477,6 +515,7 @@ class FieldMapBatch:
         if st != FM_OK:
             raise FmError(st, f"{what}: {self.lib.fm_strerror(st).decode()}")
 
+    @_ordered
     def set_data(self, k, y, smap, te, mask=None, beta=2.0 ** -3):
         nx, ny, nz, nc, L = self.shapes[k]
         if not (y.is_cuda and y.dtype == self.cdtype and y.is_contiguous() and tuple(y.shape) == (L, nc, nz, ny, nx)):
@@ -489,6 +528,7 @@ class FieldMapBatch:
         nx, ny, nz, _, _ = self.shapes[k]
         return self._torch.empty((nz, ny, nx), dtype=self.rdtype, device=self.device)
 
+    @_ordered
     def solve(self, omegas=None, niter=50, want_history=True):
         """Returns (list of field maps, list of cost histories or None)."""
         n = len(self.shapes)
@@ -517,6 +557,12 @@ class FieldMapBatch:
         f, wxy, wz = C.c_double(), C.c_int(), C.c_int()
         self._check(self.lib.fm_batch_schedule(self._h, C.byref(f), C.byref(wxy), C.byref(wz)), "fm_batch_schedule")
         return f.value, (wxy.value, wz.value)
+
+    def bwd_blocks_per_sm(self):
+        """Back-substitution blocks per SM in effect (chosen by autotune)."""
+        n = C.c_int()
+        self._check(self.lib.fm_batch_bwd_blocks(self._h, C.byref(n)), "fm_batch_bwd_blocks")
+        return n.value
 
     def close(self):
         if getattr(self, "_h", None):

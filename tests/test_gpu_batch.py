@@ -55,6 +55,7 @@ def test_batch_autotune_picks_a_candidate_and_results_stay_correct():
     assert f in (1.0, 0.5, 0.25, 0.125) and ms > 0
     frac, weights = b.schedule()
     assert frac == f and weights in ((2, 1), (1, 1), (3, 2))
+    assert b.bwd_blocks_per_sm() in (1, 2, 3)
     ws, costs = b.solve(niter=4)
     for k, v in enumerate(vols):
         r = Oracle.from_volume(v).solve(niter=4, nls=5)

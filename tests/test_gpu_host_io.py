@@ -99,3 +99,31 @@ def test_asynchronous_solve_reports_its_error_at_the_next_synchronisation():
     assert e.value.status == FM_ERR_NOT_PD
     fm.synchronize()  # the error was reported once and cleared
     fm.close()
+
+
+@pytest.mark.parametrize("precond", ["ic0", "none"])
+def test_handle_on_a_side_stream_is_ordered_with_the_current_stream(precond):
+    """A FieldMap created on a stream other than torch's current one: the tensors its calls
+    return must be complete when read on the current stream right after the call, although
+    fm_solve returns without waiting when no cost history is asked for."""
+    import torch
+    from synth import full8_small_config
+    vol = full8_small_config()
+    fm_cur = open_fm(vol, "fp32", precond=precond)
+    w_ref, _ = fm_cur.solve(niter=40, want_history=False)
+    w_ref = w_ref.clone()
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    fm_side = open_fm(vol, "fp32", precond=precond, stream=side)
+    for niter in (40, 1, 40):
+        w, _ = fm_side.solve(niter=niter, want_history=False)
+        got = w.clone()  # on the current stream, with no explicit synchronisation
+        if niter == 40:
+            assert torch.equal(got, w_ref)
+        else:
+            assert not torch.equal(got, w_ref)
+    _, g, _ = fm_side.cost_grad(w_ref)
+    _, g_ref, _ = fm_cur.cost_grad(w_ref)
+    assert torch.equal(g.clone(), g_ref)
+    fm_side.close()
+    fm_cur.close()
