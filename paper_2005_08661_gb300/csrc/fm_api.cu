@@ -40,11 +40,12 @@ struct fm_ctx {
     void *d = nullptr, *p = nullptr, *v = nullptr, *ip = nullptr;
     double *scal = nullptr, *partials = nullptr, *tile_part = nullptr;
     void* face = nullptr;
+    size_t face_bytes = 0;  // per-tile IC face buffers (the forward part starts unset: all bits set)
     double *hist_cost = nullptr, *hist_alpha = nullptr, *hist_mu = nullptr;
     int hist_cap = 0;
     int hist_gen = 0;      // bumped when the history buffers move (captured graphs hold them)
     int* istate = nullptr;
-    int* icint = nullptr;  // [0] fwd ticket, [1] bwd ticket, [2] bwd done, [3] pad, flags fwd[nt], flags bwd[nt]
+    int* icint = nullptr;  // IC sweeps: [0] forward ticket, [1] back-substitution ticket, [2] its done count, [3] pad
     int* order = nullptr;
     int ntx = 0, nty = 0, ntz = 0, ntiles = 0;
     int ic_wxy = 2, ic_wz = 1;  // forward tile claim order weights
@@ -151,9 +152,12 @@ void free_all(fm_ctx* c) {
 cudaError_t reset_barrier(fm_ctx* c) {
     return cudaMemsetAsync(c->istate + I_BAR_COUNT, 0, sizeof(int), c->stream);
 }
+// After a device error the IC forward sweep's face entries may hold values that no reader
+// consumed (a fetch that gave up), so they are set back to the unset pattern too.
 cudaError_t reset_dev(fm_ctx* c) {
     cudaError_t e = cudaMemsetAsync(c->istate + I_ERR, 0, sizeof(int), c->stream);
     if (e == cudaSuccess) e = reset_barrier(c);
+    if (e == cudaSuccess && c->face) e = cudaMemsetAsync(c->face, 0xff, c->face_bytes, c->stream);
     return e;
 }
 
@@ -242,11 +246,9 @@ cudaError_t run_grad(fm_ctx* c, const void* w_in, const void* zdir, void* w_out,
 template <typename T>
 cudaError_t run_ic0(fm_ctx* c, const void* d, const void* g, void* p, const void* gdot, const void* gpdot,
                     int slot, float* ip_lo = nullptr) {
-    const size_t nint = 4 + 2 * (size_t)c->ntiles;
-    cudaError_t e = cudaMemsetAsync(c->icint, 0, nint * sizeof(int), c->stream);
+    cudaError_t e = cudaMemsetAsync(c->icint, 0, 4 * sizeof(int), c->stream);
     if (e != cudaSuccess) return e;
     IcArgs f = ic_args(c);
-    f.flags = c->icint + 4;
     f.ticket = c->icint + 0;
     f.d = d;
     f.ip_in = d ? nullptr : c->ip;
@@ -265,7 +267,6 @@ cudaError_t run_ic0(fm_ctx* c, const void* d, const void* g, void* p, const void
     }
     if (e != cudaSuccess) return e;
     IcArgs b = ic_args(c);
-    b.flags = c->icint + 4 + c->ntiles;
     b.ticket = c->icint + 1;
     b.done = c->icint + 2;
     b.order = c->order + c->ntiles;
@@ -805,17 +806,28 @@ int implicit_t(fm_ctx* c, const void* y, const void* smap, const void* w_hat, co
     return FM_OK;
 }
 
+#ifndef FM_IC_BXY
+#define FM_IC_BXY 2
+#endif
+#ifndef FM_IC_BBLK
+#define FM_IC_BBLK 2
+#endif
+#ifndef FM_IC_BZ
+#define FM_IC_BZ 1
+#endif
+
 // Tile claim orders: a weighted tile hyperplane wxy (X + Y) + wz Z (ties: z, y, x).  Every
-// weight is positive, so a tile's -x, -y, -z neighbours always come first.  The forward sweep
-// streams faces, and a tile there starts about twice as many steps behind its x / y
-// predecessors as behind its z predecessor, so it takes wxy : wz (default 2 : 1).  The
-// tile-by-tile back substitution walks the plain hyperplane X + Y + Z backwards.  Uploads
-// both orders synchronously.
+// weight is positive, so a tile's -x, -y, -z neighbours always come first.  Both sweeps
+// stream faces, and a tile starts about 38 steps plus one hand-off behind its x / y
+// predecessors and 14 steps plus one hand-off behind its z predecessor, so the forward order
+// takes wxy : wz (default 2 : 1) and the back substitution walks FM_IC_BXY : FM_IC_BZ
+// (2 : 1; measured on the 256 x 256 x 128 volume against 1 : 1 and 3 : 2) backwards.
+// Uploads both orders synchronously.
 bool set_ic_order(fm_ctx* c, int wxy, int wz) {
     std::vector<int> ord(2 * (size_t)c->ntiles);
     const int ntx = c->ntx, nty = c->nty;
     for (int pass = 0; pass < 2; ++pass) {
-        const int a_xy = pass == 0 ? wxy : 1, a_z = pass == 0 ? wz : 1;
+        const int a_xy = pass == 0 ? wxy : FM_IC_BXY, a_z = pass == 0 ? wz : FM_IC_BZ;
         auto first = ord.begin() + (size_t)pass * c->ntiles;
         for (int t = 0; t < c->ntiles; ++t) first[t] = t;
         std::stable_sort(first, first + c->ntiles, [&](int a, int b) {
@@ -961,7 +973,7 @@ int fm_create(fm_ctx** out, int nx, int ny, int nz, int ncoil, int necho, const 
         const int occ_b = f64 ? ic_max_blocks_per_sm<double>(true) : ic_max_blocks_per_sm<float>(true);
         if (occ_f < 1 || occ_b < 1) return bail(FM_ERR_CUDA);
         c->grid_ic = std::max(1, std::min(c->ntiles, occ_f * c->nsm));
-        c->grid_icb = std::max(1, std::min(c->ntiles, std::min(occ_b, 2) * c->nsm));
+        c->grid_icb = std::max(1, std::min(c->ntiles, std::min(occ_b, FM_IC_BBLK) * c->nsm));
         c->occ_icb = occ_b;
     }
     c->base_data = c->grid_data;
@@ -1002,11 +1014,12 @@ int fm_create(fm_ctx** out, int nx, int ny, int nz, int ncoil, int necho, const 
     A(&c->d, vb); A(&c->p, vb); A(&c->v, vb); A(&c->ip, vb); A(&c->rho, vb);
     A(&c->scal, S_NSCAL * sizeof(double));
     A(&c->partials, std::max<size_t>(8 * (size_t)std::max(c->grid_data, c->grid_ls), nchunks) * sizeof(double));
-    A(&c->face, (size_t)c->ntiles *
-                    (o.precision == FM_FP64 ? ic_face_bytes_per_tile<double>() : ic_face_bytes_per_tile<float>()));
+    c->face_bytes = (size_t)c->ntiles *
+                    (o.precision == FM_FP64 ? ic_face_bytes_per_tile<double>() : ic_face_bytes_per_tile<float>());
+    A(&c->face, c->face_bytes);
     A(&c->tile_part, 2 * (size_t)c->ntiles * sizeof(double));
     A(&c->istate, I_NISTATE * sizeof(int));
-    A(&c->icint, (4 + 2 * (size_t)c->ntiles) * sizeof(int));
+    A(&c->icint, 4 * sizeof(int));
     A(&c->order, 2 * (size_t)c->ntiles * sizeof(int));  // forward order, then the back substitution's
 
     if (!ok) { cudaGetLastError(); return bail(FM_ERR_OOM); }
@@ -1023,7 +1036,8 @@ int fm_create(fm_ctx** out, int nx, int ny, int nz, int ncoil, int necho, const 
     if (!set_ic_order(c, FM_IC_WXY, FM_IC_WZ) ||
         cudaMemset(c->scal, 0, S_NSCAL * sizeof(double)) != cudaSuccess ||
         cudaMemset(c->istate, 0, I_NISTATE * sizeof(int)) != cudaSuccess ||
-        cudaMemset(c->nb, 0, (size_t)c->nv) != cudaSuccess)
+        cudaMemset(c->nb, 0, (size_t)c->nv) != cudaSuccess ||
+        cudaMemset(c->face, 0xff, c->face_bytes) != cudaSuccess)  // forward faces start unset
         return bail(FM_ERR_CUDA);
     *out = c;
     return FM_OK;

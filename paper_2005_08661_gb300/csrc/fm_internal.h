@@ -259,7 +259,6 @@ struct IcArgs {
     Geo geo;
     int ntx, nty, ntz, ntiles;
     const int* order;      // [ntiles] tiles in a dependency-respecting order
-    int* flags;            // [ntiles] 0/1
     int* ticket;           // claim counter
     int* done;             // finished-tile counter
     double beta;

@@ -21,10 +21,10 @@
 // per hyperplane, taking the -y value from the neighbouring lane by shuffle, the -z value
 // from the warp below through shared memory and the -x value from its own register.  The
 // step body is branch-free (divergent branches cost more per step than the idle lanes'
-// arithmetic).  In the forward sweep faces stream between tiles while they sweep (see
-// "streamed faces" below): a tile runs a fixed number of hyperplanes behind its
-// predecessors instead of waiting for them to finish.  The back substitution goes tile by
-// tile.  The row-coalesced write-back of the whole tile follows the sweep.
+// arithmetic).  In both sweeps faces stream between tiles while they sweep (see "streamed
+// faces" below): a tile runs a fixed number of hyperplanes behind its predecessors instead
+// of waiting for them to finish.  The row-coalesced write-back of the whole tile follows the
+// sweep.
 //
 // Pivot arithmetic.  FP64 mode uses IEEE double.  FP32 mode carries each inverse pivot as
 // an unevaluated pair a + b of floats (about 46 significant bits, like double-float), but
@@ -122,6 +122,7 @@ template <> struct PivOps<float> {
     }
 };
 
+
 // Faces are written by other CTAs of the same launch: read them through L2.
 __device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ float ld_cg(const float* p) { return __ldcg(p); }
@@ -207,27 +208,17 @@ __device__ __forceinline__ void stage_row_u8(uint8_t* s, const uint8_t* g, int r
 #ifndef FM_IC_CS
 #define FM_IC_CS 7
 #endif
-#ifndef FM_IC_SPLIT
-#define FM_IC_SPLIT 1
-#endif
-#ifndef FM_IC_SLEEP
-#define FM_IC_SLEEP 64
-#endif
 constexpr int kTZ = 8;              // tile = 32 x 32 x 8 voxels, 8 compute warps
 constexpr int kSteps = 62 + kTZ;    // local hyperplanes lx + ly + lz of a tile
 constexpr int kCS = FM_IC_CS;       // steps per published chunk
 constexpr int kNch = (kSteps + kCS - 1) / kCS;
 constexpr int kCompute = 32 * kTZ;  // compute threads
-constexpr bool kSplit = FM_IC_SPLIT != 0;  // separate warps fetch faces and publish progress
-constexpr int kThreadsIC = kCompute + (kSplit ? 64 : 32);
-constexpr unsigned kSleepMax = FM_IC_SLEEP;  // cap of the streaming warps' poll backoff (ns)
-#ifndef FM_IC_BWD_UNROLL
-#define FM_IC_BWD_UNROLL 7
-#endif
-constexpr int kBwdUnroll = FM_IC_BWD_UNROLL;  // unroll factor of the back substitution's step loop
+constexpr int kThreadsIC = kCompute + 32;  // + one warp that fetches incoming faces
 
 // Face layout per tile (counts of values): x face [TZ][32] (lz, ly), y face [TZ][32]
-// (lz, lx), z face [32][32] (ly, lx).
+// (lz, lx), z face [32][32].  In shared memory the z face is (ly, lx); in the forward
+// sweep's global face buffer it is stored by diagonals t = lx + ly (see zdiag), so the
+// entries produced at one step, and fetched for one step, are contiguous.
 struct FN {
     static constexpr int x = 0, y = kTZ * 32, z = 2 * kTZ * 32, n = 2 * kTZ * 32 + 1024;
 };
@@ -267,126 +258,159 @@ __device__ __forceinline__ int out_face_vox(int i, bool fwd) {
 
 // ------------------------------------------------------------------ streamed faces
 //
-// A forward tile's sweep does not wait for its predecessor tiles to finish: each tile
-// publishes, in a flag holding a step count, how many of its local hyperplanes are done, and
-// writes every voxel of its three outgoing faces to the face buffer as soon as it computes
-// it.  A successor's step s needs, from its -x and -y neighbours, face values those tiles
-// produce at their step s + 31, and from its -z neighbour values produced at step
-// s + kTZ - 1.  So a successor can run about 32 steps behind its x / y predecessors and kTZ
-// behind its z predecessor instead of a whole tile (70 steps) behind; the chain through the
-// grid shrinks from (tile levels) x 70 steps towards the nx + ny + nz hyperplanes of the
-// global wavefront, less the hand-off latency between CTAs (a few microseconds per hop).
+// A forward tile's sweep does not wait for its predecessor tiles to finish: every voxel of a
+// tile's three outgoing faces is written to the face buffer as soon as it is computed.  A
+// successor's step s needs, from its -x and -y neighbours, face values those tiles produce
+// at their step s + 31, and from its -z neighbour values produced at step s + kTZ - 1.  So a
+// successor runs about 32 steps behind its x / y predecessors and kTZ behind its z
+// predecessor instead of a whole tile (70 steps) behind; the chain through the grid shrinks
+// from (tile levels) x 70 steps towards the nx + ny + nz hyperplanes of the global wavefront,
+// plus one hand-off latency per tile hop.
 //
-// One extra warp per CTA does the streaming: it polls the predecessors' flags (bounded, with
-// backoff), copies each chunk's incoming face values into shared memory as soon as they are
-// published, signals the compute warps through a shared-memory counter, and forwards the
-// compute warps' own progress to this tile's flag.  The compute warps synchronise among
-// themselves with a named barrier and never poll global memory.
+// The face entries are their own ready signal.  Between launches every forward face entry
+// holds an all-ones bit pattern -- a NaN that no FP32 / FP64 operation produces (arithmetic
+// returns the canonical NaN) and that a producer never writes (canon).  A successor polls the
+// entries themselves with relaxed loads: an entry that no longer holds the pattern has its
+// final value for this launch (each entry is written once, element by element, with relaxed
+// stores).  This spares the producer a release fence and the consumer a flag round trip
+// before the data round trip: the hand-off is one store's propagation plus the poll.  Each
+// entry has exactly one reader (the neighbour across that face), which writes the pattern
+// back after reading it, so the buffer is ready for the next launch; the host fills it with
+// the pattern when the context is created and after a device error.
+//
+// One extra warp per CTA fetches the faces: chunk by chunk (kCS steps), it polls the
+// entries the chunk needs (bounded, with a short sleep), copies them into shared memory and
+// signals the compute warps through a shared-memory counter.  The compute warps synchronise
+// among themselves with a named barrier and never poll global memory.
 
 __device__ __forceinline__ void bar_compute() { asm volatile("bar.sync 1, %0;" ::"n"(kCompute) : "memory"); }
-__device__ __forceinline__ int ld_acq_cta(const int* p) {
-    int v;
-    asm volatile("ld.acquire.cta.shared.b32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+
+// the unset pattern of a face entry, and values kept clear of it
+__device__ __forceinline__ bool unset(float x) { return __float_as_uint(x) == 0xffffffffu; }
+__device__ __forceinline__ bool unset(double x) { return __double_as_longlong(x) == -1LL; }
+__device__ __forceinline__ bool unset(PF x) { return unset(x.a) || unset(x.b); }
+__device__ __forceinline__ float canon(float x) { return unset(x) ? __uint_as_float(0x7fffffffu) : x; }
+__device__ __forceinline__ double canon(double x) {
+    return unset(x) ? __longlong_as_double(0x7fffffffffffffffLL) : x;
+}
+__device__ __forceinline__ PF canon(PF x) { return {canon(x.a), canon(x.b)}; }
+
+// relaxed (gpu scope) loads and stores of face entries
+__device__ __forceinline__ float ld_rlx(const float* p) {
+    float v;
+    asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
     return v;
 }
-__device__ __forceinline__ void st_rel_cta(int* p, int v) {
-    asm volatile("st.release.cta.shared.b32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
+__device__ __forceinline__ double ld_rlx(const double* p) {
+    double v;
+    asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ PF ld_rlx(const PF* p) {
+    PF v;
+    asm volatile("ld.relaxed.gpu.global.v2.f32 {%0, %1}, [%2];" : "=f"(v.a), "=f"(v.b) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ void st_unset(float* p) {
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(-1) : "memory");
+}
+__device__ __forceinline__ void st_unset(double* p) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(-1LL) : "memory");
+}
+__device__ __forceinline__ void st_unset(PF* p) {
+    asm volatile("st.relaxed.gpu.global.v2.b32 [%0], {%1, %1};" ::"l"(p), "r"(-1) : "memory");
 }
 
-// Published steps a predecessor must have completed before chunk c may start: x / y faces
-// are produced 31 steps, z faces kTZ - 1 steps, after they are needed downstream.
-__device__ __forceinline__ int need_xy(int c) { return min((c + 1) * kCS + 31, kSteps); }
-__device__ __forceinline__ int need_z(int c) { return min((c + 1) * kCS + kTZ - 1, kSteps); }
+// Offset of diagonal t = lx + ly (0 <= t <= 62) in the diagonal-major z face: diagonal t holds
+// min(t + 1, 63 - t) entries, ordered by lx.
+__device__ __forceinline__ int zdiag(int t) { return t <= 32 ? t * (t + 1) / 2 : 528 + (t - 32) * (95 - t) / 2; }
 
-// Face entries used (ox = oz = 0) or produced (ox = 31, oz = kTZ - 1) at local step s of
-// the forward sweep: x face (ly, lz) with ly + lz = s - ox, y face (lx, lz) with lx + lz = s - ox,
-// z face (lx, ly) with lx + ly = s - oz.  Each lane takes at most one z-face entry and one x- or
-// y-face entry per step; -1 = none.
-__device__ __forceinline__ int z_entry(int s, int oz, int lane) {
-    const int t = s - oz, lx = max(0, t - 31) + lane;
-    return (t >= 0 && lx <= min(31, t)) ? FN::z + (t - lx) * 32 + lx : -1;
+// Face entries used at local step s of the forward sweep: x face (ly, lz) with ly + lz = s,
+// y face (lx, lz) with lx + lz = s, z face (lx, ly) with lx + ly = s.  Each lane takes at most
+// one z-face entry and one x- or y-face entry per step; -1 = none.  z_entry returns the shared
+// memory index; lane k of a z diagonal reads global entry FN::z + zdiag(s) + k.
+__device__ __forceinline__ int z_entry(int s, int lane) {
+    const int lx = max(0, s - 31) + lane;
+    return (s >= 0 && lx <= min(31, s)) ? FN::z + (s - lx) * 32 + lx : -1;
 }
-__device__ __forceinline__ int xy_entry(int s, int ox, int lane, int& which) {
-    const int t = s - ox;
+__device__ __forceinline__ int xy_entry(int s, int lane, int& which) {
     if (lane < kTZ) {  // x face: lanes 0..TZ-1 take lz = lane
-        const int ly = t - lane;
+        const int ly = s - lane;
         which = 0;
         return (ly >= 0 && ly < 32) ? FN::x + lane * 32 + ly : -1;
     }
     if (lane >= 16 && lane < 16 + kTZ) {  // y face: lanes 16.. take lz = lane - 16
-        const int lz = lane - 16, lx = t - lz;
+        const int lz = lane - 16, lx = s - lz;
         which = 1;
         return (lx >= 0 && lx < 32) ? FN::y + lz * 32 + lx : -1;
     }
     return -1;
 }
 
-// The streaming warp's loop for one tile.  src[3]: predecessor tiles (x, y, z) or -1;
-// load(c) copies chunk c's entries (zeros where there is no predecessor); flags hold step
-// counts.  Returns false if a wait gave up.
-template <typename L>
-__device__ __forceinline__ bool stream_faces(const int* flags, int* own_flag, const int (&src)[3], int* s_ready,
-                                             int* s_done, long long spin_limit, bool fetch, bool publish, L&& load) {
-    const int lane = threadIdx.x & 31;
-    int next = fetch ? 0 : kNch, published = publish ? 0 : kSteps;
-    long long idle = 0;
-    unsigned ns = 32;
-    bool ok = true;
-    while (next < kNch || published < kSteps) {
-        bool did = false;
-        if (next < kNch) {
-            // lanes 0..2 poll the three predecessors at once
-            int have = 1;
-            const int mine = lane == 0 ? src[0] : lane == 1 ? src[1] : lane == 2 ? src[2] : -1;
-            if (ok && mine >= 0) have = ld_acquire(flags + mine) >= (lane == 2 ? need_z(next) : need_xy(next));
-            have = __all_sync(0xffffffffu, have);
-            if (have || !ok) {
-                __syncwarp();  // orders every lane's face loads after lanes 0..2's acquires
-                load(next);
-                __syncwarp();
-                if (lane == 0) st_rel_cta(s_ready, next + 1);
-                ++next;
-                did = true;
-            }
-        }
-        if (published < kSteps) {
-            const int local = __shfl_sync(0xffffffffu, lane == 0 ? ld_acq_cta(s_done) : 0, 0);
-            if (local > published) {
-                if (lane == 0) st_release(own_flag, local);
-                published = local;
-                did = true;
-            }
-        }
-        if (did) {
-            idle = 0;
-            ns = 32;
-        } else {
-            if (++idle > spin_limit && ok) {
-                ok = false;  // give up waiting: the faces stay unfilled, the error is reported
-                idle = 0;
-            }
-            __nanosleep(ns);
-            if (ns < kSleepMax) ns <<= 1;
-        }
-    }
-    return ok;
+// Predicated relaxed stores of outgoing face entries: written by the one lane that produces
+// the entry at a step, without a divergent branch in the step body.  The caller keeps the
+// value clear of the unset pattern: an inverse pivot is finite by construction (0 where the
+// pivot is not positive or outside the mask), and v passes through canon.
+__device__ __forceinline__ void st_if(bool p, double* a, double v) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q st.relaxed.gpu.global.f64 [%1], %2;\n\t}"
+                 ::"r"((int)p), "l"(a), "d"(v) : "memory");
+}
+__device__ __forceinline__ void st_if(bool p, float* a, float v) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q st.relaxed.gpu.global.f32 [%1], %2;\n\t}"
+                 ::"r"((int)p), "l"(a), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_if(bool p, PF* a, PF v) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q st.relaxed.gpu.global.v2.f32 [%1], {%2, %3};\n\t}"
+                 ::"r"((int)p), "l"(a), "f"(v.a), "f"(v.b) : "memory");
 }
 
-// Compute warps: wait until chunk c of the incoming faces is in shared memory (bounded).
-__device__ __forceinline__ void wait_chunk(const int* s_ready, int c, long long limit, int* istate) {
+// After a tile's sweep every entry of its incoming faces has been read (the compute warps
+// waited for every chunk), so the compute warps return them to the unset pattern for the
+// next launch: the -x (or +x) neighbour's x face, the y neighbour's y face and the z
+// neighbour's z face are contiguous ranges of those tiles' face buffers.
+template <typename T>
+__device__ __forceinline__ void unset_faces(T* fx, T* fy, T* fz) {
+    for (int i = threadIdx.x; i < FN::n; i += kCompute) {
+        T* f = i < FN::y ? fx : i < FN::z ? fy : fz;
+        if (f) st_unset(f + i);
+    }
+}
+
+// Chunk hand-off from the fetch warp to the compute warps: one mbarrier per chunk with an
+// arrival count of 1, completing one phase per tile (the wait parity is the CTA's tile count
+// & 1).  The fetch warp's lane 0 arrives (release) once the chunk's faces are in shared
+// memory; the compute warps wait with try_wait (acquire), which suspends the warp instead of
+// spinning and, unlike an acquire load, does not wait for the warp's own outstanding global
+// stores to drain.
+__device__ __forceinline__ void mbar_init(unsigned long long* m, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* m) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n\t}"
+                 ::"r"(smem_u32(m)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* m, unsigned parity) {
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(smem_u32(m)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Compute warps: wait until a chunk of the incoming faces is in shared memory (bounded).
+__device__ __forceinline__ void wait_chunk(unsigned long long* m, unsigned parity, long long limit, int* istate) {
     long long n = 0;
-    while (ld_acq_cta(s_ready) <= c) {
+    while (!mbar_try_wait(m, parity)) {
         if (++n > limit) {
             set_err(istate, FM_ERR_TIMEOUT);
             break;
         }
-        __nanosleep(32);
     }
 }
 
-// mode 0: pivots from d (factor + forward); mode 1: stored 1/pi (forward only)
-template <typename T>
-__global__ void __launch_bounds__(kThreadsIC) k_ic_fwd(IcArgs a, int mode, PivScal pc) {
+// MODE 0: pivots from d (factor + forward); MODE 1: stored 1/pi (forward only)
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kThreadsIC) k_ic_fwd(IcArgs a, PivScal pc) {
+    constexpr int mode = MODE;
     using Ops = PivOps<T>;
     using P = typename Ops::P;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -398,7 +422,8 @@ __global__ void __launch_bounds__(kThreadsIC) k_ic_fwd(IcArgs a, int mode, PivSc
     T* f_v = (T*)(zb_ip + 2 * kTZ * 32);
     T* zb_v = f_v + FN::n;
     uint8_t* snb = (uint8_t*)(zb_v + 2 * kTZ * 32);  // [TZ][32][32]
-    __shared__ int s_tile, s_ready, s_done;
+    __shared__ int s_tile;
+    __shared__ __align__(8) unsigned long long s_mbar[kNch];
 
     const Geo geo = a.geo;
     const int nx = geo.nx, ny = geo.ny, nz = geo.nz;
@@ -414,12 +439,13 @@ __global__ void __launch_bounds__(kThreadsIC) k_ic_fwd(IcArgs a, int mode, PivSc
     auto face_ip = [&](int t) { return (P*)(faceb + (size_t)t * face_bytes_per_tile<T>()); };
     auto face_v = [&](int t) { return (T*)(face_ip(t) + FN::n); };
 
+    if (tid == 0)
+        for (int c = 0; c < kNch; ++c) mbar_init(&s_mbar[c], 1);
+    unsigned par = 0;  // phase parity of this CTA's current tile
     for (;;) {
         if (tid == 0) {
             const int t = atomicAdd(a.ticket, 1);
             s_tile = t < a.ntiles ? a.order[t] : -1;
-            s_ready = 0;
-            s_done = 0;
         }
         __syncthreads();
         const int tile = s_tile;
@@ -428,32 +454,64 @@ __global__ void __launch_bounds__(kThreadsIC) k_ic_fwd(IcArgs a, int mode, PivSc
         const int x0 = X * 32, y0 = Y * 32, z0 = Z * kTZ;
 
         if (wz == kTZ) {
-            // streaming warp: the -x, -y, -z neighbours' outgoing +x, +y, +z faces
-            const int src[3] = {X > 0 ? tile - 1 : -1, Y > 0 ? tile - a.ntx : -1,
-                                Z > 0 ? tile - a.ntx * a.nty : -1};
-            auto load = [&](int c) {
-                // all loads of the chunk first (in flight together), then the shared stores
+            // fetch warp: the -x, -y, -z neighbours' outgoing +x, +y, +z faces, chunk by chunk
+            const int sx = X > 0 ? tile - 1 : -1, sy = Y > 0 ? tile - a.ntx : -1;
+            const int sz = Z > 0 ? tile - a.ntx * a.nty : -1;
+            bool ok = true;
+            for (int c = 0; c < kNch; ++c) {
                 P zp[kCS], qp[kCS];
                 T zv[kCS], qv[kCS];
-                int zi[kCS], qi[kCS];
+                int zi[kCS], zg[kCS], qi[kCS], qsrc[kCS];
+                unsigned want = 0;  // bit q: z entry of step q; bit kCS + q: x / y entry
 #pragma unroll
                 for (int q = 0; q < kCS; ++q) {
                     const int s = c * kCS + q;
                     int which = 0;
-                    zi[q] = s < kSteps ? z_entry(s, 0, lane) : -1;
-                    qi[q] = s < kSteps ? xy_entry(s, 0, lane, which) : -1;
-                    const int sz = src[2], sq = which ? src[1] : src[0];
+                    zi[q] = s < kSteps ? z_entry(s, lane) : -1;
+                    zg[q] = FN::z + zdiag(min(s, 62)) + lane;
+                    qi[q] = s < kSteps ? xy_entry(s, lane, which) : -1;
+                    qsrc[q] = which ? sy : sx;
                     zp[q] = Ops::zero();
                     qp[q] = Ops::zero();
                     zv[q] = T(0);
                     qv[q] = T(0);
-                    if (zi[q] >= 0 && sz >= 0) {
-                        if (mode == 0) zp[q] = ld_cg(face_ip(sz) + zi[q]);
-                        zv[q] = ld_cg(face_v(sz) + zi[q]);
+                    if (zi[q] >= 0 && sz >= 0) want |= 1u << q;
+                    if (qi[q] >= 0 && qsrc[q] >= 0) want |= 1u << (kCS + q);
+                }
+                // poll until every wanted entry is set (all of a round's loads are in flight
+                // together); a wait that gives up leaves zeros and reports the timeout
+                unsigned todo = ok ? want : 0u;
+                long long tries = 0;
+                while (__any_sync(0xffffffffu, todo != 0u)) {
+#pragma unroll
+                    for (int q = 0; q < kCS; ++q) {
+                        if (todo & (1u << q)) {
+                            if (mode == 0) zp[q] = ld_rlx(face_ip(sz) + zg[q]);
+                            zv[q] = ld_rlx(face_v(sz) + zg[q]);
+                        }
+                        if (todo & (1u << (kCS + q))) {
+                            if (mode == 0) qp[q] = ld_rlx(face_ip(qsrc[q]) + qi[q]);
+                            qv[q] = ld_rlx(face_v(qsrc[q]) + qi[q]);
+                        }
                     }
-                    if (qi[q] >= 0 && sq >= 0) {
-                        if (mode == 0) qp[q] = ld_cg(face_ip(sq) + qi[q]);
-                        qv[q] = ld_cg(face_v(sq) + qi[q]);
+#pragma unroll
+                    for (int q = 0; q < kCS; ++q) {
+                        if ((todo & (1u << q)) && !unset(zv[q]) && (mode != 0 || !unset(zp[q])))
+                            todo &= ~(1u << q);
+                        if ((todo & (1u << (kCS + q))) && !unset(qv[q]) && (mode != 0 || !unset(qp[q])))
+                            todo &= ~(1u << (kCS + q));
+                    }
+                    if (++tries > a.spin_limit && __any_sync(0xffffffffu, todo != 0u)) {
+                        ok = false;
+#pragma unroll
+                        for (int q = 0; q < kCS; ++q) {
+                            if (todo & (1u << q)) { zp[q] = Ops::zero(); zv[q] = T(0); }
+                            if (todo & (1u << (kCS + q))) { qp[q] = Ops::zero(); qv[q] = T(0); }
+                        }
+                        want &= ~todo;
+                        todo = 0u;
+                    } else if (todo != 0u) {
+                        __nanosleep(20);
                     }
                 }
 #pragma unroll
@@ -461,12 +519,10 @@ __global__ void __launch_bounds__(kThreadsIC) k_ic_fwd(IcArgs a, int mode, PivSc
                     if (zi[q] >= 0) { f_ip[zi[q]] = zp[q]; f_v[zi[q]] = zv[q]; }
                     if (qi[q] >= 0) { f_ip[qi[q]] = qp[q]; f_v[qi[q]] = qv[q]; }
                 }
-            };
-            if (!stream_faces(a.flags, a.flags + tile, src, &s_ready, &s_done, a.spin_limit, true, !kSplit, load))
-                set_err(a.istate, FM_ERR_TIMEOUT);
-        } else if (wz > kTZ) {
-            const int src[3] = {-1, -1, -1};
-            stream_faces(a.flags, a.flags + tile, src, &s_ready, &s_done, a.spin_limit, false, true, [](int) {});
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&s_mbar[c]);
+            }
+            if (!ok) set_err(a.istate, FM_ERR_TIMEOUT);  // the host resets the faces with the error
         } else {
             // stage this tile's inputs and form H while the predecessors are still running
             stage_row<T>(sg, g, tid, x0, y0, z0, geo, T(0));
@@ -504,12 +560,14 @@ __global__ void __launch_bounds__(kThreadsIC) k_ic_fwd(IcArgs a, int mode, PivSc
             const int zr = (lz > 0 ? lz - 1 : 0) * 32 + ly, zw = lz * 32 + ly;
             P* oip = face_ip(tile);
             T* ov = face_v(tile);
-            const long long wlimit = 16 * a.spin_limit;
             P out_ip = Ops::zero();
             T out_v = 0;
             bool bad = false;
+            // zdiag(t) - max(0, t - 31) for this warp's current diagonal t = s - lz (0 while t < 0):
+            // the z-face entry of lane ly at step s is FN::z + zbase + lx
+            int zbase = 0;
             for (int c = 0; c < kNch; ++c) {
-              wait_chunk(&s_ready, c, wlimit, a.istate);
+              wait_chunk(&s_mbar[c], par, a.spin_limit, a.istate);
 #pragma unroll
               for (int q = 0; q < kCS; ++q) {
                 const int s = c * kCS + q;
@@ -521,60 +579,70 @@ __global__ void __launch_bounds__(kThreadsIC) k_ic_fwd(IcArgs a, int mode, PivSc
                 const int lw = lx & 31;
                 const int i = row + lw;
                 const int par = (s & 1) * kTZ * 32;
-                const P fyp = fy_ip[lw], fzp = fz_ip[lw], zbp = zb_ip[(kTZ * 32 - par) + zr];
                 const T fyq = fy_v[lw], fzq = fz_v[lw], zbq = zb_v[(kTZ * 32 - par) + zr];
-                const P fxp = f_ip[fxi];
                 const T fxq = f_v[fxi];
-                const P xip = lx == 0 ? fxp : out_ip;
                 const T xv = lx == 0 ? fxq : out_v;
-                const P yip = ly == 0 ? fyp : up_ip;
                 const T yv = ly == 0 ? fyq : up_v;
-                const P zip = lz == 0 ? fzp : zbp;
                 const T zv = lz == 0 ? fzq : zbq;
                 const T hH = sd[i];
-                const T rhs = sg[i] + betaT * ((xv + yv) + zv);
+                const T gi = sg[i];
+                const T rhs = gi + betaT * ((xv + yv) + zv);
                 P ipj = Ops::zero();
                 T vj;
-                bool ok = true;
-                if (mode == 0) {
+                if constexpr (MODE == 0) {
+                    const P fyp = fy_ip[lw], fzp = fz_ip[lw], zbp = zb_ip[(kTZ * 32 - par) + zr];
+                    const P fxp = f_ip[fxi];
+                    const P xip = lx == 0 ? fxp : out_ip;
+                    const P yip = ly == 0 ? fyp : up_ip;
+                    const P zip = lz == 0 ? fzp : zbp;
+                    const T hL = Ops::kLo ? sl[i] : T(0);
                     const bool inm = hH >= T(0);  // H_jj, or -1 outside the mask
-                    ipj = Ops::inv_pivot(hH, Ops::kLo ? sl[i] : T(0), a.beta, pc, xip, yip, zip, ok);
+                    bool ok = true;
+                    ipj = Ops::inv_pivot(hH, hL, a.beta, pc, xip, yip, zip, ok);
                     if (!inm) ipj = Ops::zero();
-                    ok = ok || !inm;
+                    bad |= act & !(ok || !inm);
                     vj = rhs * (T)Ops::hi(ipj);
+                    // every lane stores: an inactive lane writes back what it read
+                    sd[i] = act ? (T)Ops::hi(ipj) : hH;
+                    if (Ops::kLo) sl[i] = act ? (T)Ops::lo(ipj) : hL;
+                    zb_ip[par + zw] = ipj;
                 } else {
                     vj = rhs * hH;  // stored 1/pi
                 }
-                if (act) {
-                    bad |= !ok;
-                    if (mode == 0) {
-                        sd[i] = (T)Ops::hi(ipj);
-                        if (Ops::kLo) sl[i] = (T)Ops::lo(ipj);
-                    }
-                    sg[i] = vj;
-                    out_ip = ipj;
-                    out_v = vj;
-                    zb_ip[par + zw] = ipj;
-                    zb_v[par + zw] = vj;
-                    // outgoing faces go out as they are produced
-                    if (lx == 31) {
-                        if (mode == 0) oip[FN::x + zw] = ipj;
-                        ov[FN::x + zw] = vj;
-                    }
-                    if (ly == 31) {
-                        if (mode == 0) oip[FN::y + lz * 32 + lx] = ipj;
-                        ov[FN::y + lz * 32 + lx] = vj;
-                    }
-                    if (lz == kTZ - 1) {
-                        if (mode == 0) oip[FN::z + ly * 32 + lx] = ipj;
-                        ov[FN::z + ly * 32 + lx] = vj;
-                    }
+                sg[i] = act ? vj : gi;
+                // an inactive lane's outputs are read by no active lane at the next step
+                out_ip = ipj;
+                out_v = vj;
+                zb_v[par + zw] = vj;
+                // outgoing faces go out as they are produced
+                const bool fx_out = act & (lx == 31), fy_out = act & (ly == 31), fz_out = act & (lz == kTZ - 1);
+                const int zo = FN::z + zbase + lw;
+                if constexpr (MODE == 0) {
+                    st_if(fx_out, oip + FN::x + zw, ipj);
+                    st_if(fy_out, oip + FN::y + lz * 32 + lw, ipj);
+                    st_if(fz_out, oip + zo, ipj);
+                }
+                const T vc = canon(vj);
+                st_if(fx_out, ov + FN::x + zw, vc);
+                st_if(fy_out, ov + FN::y + lz * 32 + lw, vc);
+                st_if(fz_out, ov + zo, vc);
+                {  // next step's diagonal t + 1 = s + 1 - lz: zbase(t + 1) = zbase(t) + max(0, min(t + 1, 62 - t))
+                    const int t = s - lz;
+                    zbase += max(0, min(t + 1, 62 - t));
                 }
                 bar_compute();
               }
-              if (tid == 0) st_rel_cta(&s_done, min((c + 1) * kCS, kSteps));
             }
             if (bad) set_err(a.istate, FM_ERR_NOT_PD);
+            {
+                const int sx = X > 0 ? tile - 1 : -1, sy = Y > 0 ? tile - a.ntx : -1;
+                const int sz = Z > 0 ? tile - a.ntx * a.nty : -1;
+                if (mode == 0)
+                    unset_faces<P>(sx >= 0 ? face_ip(sx) : nullptr, sy >= 0 ? face_ip(sy) : nullptr,
+                                   sz >= 0 ? face_ip(sz) : nullptr);
+                unset_faces<T>(sx >= 0 ? face_v(sx) : nullptr, sy >= 0 ? face_v(sy) : nullptr,
+                               sz >= 0 ? face_v(sz) : nullptr);
+            }
             // write back row-coalesced (warp lz writes its 32 rows, lane = x)
             const int nvalid = min(32, nx - x0);
             const int z = z0 + wz;
@@ -589,15 +657,40 @@ __global__ void __launch_bounds__(kThreadsIC) k_ic_fwd(IcArgs a, int mode, PivSc
             }
         }
         __syncthreads();
+        par ^= 1u;
     }
 }
 
-// Back substitution, tile by tile: a tile waits until its +x, +y, +z neighbours have
-// finished and published their low faces (flag = 1).  Its steps are about half as long as
-// the forward sweep's, which makes streaming's fixed hand-off latency relatively costlier:
-// measured on the 256 x 256 x 128 workload, the tile-by-tile form is faster here.
+// Deterministic sum of Q doubles over the compute warps (named barrier, the same tree as
+// block_sum over 8 warps); result valid in thread 0.
+template <int Q>
+__device__ __forceinline__ void block_sum_compute(double (&v)[Q], double* sbuf /* >= 32*Q */) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) v[q] = warp_sum(v[q]);
+    bar_compute();
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < Q; ++q) sbuf[q * 32 + wid] = v[q];
+    bar_compute();
+    if (wid == 0) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const double x = lane < kTZ ? sbuf[q * 32 + lane] : 0.0;
+            v[q] = warp_sum(x);
+        }
+    }
+    bar_compute();
+}
+
+// Back substitution, streamed like the forward sweep: the reverse sweep of a tile needs, at
+// its local hyperplane s, the +x / +y neighbours' low-face values those tiles produce 31
+// steps earlier in their own reverse sweeps, and the +z neighbour's 7 (kTZ - 1) steps
+// earlier.  Every low-face voxel (lx = 0, ly = 0, lz = 0) goes to the face buffer as it is
+// computed (the z face by diagonals, as in the forward sweep), and a fetch warp polls the
+// entries each chunk of kCS reverse steps needs, with the same unset-pattern hand-off.
 template <typename T>
-__global__ void __launch_bounds__(32 * kTZ) k_ic_bwd(IcArgs a) {
+__global__ void __launch_bounds__(kThreadsIC) k_ic_bwd(IcArgs a) {
     using P = typename PivOps<T>::P;
     extern __shared__ __align__(16) unsigned char smem[];
     T* sv = (T*)smem;                 // [TZ][32][32]: v, then p
@@ -605,6 +698,7 @@ __global__ void __launch_bounds__(32 * kTZ) k_ic_bwd(IcArgs a) {
     T* f_p = sip + kTZ * 1024;        // incoming faces (the successors' -x, -y, -z faces)
     T* zb = f_p + FN::n;              // [2][TZ][32]
     __shared__ int s_tile;
+    __shared__ __align__(8) unsigned long long s_mbar[kNch];
     __shared__ bool s_last;
     __shared__ double sbuf[2 * 32];
 
@@ -624,6 +718,11 @@ __global__ void __launch_bounds__(32 * kTZ) k_ic_bwd(IcArgs a) {
         return (T*)(faceb + (size_t)t * face_bytes_per_tile<T>() + (size_t)FN::n * (sizeof(P) + sizeof(T)));
     };
 
+    if (tid == 0) {
+        s_last = false;
+        for (int c = 0; c < kNch; ++c) mbar_init(&s_mbar[c], 1);
+    }
+    unsigned par = 0;  // phase parity of this CTA's current tile
     for (;;) {
         if (tid == 0) {
             const int t = atomicAdd(a.ticket, 1);
@@ -635,100 +734,170 @@ __global__ void __launch_bounds__(32 * kTZ) k_ic_bwd(IcArgs a) {
         const int X = tile % a.ntx, Y = (tile / a.ntx) % a.nty, Z = tile / (a.ntx * a.nty);
         const int x0 = X * 32, y0 = Y * 32, z0 = Z * kTZ;
 
-        stage_row<T>(sv, vin, tid, x0, y0, z0, geo, T(0));
-        stage_row<T>(sip, ipb, tid, x0, y0, z0, geo, T(0));
-        if (tid == 0) {
+        if (wz == kTZ) {
+            // fetch warp: the +x, +y, +z neighbours' outgoing low faces, chunk by chunk
+            const int sx = X + 1 < a.ntx ? tile + 1 : -1, sy = Y + 1 < a.nty ? tile + a.ntx : -1;
+            const int sz = Z + 1 < a.ntz ? tile + a.ntx * a.nty : -1;
             bool ok = true;
-            if (X + 1 < a.ntx) ok = spin_until(a.flags + tile + 1, 1, a.spin_limit) && ok;
-            if (Y + 1 < a.nty) ok = spin_until(a.flags + tile + a.ntx, 1, a.spin_limit) && ok;
-            if (Z + 1 < a.ntz) ok = spin_until(a.flags + tile + a.ntx * a.nty, 1, a.spin_limit) && ok;
-            if (!ok) set_err(a.istate, FM_ERR_TIMEOUT);
-        }
-        __syncthreads();
-        // incoming faces: the +x / +y / +z neighbours' outgoing low faces (lx = 0, ly = 0, lz = 0)
-        for (int i = tid; i < FN::n; i += 32 * kTZ) {
-            T q = 0;
-            int src = -1;
-            if (i < FN::y) { if (X + 1 < a.ntx) src = tile + 1; }
-            else if (i < FN::z) { if (Y + 1 < a.nty) src = tile + a.ntx; }
-            else if (Z + 1 < a.ntz) src = tile + a.ntx * a.nty;
-            if (src >= 0) q = ld_cg(face_p(src) + i);
-            f_p[i] = q;
-        }
-        cp_wait_all();
-        __syncthreads();
-
-        // sweep in reverse, branch-free as in the forward kernel
-        const int ly = lane, lz = wz, l0 = ly + lz;
-        const int row = (lz * 32 + ly) * 32;
-        const T fx = f_p[FN::x + lz * 32 + ly];
-        const T* fy = f_p + FN::y + lz * 32;
-        const T* fz = f_p + FN::z + ly * 32;
-        const int zr = (lz < kTZ - 1 ? lz + 1 : lz) * 32 + ly, zw = lz * 32 + ly;
-        T out = 0;
-#pragma unroll kBwdUnroll
-        for (int s = kSteps - 1; s >= 0; --s) {
-            const T dn = __shfl_down_sync(0xffffffffu, out, 1);
-            const int lx = s - l0;
-            const bool act = (unsigned)lx < 32u;
-            const int lw = lx & 31;
-            const int i = row + lw;
-            const int par = (s & 1) * kTZ * 32;
-            const T fyv = fy[lw], fzv = fz[lw], zbv = zb[(kTZ * 32 - par) + zr];
-            const T px = lx == 31 ? fx : out;
-            const T py = ly == 31 ? fyv : dn;
-            const T pz = lz == kTZ - 1 ? fzv : zbv;
-            const T pj = sv[i] + beta * sip[i] * ((px + py) + pz);
-            if (act) {
-                sv[i] = pj;
-                out = pj;
-                zb[par + zw] = pj;
+            for (int c = 0; c < kNch; ++c) {
+                T zv[kCS], qv[kCS];
+                int zi[kCS], zg[kCS], qi[kCS], qsrc[kCS];
+                unsigned want = 0;
+#pragma unroll
+                for (int q = 0; q < kCS; ++q) {
+                    // reverse step c * kCS + q is local hyperplane s; the +z face entry (lx, ly) is
+                    // used at s = lx + ly + kTZ - 1, the +x / +y entries at s = 31 + ly + lz / lx + lz
+                    const int s = kSteps - 1 - (c * kCS + q);
+                    int which = 0;
+                    const bool in = s >= 0;
+                    zi[q] = in ? z_entry(s - (kTZ - 1), lane) : -1;
+                    zg[q] = FN::z + zdiag(min(max(s - (kTZ - 1), 0), 62)) + lane;
+                    qi[q] = in ? xy_entry(s - 31, lane, which) : -1;
+                    qsrc[q] = which ? sy : sx;
+                    zv[q] = T(0);
+                    qv[q] = T(0);
+                    if (zi[q] >= 0 && sz >= 0) want |= 1u << q;
+                    if (qi[q] >= 0 && qsrc[q] >= 0) want |= 1u << (kCS + q);
+                }
+                unsigned todo = ok ? want : 0u;
+                long long tries = 0;
+                while (__any_sync(0xffffffffu, todo != 0u)) {
+#pragma unroll
+                    for (int q = 0; q < kCS; ++q) {
+                        if (todo & (1u << q)) zv[q] = ld_rlx(face_p(sz) + zg[q]);
+                        if (todo & (1u << (kCS + q))) qv[q] = ld_rlx(face_p(qsrc[q]) + qi[q]);
+                    }
+#pragma unroll
+                    for (int q = 0; q < kCS; ++q) {
+                        if ((todo & (1u << q)) && !unset(zv[q])) todo &= ~(1u << q);
+                        if ((todo & (1u << (kCS + q))) && !unset(qv[q])) todo &= ~(1u << (kCS + q));
+                    }
+                    if (++tries > a.spin_limit && __any_sync(0xffffffffu, todo != 0u)) {
+                        ok = false;
+#pragma unroll
+                        for (int q = 0; q < kCS; ++q) {
+                            if (todo & (1u << q)) zv[q] = T(0);
+                            if (todo & (1u << (kCS + q))) qv[q] = T(0);
+                        }
+                        want &= ~todo;
+                        todo = 0u;
+                    } else if (todo != 0u) {
+                        __nanosleep(20);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kCS; ++q) {
+                    if (zi[q] >= 0) f_p[zi[q]] = zv[q];
+                    if (qi[q] >= 0) f_p[qi[q]] = qv[q];
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&s_mbar[c]);
             }
-            __syncthreads();
-        }
-        {
+            if (!ok) set_err(a.istate, FM_ERR_TIMEOUT);  // the host resets the faces with the error
+        } else {
+            stage_row<T>(sv, vin, tid, x0, y0, z0, geo, T(0));
+            stage_row<T>(sip, ipb, tid, x0, y0, z0, geo, T(0));
+            cp_wait_all();
+            bar_compute();
+
+            // sweep in reverse, branch-free as in the forward kernel; the low-face entries a chunk
+            // produces go out after the chunk, read back from shared memory by every warp
+            const int ly = lane, lz = wz, l0 = ly + lz;
+            const int row = (lz * 32 + ly) * 32;
+            const int fxi = FN::x + lz * 32 + ly;
+            const T* fy = f_p + FN::y + lz * 32;
+            const T* fz = f_p + FN::z + ly * 32;
+            const int zr = (lz < kTZ - 1 ? lz + 1 : lz) * 32 + ly, zw = lz * 32 + ly;
             T* op = face_p(tile);
-            for (int i = tid; i < FN::n; i += 32 * kTZ) op[i] = sv[out_face_vox(i, false)];
-        }
-        __syncthreads();
-        if (tid == 0) st_release(a.flags + tile, 1);
+            T out = 0;
+            for (int c = 0; c < kNch; ++c) {
+                wait_chunk(&s_mbar[c], par, a.spin_limit, a.istate);
+                const T fxv = f_p[fxi];  // used at s = 31 + l0, in the chunk whose fetch brought it
+#pragma unroll
+                for (int q = 0; q < kCS; ++q) {
+                    const int s = kSteps - 1 - (c * kCS + q);
+                    if (kSteps % kCS != 0 && s < 0) break;
+                    const T dn = __shfl_down_sync(0xffffffffu, out, 1);
+                    const int lx = s - l0;
+                    const bool act = (unsigned)lx < 32u;
+                    const int lw = lx & 31;
+                    const int i = row + lw;
+                    const int par = (s & 1) * kTZ * 32;
+                    const T fyv = fy[lw], fzv = fz[lw], zbv = zb[(kTZ * 32 - par) + zr];
+                    const T px = lx == 31 ? fxv : out;
+                    const T py = ly == 31 ? fyv : dn;
+                    const T pz = lz == kTZ - 1 ? fzv : zbv;
+                    const T vi = sv[i];
+                    const T pj = vi + beta * sip[i] * ((px + py) + pz);
+                    // every lane stores (an inactive lane writes back what it read); an inactive
+                    // lane's outputs are read by no active lane at the next step
+                    sv[i] = act ? pj : vi;
+                    out = pj;
+                    zb[par + zw] = pj;
+                    bar_compute();
+                }
+                // low faces produced at local hyperplanes s0..s1 of this chunk
+                const int s1 = kSteps - 1 - c * kCS, s0 = max(s1 - kCS + 1, 0);
+                // x face (ly, lz): this thread's lx = 0 voxel, produced at s = l0
+                st_if(l0 >= s0 && l0 <= s1, op + FN::x + zw, canon(sv[row]));
+                {  // y face (lx, lz): lane 0 of warp lz produced one per step; lane q stores step s1 - q
+                    const int sq = s1 - lane, lxy = sq - lz;
+                    const bool ok = lane < kCS && sq >= s0 && (unsigned)lxy < 32u;
+                    st_if(ok, op + FN::y + lz * 32 + (lxy & 31), canon(sv[lz * 1024 + (lxy & 31)]));
+                }
+                if (wz < kCS) {  // z face diagonal s1 - wz: entry (lx, ly) of the lz = 0 plane
+                    const int sq = s1 - wz, lxz = sq - ly;
+                    const bool ok = sq >= s0 && (unsigned)lxz < 32u;
+                    const int zo = FN::z + zdiag(min(max(sq, 0), 62)) - max(0, sq - 31) + (lxz & 31);
+                    st_if(ok, op + zo, canon(sv[ly * 32 + (lxz & 31)]));
+                }
+            }
 
-        // write back, then the dot products (off the wavefront's critical path)
-        const int nvalid = min(32, nx - x0);
-        const int z = z0 + wz;
-        const bool zin = z < nz && lane < nvalid;
-        double acc[2] = {0.0, 0.0};
-        if (zin) {
-            for (int ly2 = 0; ly2 < 32 && y0 + ly2 < ny; ++ly2) {
-                const long long j = (long long)z * nxy + (long long)(y0 + ly2) * nx + x0 + lane;
-                const T pj = sv[(wz * 32 + ly2) * 32 + lane];
-                p[j] = pj;
-                if (gd) acc[0] += (double)(gd[j] * pj);
-                if (gpd) acc[1] += (double)(gpd[j] * pj);
+            {
+                const int sx = X + 1 < a.ntx ? tile + 1 : -1, sy = Y + 1 < a.nty ? tile + a.ntx : -1;
+                const int sz = Z + 1 < a.ntz ? tile + a.ntx * a.nty : -1;
+                unset_faces<T>(sx >= 0 ? face_p(sx) : nullptr, sy >= 0 ? face_p(sy) : nullptr,
+                               sz >= 0 ? face_p(sz) : nullptr);
             }
-        }
-        if (a.tile_part) {
-            block_sum<2>(acc, sbuf);
-            if (tid == 0) {
-                a.tile_part[tile] = acc[0];
-                a.tile_part[a.ntiles + tile] = acc[1];
-                __threadfence();
-                const int prev = atomicAdd(a.done, 1);
-                s_last = (prev == a.ntiles - 1);
-                if (s_last) __threadfence();
+            // write back, then the dot products (off the wavefront's critical path)
+            const int nvalid = min(32, nx - x0);
+            const int z = z0 + wz;
+            const bool zin = z < nz && lane < nvalid;
+            double acc[2] = {0.0, 0.0};
+            if (zin) {
+                for (int ly2 = 0; ly2 < 32 && y0 + ly2 < ny; ++ly2) {
+                    const long long j = (long long)z * nxy + (long long)(y0 + ly2) * nx + x0 + lane;
+                    const T pj = sv[(wz * 32 + ly2) * 32 + lane];
+                    p[j] = pj;
+                    if (gd) acc[0] += (double)(gd[j] * pj);
+                    if (gpd) acc[1] += (double)(gpd[j] * pj);
+                }
             }
-            __syncthreads();
-            if (s_last) {
-                double tot[2];
-                sum_partials<2>(a.tile_part, a.ntiles, tot, sbuf);
+            if (a.tile_part) {
+                block_sum_compute(acc, sbuf);
                 if (tid == 0) {
-                    a.scal[S_GP] = tot[0];
-                    a.scal[S_GPREVP] = tot[1];
-                    if (!isfinite(tot[0]) || !isfinite(tot[1])) set_err(a.istate, FM_ERR_NONFINITE);
+                    a.tile_part[tile] = acc[0];
+                    a.tile_part[a.ntiles + tile] = acc[1];
+                    __threadfence();
+                    const int prev = atomicAdd(a.done, 1);
+                    s_last = (prev == a.ntiles - 1);
+                    if (s_last) __threadfence();
                 }
             }
         }
         __syncthreads();
+        if (a.tile_part && s_last) {
+            double tot[2];
+            sum_partials<2>(a.tile_part, a.ntiles, tot, sbuf);
+            if (tid == 0) {
+                a.scal[S_GP] = tot[0];
+                a.scal[S_GPREVP] = tot[1];
+                if (!isfinite(tot[0]) || !isfinite(tot[1])) set_err(a.istate, FM_ERR_NONFINITE);
+            }
+            __syncthreads();
+            if (tid == 0) s_last = false;
+        }
+        par ^= 1u;
     }
 }
 
@@ -739,8 +908,10 @@ template <typename T>
 static cudaError_t prep() {
     static bool done = false;  // attributes are per function, set once per process
     if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_ic_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_ic_fwd<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)FwdSmem<T>::bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_ic_fwd<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FwdSmem<T>::bytes);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_ic_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)BwdSmem<T>::bytes);
@@ -753,8 +924,8 @@ int ic_max_blocks_per_sm(bool bwd) {
     if (prep<T>() != cudaSuccess) return 0;
     int n = 0;
     const cudaError_t e =
-        bwd ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ic_bwd<T>, 32 * kTZ, BwdSmem<T>::bytes)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ic_fwd<T>, kThreadsIC, FwdSmem<T>::bytes);
+        bwd ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ic_bwd<T>, kThreadsIC, BwdSmem<T>::bytes)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ic_fwd<T, 0>, kThreadsIC, FwdSmem<T>::bytes);
     return e == cudaSuccess ? n : 0;
 }
 
@@ -772,7 +943,10 @@ template <typename T>
 cudaError_t launch_ic_fwd(const IcArgs& a, int grid, cudaStream_t s) {
     cudaError_t e = prep<T>();
     if (e != cudaSuccess) return e;
-    k_ic_fwd<T><<<grid, kThreadsIC, FwdSmem<T>::bytes, s>>>(a, a.d ? 0 : 1, piv_scal(a.beta));
+    if (a.d)
+        k_ic_fwd<T, 0><<<grid, kThreadsIC, FwdSmem<T>::bytes, s>>>(a, piv_scal(a.beta));
+    else
+        k_ic_fwd<T, 1><<<grid, kThreadsIC, FwdSmem<T>::bytes, s>>>(a, piv_scal(a.beta));
     return cudaGetLastError();
 }
 
@@ -780,7 +954,7 @@ template <typename T>
 cudaError_t launch_ic_bwd(const IcArgs& a, int grid, cudaStream_t s) {
     cudaError_t e = prep<T>();
     if (e != cudaSuccess) return e;
-    k_ic_bwd<T><<<grid, 32 * kTZ, BwdSmem<T>::bytes, s>>>(a);
+    k_ic_bwd<T><<<grid, kThreadsIC, BwdSmem<T>::bytes, s>>>(a);
     return cudaGetLastError();
 }
 
