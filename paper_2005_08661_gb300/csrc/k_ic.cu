@@ -213,7 +213,12 @@ constexpr int kSteps = 62 + kTZ;    // local hyperplanes lx + ly + lz of a tile
 constexpr int kCS = FM_IC_CS;       // steps per published chunk
 constexpr int kNch = (kSteps + kCS - 1) / kCS;
 constexpr int kCompute = 32 * kTZ;  // compute threads
-constexpr int kThreadsIC = kCompute + 32;  // + one warp that fetches incoming faces
+// Warps that fetch incoming faces, taking alternate chunks, so that the polls for consecutive
+// chunks are in flight together (one poll round trip is longer than a chunk of the back
+// substitution's steps)
+constexpr int kFetchF = 2, kFetchB = 2;
+constexpr int kThreadsIC = kCompute + 32 * kFetchF;
+constexpr int kThreadsB = kCompute + 32 * kFetchB;
 
 // Face layout per tile (counts of values): x face [TZ][32] (lz, ly), y face [TZ][32]
 // (lz, lx), z face [32][32].  In shared memory the z face is (ly, lx); in the forward
@@ -348,20 +353,22 @@ __device__ __forceinline__ int xy_entry(int s, int lane, int& which) {
 }
 
 // Predicated relaxed stores of outgoing face entries: written by the one lane that produces
-// the entry at a step, without a divergent branch in the step body.  The caller keeps the
+// the entry at a step, without a divergent branch in the step body.  No compiler memory
+// clobber: the stored value is an operand, nothing in the kernel reads the entry back, and
+// volatile asm keeps its order relative to the barriers.  The caller keeps the
 // value clear of the unset pattern: an inverse pivot is finite by construction (0 where the
 // pivot is not positive or outside the mask), and v passes through canon.
 __device__ __forceinline__ void st_if(bool p, double* a, double v) {
     asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q st.relaxed.gpu.global.f64 [%1], %2;\n\t}"
-                 ::"r"((int)p), "l"(a), "d"(v) : "memory");
+                 ::"r"((int)p), "l"(a), "d"(v));
 }
 __device__ __forceinline__ void st_if(bool p, float* a, float v) {
     asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q st.relaxed.gpu.global.f32 [%1], %2;\n\t}"
-                 ::"r"((int)p), "l"(a), "f"(v) : "memory");
+                 ::"r"((int)p), "l"(a), "f"(v));
 }
 __device__ __forceinline__ void st_if(bool p, PF* a, PF v) {
     asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q st.relaxed.gpu.global.v2.f32 [%1], {%2, %3};\n\t}"
-                 ::"r"((int)p), "l"(a), "f"(v.a), "f"(v.b) : "memory");
+                 ::"r"((int)p), "l"(a), "f"(v.a), "f"(v.b));
 }
 
 // After a tile's sweep every entry of its incoming faces has been read (the compute warps
@@ -453,12 +460,12 @@ __global__ void __launch_bounds__(kThreadsIC) k_ic_fwd(IcArgs a, PivScal pc) {
         const int X = tile % a.ntx, Y = (tile / a.ntx) % a.nty, Z = tile / (a.ntx * a.nty);
         const int x0 = X * 32, y0 = Y * 32, z0 = Z * kTZ;
 
-        if (wz == kTZ) {
-            // fetch warp: the -x, -y, -z neighbours' outgoing +x, +y, +z faces, chunk by chunk
+        if (wz >= kTZ) {
+            // fetch warps: the -x, -y, -z neighbours' outgoing +x, +y, +z faces, alternate chunks each
             const int sx = X > 0 ? tile - 1 : -1, sy = Y > 0 ? tile - a.ntx : -1;
             const int sz = Z > 0 ? tile - a.ntx * a.nty : -1;
             bool ok = true;
-            for (int c = 0; c < kNch; ++c) {
+            for (int c = wz - kTZ; c < kNch; c += kFetchF) {
                 P zp[kCS], qp[kCS];
                 T zv[kCS], qv[kCS];
                 int zi[kCS], zg[kCS], qi[kCS], qsrc[kCS];
@@ -690,7 +697,7 @@ __device__ __forceinline__ void block_sum_compute(double (&v)[Q], double* sbuf /
 // computed (the z face by diagonals, as in the forward sweep), and a fetch warp polls the
 // entries each chunk of kCS reverse steps needs, with the same unset-pattern hand-off.
 template <typename T>
-__global__ void __launch_bounds__(kThreadsIC) k_ic_bwd(IcArgs a) {
+__global__ void __launch_bounds__(kThreadsB, 2) k_ic_bwd(IcArgs a) {
     using P = typename PivOps<T>::P;
     extern __shared__ __align__(16) unsigned char smem[];
     T* sv = (T*)smem;                 // [TZ][32][32]: v, then p
@@ -734,12 +741,12 @@ __global__ void __launch_bounds__(kThreadsIC) k_ic_bwd(IcArgs a) {
         const int X = tile % a.ntx, Y = (tile / a.ntx) % a.nty, Z = tile / (a.ntx * a.nty);
         const int x0 = X * 32, y0 = Y * 32, z0 = Z * kTZ;
 
-        if (wz == kTZ) {
-            // fetch warp: the +x, +y, +z neighbours' outgoing low faces, chunk by chunk
+        if (wz >= kTZ) {
+            // fetch warps: the +x, +y, +z neighbours' outgoing low faces, alternate chunks each
             const int sx = X + 1 < a.ntx ? tile + 1 : -1, sy = Y + 1 < a.nty ? tile + a.ntx : -1;
             const int sz = Z + 1 < a.ntz ? tile + a.ntx * a.nty : -1;
             bool ok = true;
-            for (int c = 0; c < kNch; ++c) {
+            for (int c = wz - kTZ; c < kNch; c += kFetchB) {
                 T zv[kCS], qv[kCS];
                 int zi[kCS], zg[kCS], qi[kCS], qsrc[kCS];
                 unsigned want = 0;
@@ -836,21 +843,18 @@ __global__ void __launch_bounds__(kThreadsIC) k_ic_bwd(IcArgs a) {
                     zb[par + zw] = pj;
                     bar_compute();
                 }
-                // low faces produced at local hyperplanes s0..s1 of this chunk
+                // low faces produced at local hyperplanes s0..s1 of this chunk: x face (ly, lz) is
+                // this thread's lx = 0 voxel, produced at s = l0; y face (lx, lz) was produced by
+                // lane 0 of warp lz, one per step, and lane q stores step s1 - q; z face diagonal
+                // s1 - wz (warps 0..kCS-1) holds entries (lx, ly) of the lz = 0 plane
                 const int s1 = kSteps - 1 - c * kCS, s0 = max(s1 - kCS + 1, 0);
-                // x face (ly, lz): this thread's lx = 0 voxel, produced at s = l0
-                st_if(l0 >= s0 && l0 <= s1, op + FN::x + zw, canon(sv[row]));
-                {  // y face (lx, lz): lane 0 of warp lz produced one per step; lane q stores step s1 - q
-                    const int sq = s1 - lane, lxy = sq - lz;
-                    const bool ok = lane < kCS && sq >= s0 && (unsigned)lxy < 32u;
-                    st_if(ok, op + FN::y + lz * 32 + (lxy & 31), canon(sv[lz * 1024 + (lxy & 31)]));
-                }
-                if (wz < kCS) {  // z face diagonal s1 - wz: entry (lx, ly) of the lz = 0 plane
-                    const int sq = s1 - wz, lxz = sq - ly;
-                    const bool ok = sq >= s0 && (unsigned)lxz < 32u;
-                    const int zo = FN::z + zdiag(min(max(sq, 0), 62)) - max(0, sq - 31) + (lxz & 31);
-                    st_if(ok, op + zo, canon(sv[ly * 32 + (lxz & 31)]));
-                }
+                const int sy_ = s1 - lane, lxy = sy_ - lz;
+                const int sz_ = s1 - wz, lxz = sz_ - ly;
+                const T vx = sv[row], vy = sv[lz * 1024 + (lxy & 31)], vz = sv[ly * 32 + (lxz & 31)];
+                const int zo = FN::z + zdiag(min(max(sz_, 0), 62)) - max(0, sz_ - 31) + (lxz & 31);
+                st_if(l0 >= s0 && l0 <= s1, op + FN::x + zw, canon(vx));
+                st_if(lane < kCS && sy_ >= s0 && (unsigned)lxy < 32u, op + FN::y + lz * 32 + (lxy & 31), canon(vy));
+                st_if(wz < kCS && sz_ >= s0 && (unsigned)lxz < 32u, op + zo, canon(vz));
             }
 
             {
@@ -924,7 +928,7 @@ int ic_max_blocks_per_sm(bool bwd) {
     if (prep<T>() != cudaSuccess) return 0;
     int n = 0;
     const cudaError_t e =
-        bwd ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ic_bwd<T>, kThreadsIC, BwdSmem<T>::bytes)
+        bwd ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ic_bwd<T>, kThreadsB, BwdSmem<T>::bytes)
             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ic_fwd<T, 0>, kThreadsIC, FwdSmem<T>::bytes);
     return e == cudaSuccess ? n : 0;
 }
@@ -954,7 +958,7 @@ template <typename T>
 cudaError_t launch_ic_bwd(const IcArgs& a, int grid, cudaStream_t s) {
     cudaError_t e = prep<T>();
     if (e != cudaSuccess) return e;
-    k_ic_bwd<T><<<grid, kThreadsIC, BwdSmem<T>::bytes, s>>>(a);
+    k_ic_bwd<T><<<grid, kThreadsB, BwdSmem<T>::bytes, s>>>(a);
     return cudaGetLastError();
 }
 
