@@ -41,10 +41,11 @@ if ROOT not in sys.path:
 # sources have changed since is reported as null.
 KERNEL_SOURCES = {"ls": ("k_data.cu",), "grad": ("k_data.cu",), "ic_fwd": ("k_ic.cu",), "ic_bwd": ("k_ic.cu",)}
 NCU_TRAFFIC_BYTES = {  # (bytes per launch, kernel_src_hash of the sources measured)
-    ("full", "ls"): (2006743552 + 10684800, "c45a72b6fcfbd267"),
-    ("full", "grad"): (504713472 + 21894826, "c45a72b6fcfbd267"),
-    ("full", "ic_fwd"): (78387584 + 34291456, "6b17fa9865553fe0"),
-    ("full", "ic_bwd"): (134262016 + 16783360, "6b17fa9865553fe0"),
+    ("full", "ls"): (2006896384 + 11910400, "c3bf7a7f74f7c32b"),
+    ("full", "grad"): (504659968 + 24824832, "c3bf7a7f74f7c32b"),
+    # the IC sweeps on the same 256x256x128 grid with one coil (their work does not depend on it)
+    ("full", "ic_fwd"): (82128384 + 37163264, "89cc6034cb5e4b8d"),
+    ("full", "ic_bwd"): (135962624 + 16716032, "89cc6034cb5e4b8d"),
 }
 
 
@@ -72,6 +73,9 @@ WORKLOADS = {
                        "50 NCG iterations, N_ls=5, IC(0)", niter=50),
     "medium": dict(desc="128x128x64 voxels, 8 coils, 3 echoes (0/2/10 ms), SNR 20 dB, beta=2^-3, "
                         "100 NCG iterations, N_ls=5, IC(0)", niter=100),
+    "full1": dict(desc="256x256x128 voxels, 1 coil, 3 echoes (0/2/10 ms), SNR 15 dB, beta=2^-3, "
+                       "100 NCG iterations, N_ls=5, IC(0) (the full grid with one coil: the IC sweeps' "
+                       "profiling case)", niter=100),
     "batch": dict(desc="32 independent volumes from 64x64x16 to 192x192x96, 1 or 8 coils, 3 echoes "
                        "(0/2/10 ms), SNR 10-25 dB, beta=2^-3, 50 NCG iterations each, N_ls=5, IC(0), one "
                        "CUDA graph launch per two iterations of all volumes", niter=50),
@@ -93,7 +97,9 @@ CPU_SAMPLE_1CORE = (32, 32, 16)  # the one-thread figure, on a smaller centred s
 
 
 def make_workload(name, seed_offset=0):
-    from synth import diff_config, full_config, small_config, wf_config
+    from synth import diff_config, full1_config, full_config, small_config, wf_config
+    if name == "full1":
+        return full1_config(seed=1002 + seed_offset)
     if name == "wf":
         return wf_config(seed=1003 + seed_offset)
     if name == "full":

@@ -8,8 +8,8 @@ solver), so both the FP64 oracle and the CUDA path may take their inputs from it
 """
 from .volumes import (Volume, make_volume, ellipsoid_mask, small_config, full_config,
                       diff_config, batch_configs, TE_MS, make_wf_volume, wf_config, fat_spectrum,
-                      WF_TE_MS, phantom_config, full8_small_config)
+                      WF_TE_MS, phantom_config, full8_small_config, full1_config)
 
 __all__ = ["Volume", "make_volume", "ellipsoid_mask", "small_config", "full_config",
            "diff_config", "batch_configs", "TE_MS", "make_wf_volume", "wf_config", "fat_spectrum",
-           "WF_TE_MS", "phantom_config", "full8_small_config"]
+           "WF_TE_MS", "phantom_config", "full8_small_config", "full1_config"]

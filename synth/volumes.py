@@ -300,6 +300,14 @@ def full_config(seed=1002, **kw):
                        nblobs=6, step_hz=40.0, name="full_256x256x128_c8", **kw)
 
 
+def full1_config(seed=1002, **kw):
+    """256x256x128, one coil: the full workload's grid and field-map recipe with a single coil
+    (the IC sweeps' work does not depend on the coil count; a profiling case that holds
+    well under a GB on the device)."""
+    return make_volume(256, 256, 128, ncoil=1, snr_db=15.0, seed=seed, fmax_hz=250.0,
+                       nblobs=6, step_hz=40.0, name="full_256x256x128_c1", **kw)
+
+
 def full8_small_config(seed=1007, **kw):
     """64x64x32, 8 coils: the full workload's recipe (echoes 0/2/10 ms, +-250 Hz mixture +
     40 Hz step, SNR 15 dB) at a size whose 100-iteration oracle solve takes minutes."""
