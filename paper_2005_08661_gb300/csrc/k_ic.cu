@@ -205,13 +205,19 @@ __device__ __forceinline__ void stage_row_u8(uint8_t* s, const uint8_t* g, int r
 
 // ------------------------------------------------------------------ tile geometry
 
-#ifndef FM_IC_CS
-#define FM_IC_CS 7
+#ifndef FM_IC_CSF
+#define FM_IC_CSF 4
+#endif
+#ifndef FM_IC_CSB
+#define FM_IC_CSB 8
 #endif
 constexpr int kTZ = 8;              // tile = 32 x 32 x 8 voxels, 8 compute warps
 constexpr int kSteps = 62 + kTZ;    // local hyperplanes lx + ly + lz of a tile
-constexpr int kCS = FM_IC_CS;       // steps per published chunk
-constexpr int kNch = (kSteps + kCS - 1) / kCS;
+// Steps per chunk (the unit of the face hand-off): forward 4, back substitution 8.  With 8
+// the back substitution's per-chunk face flush lines up with what its successors' chunks
+// need (x / y faces 31 steps later, z faces 7); at most kTZ, one z diagonal per warp.
+constexpr int kCSF = FM_IC_CSF, kCSB = FM_IC_CSB;
+static_assert(kCSB <= kTZ, "the back substitution's face flush takes one z diagonal per warp");
 constexpr int kCompute = 32 * kTZ;  // compute threads
 // Warps that fetch incoming faces, taking alternate chunks, so that the polls for consecutive
 // chunks are in flight together (one poll round trip is longer than a chunk of the back
@@ -283,7 +289,7 @@ __device__ __forceinline__ int out_face_vox(int i, bool fwd) {
 // back after reading it, so the buffer is ready for the next launch; the host fills it with
 // the pattern when the context is created and after a device error.
 //
-// One extra warp per CTA fetches the faces: chunk by chunk (kCS steps), it polls the
+// Extra warps per CTA fetch the faces: chunk by chunk (a few steps each), they poll the
 // entries the chunk needs (bounded, with a short sleep), copies them into shared memory and
 // signals the compute warps through a shared-memory counter.  The compute warps synchronise
 // among themselves with a named barrier and never poll global memory.
@@ -430,6 +436,7 @@ __global__ void __launch_bounds__(kThreadsIC) k_ic_fwd(IcArgs a, PivScal pc) {
     T* zb_v = f_v + FN::n;
     uint8_t* snb = (uint8_t*)(zb_v + 2 * kTZ * 32);  // [TZ][32][32]
     __shared__ int s_tile;
+    constexpr int kCS = kCSF, kNch = (kSteps + kCS - 1) / kCS;
     __shared__ __align__(8) unsigned long long s_mbar[kNch];
 
     const Geo geo = a.geo;
@@ -705,6 +712,7 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_ic_bwd(IcArgs a) {
     T* f_p = sip + kTZ * 1024;        // incoming faces (the successors' -x, -y, -z faces)
     T* zb = f_p + FN::n;              // [2][TZ][32]
     __shared__ int s_tile;
+    constexpr int kCS = kCSB, kNch = (kSteps + kCS - 1) / kCS;
     __shared__ __align__(8) unsigned long long s_mbar[kNch];
     __shared__ bool s_last;
     __shared__ double sbuf[2 * 32];
