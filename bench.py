@@ -44,8 +44,8 @@ NCU_TRAFFIC_BYTES = {  # (bytes per launch, kernel_src_hash of the sources measu
     ("full", "ls"): (2006896384 + 11910400, "c3bf7a7f74f7c32b"),
     ("full", "grad"): (504659968 + 24824832, "c3bf7a7f74f7c32b"),
     # the IC sweeps on the same 256x256x128 grid with one coil (their work does not depend on it)
-    ("full", "ic_fwd"): (82128384 + 37163264, "89cc6034cb5e4b8d"),
-    ("full", "ic_bwd"): (135962624 + 16716032, "89cc6034cb5e4b8d"),
+    ("full", "ic_fwd"): (79717120 + 37039360, "b6d43e25cc88cb40"),
+    ("full", "ic_bwd"): (135755520 + 19821312, "b6d43e25cc88cb40"),
 }
 
 
