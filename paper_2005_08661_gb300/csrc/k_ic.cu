@@ -871,18 +871,33 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_ic_bwd(IcArgs a) {
                 unset_faces<T>(sx >= 0 ? face_p(sx) : nullptr, sy >= 0 ? face_p(sy) : nullptr,
                                sz >= 0 ? face_p(sz) : nullptr);
             }
-            // write back, then the dot products (off the wavefront's critical path)
+            // write back, then the dot products (off the wavefront's critical path).  The loads of
+            // g and g_prev go out kWb rows at a time, so that a tile pays a few memory round
+            // trips here, not one per row (the CTA claims its next tile only after this)
             const int nvalid = min(32, nx - x0);
             const int z = z0 + wz;
             const bool zin = z < nz && lane < nvalid;
+            const int nrow = min(32, ny - y0);
             double acc[2] = {0.0, 0.0};
             if (zin) {
-                for (int ly2 = 0; ly2 < 32 && y0 + ly2 < ny; ++ly2) {
-                    const long long j = (long long)z * nxy + (long long)(y0 + ly2) * nx + x0 + lane;
-                    const T pj = sv[(wz * 32 + ly2) * 32 + lane];
-                    p[j] = pj;
-                    if (gd) acc[0] += (double)(gd[j] * pj);
-                    if (gpd) acc[1] += (double)(gpd[j] * pj);
+                constexpr int kWb = 16;
+                for (int r0 = 0; r0 < 32; r0 += kWb) {
+                    T pv[kWb], gv[kWb], gpv[kWb];
+#pragma unroll
+                    for (int k = 0; k < kWb; ++k) {
+                        const int ly2 = r0 + k;
+                        const bool in = ly2 < nrow;
+                        const long long j = (long long)z * nxy + (long long)(y0 + (in ? ly2 : 0)) * nx + x0 + lane;
+                        pv[k] = in ? sv[(wz * 32 + ly2) * 32 + lane] : T(0);
+                        gv[k] = (gd && in) ? gd[j] : T(0);
+                        gpv[k] = (gpd && in) ? gpd[j] : T(0);
+                        if (in) p[j] = pv[k];
+                    }
+#pragma unroll
+                    for (int k = 0; k < kWb; ++k) {
+                        acc[0] += (double)(gv[k] * pv[k]);
+                        acc[1] += (double)(gpv[k] * pv[k]);
+                    }
                 }
             }
             if (a.tile_part) {
