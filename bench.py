@@ -41,11 +41,11 @@ if ROOT not in sys.path:
 # sources have changed since is reported as null.
 KERNEL_SOURCES = {"ls": ("k_data.cu",), "grad": ("k_data.cu",), "ic_fwd": ("k_ic.cu",), "ic_bwd": ("k_ic.cu",)}
 NCU_TRAFFIC_BYTES = {  # (bytes per launch, kernel_src_hash of the sources measured)
-    ("full", "ls"): (2006896384 + 11910400, "c3bf7a7f74f7c32b"),
-    ("full", "grad"): (504659968 + 24824832, "c3bf7a7f74f7c32b"),
+    ("full", "ls"): (2006893312 + 11926272, "9f3ad314c67ee749"),
+    ("full", "grad"): (504651264 + 24779264, "9f3ad314c67ee749"),
     # the IC sweeps on the same 256x256x128 grid with one coil (their work does not depend on it)
-    ("full", "ic_fwd"): (79717120 + 37039360, "b6d43e25cc88cb40"),
-    ("full", "ic_bwd"): (135755520 + 19821312, "b6d43e25cc88cb40"),
+    ("full", "ic_fwd"): (79791616 + 37023744, "d44f8776920828ab"),
+    ("full", "ic_bwd"): (137298432 + 18705664, "d44f8776920828ab"),
 }
 
 

@@ -201,7 +201,9 @@ __global__ void __launch_bounds__(kThreads) k_grad(DataArgs a) {
     const T beta = (T)a.beta;
     auto upd = [&](long long k) -> T { return z ? w_in[k] + alpha * z[k] : w_in[k]; };
     const long long nm = a.istate[I_NMASK];
-    double acc = 0.0;
+    // the thread's cost and penalty sums in T with Kahan compensation, converted to double
+    // once (per-voxel FP64 additions would queue on GB300's narrow FP64 pipe)
+    T cs = 0, cc = 0, rs = 0, rc = 0;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nm;
          k += (long long)gridDim.x * blockDim.x) {
         const long long j = a.vlist[k];
@@ -219,9 +221,16 @@ __global__ void __launch_bounds__(kThreads) k_grad(DataArgs a) {
         eval_any<T, NC, true, true>(a, k, wj, cst, gr, cu);
         if (g) g[j] = gr + beta * lap;
         if (d) d[j] = cu;
-        acc += (double)cst + 0.5 * a.beta * (double)reg;
+        {
+            const T y1 = cst - cc, t1 = cs + y1;
+            cc = (t1 - cs) - y1;
+            cs = t1;
+            const T y2 = reg - rc, t2 = rs + y2;
+            rc = (t2 - rs) - y2;
+            rs = t2;
+        }
     }
-    double v[1] = {acc}, out[1];
+    double v[1] = {((double)cs - (double)cc) + 0.5 * a.beta * ((double)rs - (double)rc)}, out[1];
     if (last_block_reduce<1>(v, a.partials, (unsigned*)(a.istate + I_DONE0), out, sbuf)) {
         if (threadIdx.x == 0) {
             const double total = a.scal[S_K] + out[0];

@@ -873,7 +873,10 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_ic_bwd(IcArgs a) {
             }
             // write back, then the dot products (off the wavefront's critical path).  The loads of
             // g and g_prev go out kWb rows at a time, so that a tile pays a few memory round
-            // trips here, not one per row (the CTA claims its next tile only after this)
+            // trips here, not one per row (the CTA claims its next tile only after this).  A
+            // thread's 32 products are summed in T with Kahan compensation and converted to
+            // double once: per-product FP64 additions would queue on GB300's narrow FP64 pipe
+            // (about 1/64 of the FP32 rate) behind every other CTA on the SM.
             const int nvalid = min(32, nx - x0);
             const int z = z0 + wz;
             const bool zin = z < nz && lane < nvalid;
@@ -881,6 +884,7 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_ic_bwd(IcArgs a) {
             double acc[2] = {0.0, 0.0};
             if (zin) {
                 constexpr int kWb = 16;
+                T s0 = 0, c0 = 0, s1 = 0, c1 = 0;  // Kahan sums of g p and g_prev p
                 for (int r0 = 0; r0 < 32; r0 += kWb) {
                     T pv[kWb], gv[kWb], gpv[kWb];
 #pragma unroll
@@ -895,10 +899,16 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_ic_bwd(IcArgs a) {
                     }
 #pragma unroll
                     for (int k = 0; k < kWb; ++k) {
-                        acc[0] += (double)(gv[k] * pv[k]);
-                        acc[1] += (double)(gpv[k] * pv[k]);
+                        const T y0k = gv[k] * pv[k] - c0, t0 = s0 + y0k;
+                        c0 = (t0 - s0) - y0k;
+                        s0 = t0;
+                        const T y1k = gpv[k] * pv[k] - c1, t1 = s1 + y1k;
+                        c1 = (t1 - s1) - y1k;
+                        s1 = t1;
                     }
                 }
+                acc[0] = (double)s0 - (double)c0;
+                acc[1] = (double)s1 - (double)c1;
             }
             if (a.tile_part) {
                 block_sum_compute(acc, sbuf);
