@@ -111,6 +111,58 @@ __device__ __forceinline__ T polar_angle(double wr, double wi) {
     return (T)((fr != 0.0f || fi != 0.0f) ? atan2f(fi, fr) : 0.0f);
 }
 
+// ------------------------------------------------------------------ float-float arithmetic
+//
+// FP32 field-map setup: the cost constant K_j = (sum_m A_m)^2 - (sum_m |Z_m|)^2 cancels
+// heavily when the coil-combined echoes are in phase, so its inputs must be accurate far
+// beyond float; GB300's FP64 pipe runs at about 1/64 of the FP32 rate, so they are carried as
+// unevaluated float pairs hi + lo (about 48 significant bits) on the FP32 pipe instead:
+// Knuth's two-sum, the FMA two-product, and Dekker's double-length add, multiply and square
+// root built on them.
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+    const float s = a + b, bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ FF ff_fast(float a, float b) {  // |a| >= |b| (or a == 0)
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ FF ff_prod(float a, float b) {  // exact product
+    const float p = a * b;
+    return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ FF ff_neg(FF x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ FF ff_add(FF x, FF y) {
+    const FF s = ff_two_sum(x.hi, y.hi);
+    const FF t = ff_two_sum(x.lo, y.lo);
+    const FF u = ff_fast(s.hi, s.lo + t.hi);
+    return ff_fast(u.hi, u.lo + t.lo);
+}
+__device__ __forceinline__ FF ff_mul(FF x, FF y) {
+    const FF p = ff_prod(x.hi, y.hi);
+    return ff_fast(p.hi, fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, p.lo)));
+}
+__device__ __forceinline__ FF ff_sqr(FF x) {
+    const FF p = ff_prod(x.hi, x.hi);
+    return ff_fast(p.hi, fmaf(2.0f * x.hi, x.lo, p.lo));
+}
+__device__ __forceinline__ FF ff_sqrt(FF x) {  // x >= 0: one Newton step from sqrtf(hi)
+    if (!(x.hi > 0.0f)) return {0.0f, 0.0f};
+    const float r = sqrtf(x.hi);
+    const FF rr = ff_prod(r, r);
+    const float d = ((x.hi - rr.hi) - rr.lo) + x.lo;
+    return ff_fast(r, d * (0.5f / r));
+}
+__device__ __forceinline__ FF ff_recip(FF x) {  // x > 0: one Newton step from 1 / hi
+    const float q = 1.0f / x.hi;
+    const FF p = ff_prod(q, x.hi);
+    const float r = ((1.0f - p.hi) - p.lo) - q * x.lo;
+    return ff_fast(q, q * r);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kSetupThreads) k_setup(SetupArgs a) {
     using T2 = typename V2<T>::t;
@@ -163,6 +215,83 @@ __global__ void __launch_bounds__(kSetupThreads) k_setup(SetupArgs a) {
             continue;
         }
         a.vlist[k] = (int)j;
+        if (sizeof(T) == 4 && !a.wf) {
+            // FP32 field-map case in float-float (see above): the same quantities as the
+            // double path below, W_cm = conj(s_c) y_cm / sqrt(L S) formed from exact products
+            // of the float inputs, the amplitudes and K_j carried to about 48 bits; the stored
+            // polar forms and the Eq. 6 start are float.  Float-float has float's exponent
+            // range, so the coil maps and the images are first scaled by exact powers of two
+            // that bring their largest component near 1 (coil sensitivities fall to the
+            // subnormal range at the edge of a field of view): W is unchanged by the coil-map
+            // scale and scales by 2^-ey with the image scale, undone on the stored amplitudes
+            // and on K_j.
+            float smax = 0.0f, ymax = 0.0f;
+            for (int c = 0; c < nc; ++c) {
+                if (sm) smax = fmaxf(smax, fmaxf(fabsf((float)sm[(size_t)c * nv + j].x),
+                                                 fabsf((float)sm[(size_t)c * nv + j].y)));
+                for (int mm = 0; mm < L; ++mm) {
+                    const T2 yv = y[((size_t)mm * nc + c) * nv + j];
+                    ymax = fmaxf(ymax, fmaxf(fabsf((float)yv.x), fabsf((float)yv.y)));
+                }
+            }
+            const int es = (sm && smax > 0.0f) ? ilogbf(smax) : 0, ey = ymax > 0.0f ? ilogbf(ymax) : 0;
+            FF S = {0.0f, 0.0f};
+            for (int c = 0; c < nc; ++c) {
+                const float sr = sm ? ldexpf((float)sm[(size_t)c * nv + j].x, -es) : 1.0f;
+                const float si = sm ? ldexpf((float)sm[(size_t)c * nv + j].y, -es) : 0.0f;
+                S = ff_add(S, ff_add(ff_prod(sr, sr), ff_prod(si, si)));
+            }
+            const bool sok = S.hi > 0.0f;
+            const FF scale = sok ? ff_recip(ff_sqrt(ff_mul(S, FF{(float)L, 0.0f}))) : FF{0.0f, 0.0f};
+            FF Zr[FM_MAX_ECHO], Zi[FM_MAX_ECHO];
+            FF sa = {0.0f, 0.0f}, sz = {0.0f, 0.0f};
+            for (int mm = 0; mm < L; ++mm) {
+                FF zr = {0.0f, 0.0f}, zi = {0.0f, 0.0f}, am = {0.0f, 0.0f};
+                for (int c = 0; c < nc; ++c) {
+                    const float sr = sm ? ldexpf((float)sm[(size_t)c * nv + j].x, -es) : 1.0f;
+                    const float si = sm ? ldexpf((float)sm[(size_t)c * nv + j].y, -es) : 0.0f;
+                    const T2 yv = y[((size_t)mm * nc + c) * nv + j];
+                    const float yr = ldexpf((float)yv.x, -ey), yi = ldexpf((float)yv.y, -ey);
+                    // conj(s) * y, scaled (2^-ey W)
+                    const FF wr = ff_mul(ff_add(ff_prod(sr, yr), ff_prod(si, yi)), scale);
+                    const FF wi = ff_mul(ff_add(ff_prod(sr, yi), ff_neg(ff_prod(si, yr))), scale);
+                    zr = ff_add(zr, wr);
+                    zi = ff_add(zi, wi);
+                    const FF amp = ff_sqrt(ff_add(ff_sqr(wr), ff_sqr(wi)));
+                    am = ff_add(am, amp);
+                    if (coils) {
+                        T2 o;
+                        o.x = (T)ldexpf(amp.hi, ey);
+                        o.y = (T)((wr.hi != 0.0f || wi.hi != 0.0f) ? atan2f(wi.hi, wr.hi) : 0.0f);
+                        coils[((size_t)mm * nc + c) * nv + k] = o;
+                    }
+                }
+                Zr[mm] = zr;
+                Zi[mm] = zi;
+                sa = ff_add(sa, am);
+                sz = ff_add(sz, ff_sqrt(ff_add(ff_sqr(zr), ff_sqr(zi))));
+            }
+            for (int p = 0; p < a.pr.P; ++p) {
+                const int mm = a.pr.m[p], n = a.pr.n[p];
+                // R = conj(Z_m) Z_n
+                const float rr = Zr[mm].hi * Zr[n].hi + Zi[mm].hi * Zi[n].hi;
+                const float ri = Zr[mm].hi * Zi[n].hi - Zi[mm].hi * Zr[n].hi;
+                T2 o;
+                o.x = (T)ldexpf(hypotf(rr, ri), 2 * ey);
+                o.y = (T)((rr != 0.0f || ri != 0.0f) ? atan2f(ri, rr) : 0.0f);
+                pairs[(size_t)p * nv + k] = o;
+            }
+            if (sok) {
+                const FF kj = ff_mul(ff_add(sa, ff_neg(sz)), ff_add(sa, sz));
+                kacc += ldexp((double)kj.hi + (double)kj.lo, 2 * ey);
+            }
+            if (a.rho) ((T*)a.rho)[k] = (T)ldexpf(sa.hi * sa.hi, 2 * ey);
+            // Eq. 6: angle(conj(z_1) z_2) / (t_2 - t_1)
+            const float er = Zr[0].hi * Zr[1].hi + Zi[0].hi * Zi[1].hi;
+            const float ei = Zr[0].hi * Zi[1].hi - Zi[0].hi * Zr[1].hi;
+            w0[j] = (T)((sok && (er != 0.0f || ei != 0.0f)) ? atan2f(ei, er) / (float)(a.te1 - a.te0) : 0.0f);
+            continue;
+        }
         double S = 0.0;
         for (int c = 0; c < nc; ++c) {
             const double sr = sm ? (double)sm[(size_t)c * nv + j].x : 1.0;
