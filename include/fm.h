@@ -96,8 +96,10 @@ typedef struct fm_opts {
     int nls;             /* monotonic line-search steps per outer iteration (N_i), >= 1; default 5 */
     int precond;         /* FM_PC_IC0 (default) | FM_PC_DIAG | FM_PC_NONE | FM_PC_RB | FM_PC_ICT */
     int curvature;       /* FM_CURV_LITERAL (default) | FM_CURV_COMBINED */
-    long long spin_limit;/* polls (at most about 0.3 us apart) before a device-side wait gives
-                            up with FM_ERR_TIMEOUT; default 1<<21 (about half a second) */
+    long long spin_limit;/* polls before a device-side wait gives up with FM_ERR_TIMEOUT (a poll
+                            is one memory round trip, a barrier check or one bounded hardware
+                            wait step, each about a microsecond at most); default 1<<21 (a
+                            few seconds at most) */
     int use_graph;       /* 1: replay the outer iteration as a captured CUDA graph (default 1) */
     double droptol;      /* FM_PC_ICT only: tolerance relative to H_max, finite, >= 0; default 1e-3 */
 } fm_opts;
