@@ -44,8 +44,8 @@ NCU_TRAFFIC_BYTES = {  # (bytes per launch, kernel_src_hash of the sources measu
     ("full", "ls"): (2006893312 + 11926272, "9f3ad314c67ee749"),
     ("full", "grad"): (504651264 + 24779264, "9f3ad314c67ee749"),
     # the IC sweeps on the same 256x256x128 grid with one coil (their work does not depend on it)
-    ("full", "ic_fwd"): (79791616 + 37023744, "d44f8776920828ab"),
-    ("full", "ic_bwd"): (137298432 + 18705664, "d44f8776920828ab"),
+    ("full", "ic_fwd"): (79556096 + 36898304, "172c2b0c4db1ac1f"),
+    ("full", "ic_bwd"): (137411328 + 18780416, "172c2b0c4db1ac1f"),
 }
 
 

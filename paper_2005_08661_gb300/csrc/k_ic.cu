@@ -404,7 +404,9 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long* m) {
 }
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long* m, unsigned parity) {
     unsigned ok;
-    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+    // suspend hint 1000 ns: each call returns within about a microsecond, so spin_limit calls
+    // bound the wait
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, 1000;\n\t"
                  "selp.u32 %0, 1, 0, p;\n\t}"
                  : "=r"(ok) : "r"(smem_u32(m)), "r"(parity) : "memory");
     return ok != 0;
