@@ -1106,6 +1106,7 @@ int fm_set_data(fm_ctx* c, const void* y, const void* smap, const double* te, co
             pr.m[pr.P] = m;
             pr.n[pr.P] = n;
             pr.dt[pr.P] = te[m] - te[n];
+            pr.dtt[pr.P] = (float)(pr.dt[pr.P] * 683565275.57643158);  // 2^32 / (2 pi)
             pr.gmag[pr.P] = std::abs(lgam[(size_t)m * c->L + n]);
             pr.gph[pr.P] = c->wf ? std::arg(lgam[(size_t)m * c->L + n]) : 0.0;
             ++pr.P;

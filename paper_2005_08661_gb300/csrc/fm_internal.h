@@ -55,6 +55,7 @@ struct Pairs {
     double dt[kMaxPairs];   // t_m - t_n
     double gmag[kMaxPairs]; // L |Gamma_mn| (1 in the field-map case)
     double gph[kMaxPairs];  // angle Gamma_mn (0 in the field-map case)
+    float dtt[kMaxPairs];   // (t_m - t_n) 2^32 / (2 pi): a field value's fixed-point phase per unit
 };
 
 template <typename T> struct V2;

@@ -46,6 +46,77 @@ __device__ __forceinline__ float sinc_wrapped(float u) {
 }
 __device__ __forceinline__ double sinc_wrapped(double u) { return u == 0.0 ? 1.0 : sin(u) / u; }
 
+// ------------------------------------------------------------------ FP32 literal curvature
+
+// In FP32 mode (field-map model) the setup stores each coil weight's angle as a fixed-point
+// fraction of a turn in the bits of the float slot: 2^32 is one turn, so a difference of two
+// angles wraps into [-1/2, 1/2) turn by the integer subtraction's own wrap-around (Eq. 11's
+// "mod pi" of the half angle).  The water-fat model and FP64 mode store radians.
+__device__ __forceinline__ float fixed_to_radians(float bits) {
+    return (float)__float_as_int(bits) * 1.4629180792671596e-09f;  // 2 pi / 2^32
+}
+template <typename T>
+__device__ __forceinline__ T coil_angle(const DataArgs& a, T y) {
+    if constexpr (sizeof(T) == 4) return a.wf ? y : fixed_to_radians(y);
+    else return y;
+}
+
+// w (t_m - t_n) as a fixed-point angle (mod one turn) from dtt = (t_m - t_n) 2^32 / (2 pi):
+// the float product split exactly into hi + lo, each rounded to an integer.
+__device__ __forceinline__ unsigned phase_fixed(float w, float dtt) {
+    const float hi = w * dtt, lo = fmaf(w, dtt, -hi);
+    return (unsigned)(unsigned long long)__float2ll_rn(hi) + (unsigned)__float2int_rn(lo);
+}
+
+// The inner coil sum of Eq. 10 for one echo pair (m, n) in FP32, two coils d per
+// instruction (the f32x2 forms of add, multiply and fused multiply-add, rounding each
+// component as the scalar operation does):
+//   sum_c |W_cm| sum_d |W_dn| sinc(wrap(angle W_dn + w (t_m - t_n) - angle W_cm)).
+// Per term: the integer difference of the fixed-point angles (offset by half a turn, plus
+// half of the 2^9 the shift drops, to round), one funnel shift that makes the float
+// 1 + (difference + 1/2) in [1, 2) with 23 fraction bits, an exact subtraction of 1.5 that
+// leaves the wrapped angle x in turns, and the degree-5 polynomial of sinc(2 pi x) in x^2
+// (csrc/sinc_poly.py).  Even and odd d are summed apart, then added.
+template <int NC>
+__device__ __forceinline__ float coil_pair_sum_x2(const float2 (&Wm)[NC], const float2 (&Wn)[NC], unsigned ph) {
+    static_assert(NC % 2 == 0, "two coils per instruction");
+    constexpr int H = NC / 2;
+    unsigned an[NC];
+    float2 ad[H];
+#pragma unroll
+    for (int dd = 0; dd < NC; ++dd) an[dd] = (unsigned)__float_as_int(Wn[dd].y) + ph + 0x80000100u;
+#pragma unroll
+    for (int h = 0; h < H; ++h) ad[h] = make_float2(Wn[2 * h].x, Wn[2 * h + 1].x);
+    const float2 c5 = make_float2(-1.9852460622787476f, -1.9852460622787476f);
+    const float2 c4 = make_float2(6.580165386199951f, 6.580165386199951f);
+    const float2 c3 = make_float2(-12.193624496459961f, -12.193624496459961f);
+    const float2 c2 = make_float2(12.987038612365723f, 12.987038612365723f);
+    const float2 c1 = make_float2(-6.579718589782715f, -6.579718589782715f);
+    const float2 c0 = make_float2(0.9999999403953552f, 0.9999999403953552f);
+    const float2 mid = make_float2(-1.5f, -1.5f);
+    float inner = 0;
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc) {
+        const unsigned bm = (unsigned)__float_as_int(Wm[cc].y);
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            const float2 f = make_float2(__uint_as_float(__funnelshift_r(an[2 * h] - bm, 0x7Fu, 9)),
+                                         __uint_as_float(__funnelshift_r(an[2 * h + 1] - bm, 0x7Fu, 9)));
+            const float2 x = __fadd2_rn(f, mid);
+            const float2 v = __fmul2_rn(x, x);
+            float2 p = __ffma2_rn(c5, v, c4);
+            p = __ffma2_rn(p, v, c3);
+            p = __ffma2_rn(p, v, c2);
+            p = __ffma2_rn(p, v, c1);
+            p = __ffma2_rn(p, v, c0);
+            acc = __ffma2_rn(ad[h], p, acc);
+        }
+        inner = fmaf(Wm[cc].x, acc.x + acc.y, inner);
+    }
+    return inner;
+}
+
 __device__ __forceinline__ void sin_cos(float x, float* s, float* c) { sincosf(x, s, c); }
 __device__ __forceinline__ void sin_cos(double x, double* s, double* c) { sincos(x, s, c); }
 
@@ -80,7 +151,7 @@ __device__ __forceinline__ void eval_voxel(const DataArgs& a, long long j /* com
                 for (int dd = 0; dd < NC; ++dd) {
                     const T2 q = coils[((size_t)n * NC + dd) * nv + j];
                     ad[dd] = q.x;
-                    psi[dd] = q.y + w * dt;
+                    psi[dd] = coil_angle(a, q.y) + w * dt;
                 }
                 T inner = 0;
 #pragma unroll
@@ -88,7 +159,7 @@ __device__ __forceinline__ void eval_voxel(const DataArgs& a, long long j /* com
                     const T2 q = coils[((size_t)m * NC + cc) * nv + j];
                     T acc = 0;
 #pragma unroll
-                    for (int dd = 0; dd < NC; ++dd) acc += ad[dd] * sinc_wrapped(wrap_angle(psi[dd] - q.y));
+                    for (int dd = 0; dd < NC; ++dd) acc += ad[dd] * sinc_wrapped(wrap_angle(psi[dd] - coil_angle(a, q.y)));
                     inner += q.x * acc;
                 }
                 d_acc += dt * dt * inner;
@@ -103,7 +174,7 @@ __device__ __forceinline__ void eval_voxel(const DataArgs& a, long long j /* com
                     T acc = 0;
                     for (int dd = 0; dd < nc; ++dd) {
                         const T2 r = coils[((size_t)n * nc + dd) * nv + j];
-                        acc += r.x * sinc_wrapped(wrap_angle(r.y + w * dt + gph - q.y));
+                        acc += r.x * sinc_wrapped(wrap_angle(coil_angle(a, r.y) + w * dt + gph - coil_angle(a, q.y)));
                     }
                     inner += q.x * acc;
                 }
@@ -150,18 +221,21 @@ __device__ __forceinline__ void eval_voxel_fixed(const DataArgs& a, long long j 
             if (COST) c_acc += R[p].x * (s * s);
             g_acc += dt * R[p].x * (s * c);
             if (CURV) {
-                if (NC == 1) {
+                if constexpr (NC == 1) {
                     d_acc += dt * dt * R[p].x * sinc_wrapped(wrap_angle(th));
+                } else if constexpr (sizeof(T) == 4 && NCL % 2 == 0) {
+                    d_acc += dt * dt * coil_pair_sum_x2<NCL>(W[m], W[n], phase_fixed(w, a.pr.dtt[p]));
                 } else {
                     T psi[NCL];
 #pragma unroll
-                    for (int dd = 0; dd < NCL; ++dd) psi[dd] = W[n][dd].y + w * dt;
+                    for (int dd = 0; dd < NCL; ++dd) psi[dd] = coil_angle(a, W[n][dd].y) + w * dt;
                     T inner = 0;
 #pragma unroll
                     for (int cc = 0; cc < NCL; ++cc) {
                         T acc = 0;
 #pragma unroll
-                        for (int dd = 0; dd < NCL; ++dd) acc += W[n][dd].x * sinc_wrapped(wrap_angle(psi[dd] - W[m][cc].y));
+                        for (int dd = 0; dd < NCL; ++dd)
+                            acc += W[n][dd].x * sinc_wrapped(wrap_angle(psi[dd] - coil_angle(a, W[m][cc].y)));
                         inner += W[m][cc].x * acc;
                     }
                     d_acc += dt * dt * inner;
@@ -188,7 +262,7 @@ __device__ __forceinline__ void eval_any(const DataArgs& a, long long j, T w, T&
 // Runs over the compact list of mask voxels; entries outside the mask are never written
 // (the host zeroes them once).
 template <typename T, int NC>
-__global__ void __launch_bounds__(kThreads) k_grad(DataArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) k_grad(DataArgs a) {
     __shared__ double sbuf[32];
     const int nx = a.geo.nx;
     const long long nxy = (long long)nx * a.geo.ny;

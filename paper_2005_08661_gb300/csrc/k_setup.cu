@@ -262,7 +262,10 @@ __global__ void __launch_bounds__(kSetupThreads) k_setup(SetupArgs a) {
                     if (coils) {
                         T2 o;
                         o.x = (T)ldexpf(amp.hi, ey);
-                        o.y = (T)((wr.hi != 0.0f || wi.hi != 0.0f) ? atan2f(wi.hi, wr.hi) : 0.0f);
+                        // the angle as a fixed-point fraction of a turn (2^32 = one turn) in
+                        // the float slot's bits, the form the FP32 curvature kernels read
+                        const float ang = (wr.hi != 0.0f || wi.hi != 0.0f) ? atan2f(wi.hi, wr.hi) : 0.0f;
+                        o.y = (T)__int_as_float(__double2int_rn((double)ang * 683565275.57643158));
                         coils[((size_t)mm * nc + c) * nv + k] = o;
                     }
                 }
