@@ -41,11 +41,11 @@ if ROOT not in sys.path:
 # sources have changed since is reported as null.
 KERNEL_SOURCES = {"ls": ("k_data.cu",), "grad": ("k_data.cu",), "ic_fwd": ("k_ic.cu",), "ic_bwd": ("k_ic.cu",)}
 NCU_TRAFFIC_BYTES = {  # (bytes per launch, kernel_src_hash of the sources measured)
-    ("full", "ls"): (2006893312 + 11926272, "9f3ad314c67ee749"),
-    ("full", "grad"): (504651264 + 24779264, "9f3ad314c67ee749"),
+    ("full", "ls"): (2007369472 + 12702720, "707eb6e8e356ed0a"),
+    ("full", "grad"): (506203648 + 27375104, "707eb6e8e356ed0a"),
     # the IC sweeps on the same 256x256x128 grid with one coil (their work does not depend on it)
-    ("full", "ic_fwd"): (79556096 + 36898304, "172c2b0c4db1ac1f"),
-    ("full", "ic_bwd"): (137411328 + 18780416, "172c2b0c4db1ac1f"),
+    ("full", "ic_fwd"): (79724800 + 37426688, "355df626ce512b8a"),
+    ("full", "ic_bwd"): (137366784 + 18694656, "355df626ce512b8a"),
 }
 
 

@@ -68,6 +68,31 @@ __device__ __forceinline__ unsigned phase_fixed(float w, float dtt) {
     return (unsigned)(unsigned long long)__float2ll_rn(hi) + (unsigned)__float2int_rn(lo);
 }
 
+// sin(2 pi x)/(2 pi x) for x in [-1/2, 1/2] turns as a degree-5 polynomial in x^2: the
+// discrete minimax fit derived by csrc/sinc_poly.py (truncation error 6.1e-8, 2.1e-7 in
+// float Horner form).
+constexpr float kSincT0 = 0.9999999403953552f;
+constexpr float kSincT1 = -6.579718589782715f;
+constexpr float kSincT2 = 12.987038612365723f;
+constexpr float kSincT3 = -12.193624496459961f;
+constexpr float kSincT4 = 6.580165386199951f;
+constexpr float kSincT5 = -1.9852460622787476f;
+
+// The wrapped angle in turns from the difference t of two fixed-point angles that carry the
+// offset 2^31 + 2^8: one funnel shift makes the float 1 + (x + 1/2) in [1, 2) with 23
+// fraction bits (the 2^8 rounds the 9 bits the shift drops), and subtracting 1.5 is exact.
+__device__ __forceinline__ float turns_of(unsigned t) {
+    return __uint_as_float(__funnelshift_r(t, 0x7Fu, 9)) - 1.5f;
+}
+__device__ __forceinline__ float sinc_turns(float x) {
+    const float v = x * x;
+    float p = fmaf(kSincT5, v, kSincT4);
+    p = fmaf(p, v, kSincT3);
+    p = fmaf(p, v, kSincT2);
+    p = fmaf(p, v, kSincT1);
+    return fmaf(p, v, kSincT0);
+}
+
 // The inner coil sum of Eq. 10 for one echo pair (m, n) in FP32, two coils d per
 // instruction (the f32x2 forms of add, multiply and fused multiply-add, rounding each
 // component as the scalar operation does):
@@ -87,12 +112,9 @@ __device__ __forceinline__ float coil_pair_sum_x2(const float2 (&Wm)[NC], const 
     for (int dd = 0; dd < NC; ++dd) an[dd] = (unsigned)__float_as_int(Wn[dd].y) + ph + 0x80000100u;
 #pragma unroll
     for (int h = 0; h < H; ++h) ad[h] = make_float2(Wn[2 * h].x, Wn[2 * h + 1].x);
-    const float2 c5 = make_float2(-1.9852460622787476f, -1.9852460622787476f);
-    const float2 c4 = make_float2(6.580165386199951f, 6.580165386199951f);
-    const float2 c3 = make_float2(-12.193624496459961f, -12.193624496459961f);
-    const float2 c2 = make_float2(12.987038612365723f, 12.987038612365723f);
-    const float2 c1 = make_float2(-6.579718589782715f, -6.579718589782715f);
-    const float2 c0 = make_float2(0.9999999403953552f, 0.9999999403953552f);
+    const float2 c5 = make_float2(kSincT5, kSincT5), c4 = make_float2(kSincT4, kSincT4);
+    const float2 c3 = make_float2(kSincT3, kSincT3), c2 = make_float2(kSincT2, kSincT2);
+    const float2 c1 = make_float2(kSincT1, kSincT1), c0 = make_float2(kSincT0, kSincT0);
     const float2 mid = make_float2(-1.5f, -1.5f);
     float inner = 0;
 #pragma unroll
@@ -167,6 +189,25 @@ __device__ __forceinline__ void eval_voxel(const DataArgs& a, long long j /* com
                 // runtime coil count; also the water-fat model, whose angle r_cdmn carries the
                 // phase of Gamma_mn and |r_cdmn| the factor L |Gamma_mn| (0 and 1 otherwise)
                 const int m = a.pr.m[p], n = a.pr.n[p], nc = a.nc;
+                if constexpr (sizeof(T) == 4) {
+                    if (!a.wf) {
+                        // field-map model in FP32: fixed-point angles (as in coil_pair_sum_x2)
+                        const unsigned ph = phase_fixed(w, a.pr.dtt[p]) + 0x80000100u;
+                        float inner = 0;
+                        for (int cc = 0; cc < nc; ++cc) {
+                            const float2 q = coils[((size_t)m * nc + cc) * nv + j];
+                            const unsigned bm = (unsigned)__float_as_int(q.y) - ph;
+                            float acc = 0;
+                            for (int dd = 0; dd < nc; ++dd) {
+                                const float2 r = coils[((size_t)n * nc + dd) * nv + j];
+                                acc += r.x * sinc_turns(turns_of((unsigned)__float_as_int(r.y) - bm));
+                            }
+                            inner += q.x * acc;
+                        }
+                        d_acc += dt * dt * inner;
+                        continue;  // the curvature is the last piece of the pair's work
+                    }
+                }
                 const T gph = (T)a.pr.gph[p];
                 T inner = 0;
                 for (int cc = 0; cc < nc; ++cc) {

@@ -28,12 +28,8 @@ def _radian_coeffs():
 
 
 def _turn_coeffs():
-    body = _src().split("coil_pair_sum_x2(")[1]
-    cs = {}
-    for k in range(6):
-        m = re.search(r"const float2 c%d = make_float2\((-?[0-9.e-]+)f" % k, body)
-        cs[k] = float(m.group(1))
-    return [cs[k] for k in range(6)]
+    src = _src()
+    return [float(re.search(r"constexpr float kSincT%d = (-?[0-9.e-]+)f;" % k, src).group(1)) for k in range(6)]
 
 
 def f32(x):
