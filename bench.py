@@ -41,8 +41,8 @@ if ROOT not in sys.path:
 # sources have changed since is reported as null.
 KERNEL_SOURCES = {"ls": ("k_data.cu",), "grad": ("k_data.cu",), "ic_fwd": ("k_ic.cu",), "ic_bwd": ("k_ic.cu",)}
 NCU_TRAFFIC_BYTES = {  # (bytes per launch, kernel_src_hash of the sources measured)
-    ("full", "ls"): (2007369472 + 12702720, "707eb6e8e356ed0a"),
-    ("full", "grad"): (506203648 + 27375104, "707eb6e8e356ed0a"),
+    ("full", "ls"): (2007300608 + 12793088, "4494fb0460a61f4d"),
+    ("full", "grad"): (506223872 + 27680256, "4494fb0460a61f4d"),
     # the IC sweeps on the same 256x256x128 grid with one coil (their work does not depend on it)
     ("full", "ic_fwd"): (79724800 + 37426688, "355df626ce512b8a"),
     ("full", "ic_bwd"): (137366784 + 18694656, "355df626ce512b8a"),
