@@ -128,3 +128,18 @@ def test_fixed_point_wrap_edges():
     an_bad = to_fixed(f32(0.3))
     bad = float(term_fixed(an_bad, to_fixed(f32(0.3)), c))
     assert abs(bad - 1.0) > 0.5
+
+
+def test_fixed_point_scale_constants_agree():
+    """The setup's angle store, the pair table's phase factor and the kernels' conversion
+    back to radians all use one turn = 2^32."""
+    csrc = os.path.join(os.path.dirname(SRC))
+    with open(os.path.join(csrc, "k_setup.cu")) as f:
+        setup = f.read()
+    with open(os.path.join(csrc, "fm_api.cu")) as f:
+        api = f.read()
+    store = float(re.search(r"__double2int_rn\(\(double\)ang \* ([0-9.]+)\)", setup).group(1))
+    phase = float(re.search(r"pr\.dtt\[pr\.P\] = \(float\)\(pr\.dt\[pr\.P\] \* ([0-9.]+)\)", api).group(1))
+    back = float(re.search(r"__float_as_int\(bits\) \* ([0-9.e-]+)f", _src()).group(1))
+    assert abs(store / TURN - 1) < 1e-15 and abs(phase / TURN - 1) < 1e-15
+    assert abs(back * TURN - 1) < 1e-7
