@@ -94,6 +94,29 @@ def test_cost_gradient_curvature_and_init(prec, case):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("te", [(0.0, 2.5), (0.0, 1.5, 4.0, 9.5)])
+@pytest.mark.parametrize("nc", [2, 3, 8])
+def test_cost_gradient_curvature_other_echo_counts(prec, te, nc):
+    """Two and four echoes: the evaluators for any echo count (compile-time coil counts 2
+    and 8, the runtime coil count for 3), whose curvature reads the coil angles in FP32 as
+    fixed-point turns (the runtime one wraps them in fixed point), against the oracle."""
+    vol = make_volume(19, 13, 7, ncoil=nc, te=te, snr_db=15.0, seed=300 + nc + 7 * len(te), fmax_hz=150.0,
+                      nblobs=3)
+    o = Oracle.from_volume(vol)
+    w = _omega(o, vol, seed=2)
+    fm = open_fm(vol, prec)
+    cost, g, d = fm.cost_grad(to_dev(w, prec))
+    tol = TOL[prec]
+    atol = _fp32_cost_atol(vol, w) if prec == "fp32" else 1e-12
+    assert cost == pytest.approx(o.cost(w), rel=tol["cost"], abs=atol)
+    g_ref, d_ref = o.grad(w), o.curv(w)
+    g, d = to_np(g), to_np(d)
+    np.testing.assert_allclose(g, g_ref, rtol=0, atol=tol["g"] * max(np.abs(g_ref).max(), 1e-30))
+    np.testing.assert_allclose(d, d_ref, rtol=tol["d"], atol=tol["d"] * max(np.abs(d_ref).max(), 1e-30))
+    fm.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("case", CASES)
 def test_ic0_pivots_and_apply(prec, case):
     vol = _vol(*case, seed=1)
