@@ -6,10 +6,10 @@ code with the CUDA path.  See fm_oracle.c for what each function computes and th
 paper passages it follows.
 
 Pins: every function here is checked against something the paper or the
-mathematics fixes (tests/test_oracle_*.py).  The exact iterate sequence of the
-solver beyond those pins (search-direction sign, Polak-Ribiere form, fixed inner
-step count) follows the readings stated in fm_oracle.c and is "parity unpinned"
-against the paper itself.
+mathematics fixes (tests/test_oracle_*.py); the Polak-Ribiere step is pinned by the
+conjugacy of successive directions on near-quadratic cases (tests/test_oracle_pr.py).
+The fixed inner step count of the line search and its zero starting step follow the
+readings stated in fm_oracle.c and are "parity unpinned" against the paper itself.
 """
 from .oracle import (Oracle, build_oracle, curv_raw, get_threads, ic0_factor, ic0_solve, ict_factor, lib_path,
                      set_threads, voxel_r, voxel_terms, wf_gamma)
